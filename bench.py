@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the splattable-neural-primitive tile rasterizer.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+projection/bounding -> key emission -> radix sort -> tile ranges -> forward
+rasterizer -> backward rasterizer -> per-primitive gradient post-passes, on the
+100k-primitive, four-view 1920 x 1080 workload (N_sigma = 16, colour MLP
+N_c = 32, FP32).  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s fwd and fwd+bwd at 1080p, 100k–500k primitives vs plain FP32 fwd; % roofline"
+WORKLOAD = "fwd100k_1080p_4view"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+# ----------------------------------------------------------------------------- work model
+def fma_per_unit(n_sigma: int, n_c: int):
+    """Algorithmic FP32 FMA counts per candidate / hit / composited pair (forward and backward)."""
+    mlp = 0 if n_c == 0 else (3 + 8) * n_c + n_c * n_c + 3 * n_c
+    fwd = {"cand": 21, "hit": 12 + 12 * n_sigma, "comp": 10 + mlp}
+    bwd = {"cand": 21, "hit": 12 + 12 * n_sigma, "comp": 10 + 3 * mlp + 24 * n_sigma + 80}
+    return fwd, bwd
+
+
+def flops(counts, per_unit):
+    return 2.0 * (counts["cand"] * per_unit["cand"] + counts["hit"] * per_unit["hit"] +
+                  counts["comp"] * per_unit["comp"])
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) leg
+def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True):
+    """Time the FP64 oracle on a bounded sample of the workload: the key stage of every
+    view (pro-rated to the sample), then forward (+ gradient) of `tiles_per_view`
+    seeded 16 x 16 tiles per view.  Returns (pixels, seconds, cores)."""
+    import numpy as np
+
+    from oracle import grad as G
+    from oracle import oracle as O
+    O.build()
+    sc, cams = wl.scene, wl.cameras
+    t0 = time.perf_counter()
+    cs = O.CScene(sc)
+    tl = O.tile_keys(sc, cams, 16, cs)
+    t_keys = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    npx = 0
+    t_pix = 0.0
+    total_px = sum(c.n_pixels for c in cams)
+    for v, cam in enumerate(cams):
+        tx_n, ty_n = O.tiles_xy(cam, 16)
+        tiles = rng.choice(tx_n * ty_n, size=tiles_per_view, replace=False)
+        pix = []
+        for t in tiles:
+            ty, tx = divmod(int(t), tx_n)
+            ys, xs = np.mgrid[ty * 16:min(ty * 16 + 16, cam.height), tx * 16:min(tx * 16 + 16, cam.width)]
+            pix.append((ys * cam.width + xs).ravel())
+        pix = np.concatenate(pix).astype(np.int32)
+        t1 = time.perf_counter()
+        out = O.render_view_tiled(sc, cams, v, tl, 16, pix, cs=cs)
+        if with_grad:
+            gt = tl.view_tile_off[v] + O.pixel_tile(cam, 16, pix)
+            lp = (tl.vals.astype(np.int64) % sc.n).astype(np.int32)
+            dL = rng.normal(size=(len(pix), 3))
+            G.grads(sc, cam, pix, gt, tl.tile_off, lp, dL)
+        t_pix += time.perf_counter() - t1
+        npx += len(pix)
+    secs = t_keys * (npx / total_px) + t_pix
+    return npx, secs, os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300 import build as B
+    from paper_2510_08491_gb300 import synth
+    from paper_2510_08491_gb300.render import Renderer, pack_scene
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    wl = synth.workload(args.workload)
+    sc, cams = wl.scene, wl.cameras
+    r = Renderer(dev)
+    ps = pack_scene(sc)
+    P = sum(c.n_pixels for c in cams)
+    cfg = L.make_config(t_min=wl.t_min, timing=True)
+    img = torch.empty((P, 3), device="cuda", dtype=torch.float32)
+    dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 1e-3
+    g_geom = torch.zeros_like(ps.geom)
+    g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g_geom.zero_()
+        g_net.zero_()
+        r.forward(ps, cams, cfg, out=img)
+        r.backward(ps, dL, g_geom, g_net)
+
+    def fwd_only():
+        r.forward(ps, cams, cfg, out=img)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = r.stats()
+    counts = {"cand": stats.n_candidates, "hit": stats.n_hits, "comp": stats.n_composited}
+    dist = world > 1
+    if dist:
+        import torch.distributed as D
+    r.ctx.stage_times(reset=True)
+    l0 = L.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        if dist:
+            D.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            D.barrier()
+    launches = (L.kernel_launches() - l0) // max(args.steps, 1)
+    ms = e0.elapsed_time(e1) / args.steps
+    st = r.ctx.stage_times(reset=True)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        D.all_reduce(t, op=D.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * P / (ms * 1e-3) / 1e6
+
+    # forward only (same workload), for the "vs plain FP32 forward" comparison
+    for _ in range(2):
+        fwd_only()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    nf = max(args.steps, 3)
+    for _ in range(nf):
+        fwd_only()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = f0.elapsed_time(f1) / nf
+    r.ctx.stage_times(reset=True)
+
+    # end to end through the public API with host buffers
+    h_geom = ps.geom.cpu().pin_memory()
+    h_net = ps.net.cpu().pin_memory()
+    h_dL = dL.cpu().pin_memory()
+    h_img = torch.empty((P, 3), dtype=torch.float32).pin_memory()
+    h_gg = torch.empty_like(g_geom, device="cpu").pin_memory()
+    h_gn = torch.empty_like(g_net, device="cpu").pin_memory()
+
+    def e2e_step():
+        ps.geom.copy_(h_geom, non_blocking=True)
+        ps.net.copy_(h_net, non_blocking=True)
+        dL.copy_(h_dL, non_blocking=True)
+        step()
+        h_img.copy_(img, non_blocking=True)
+        h_gg.copy_(g_geom, non_blocking=True)
+        h_gn.copy_(g_net, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ne = max(min(args.steps, 10), 3)
+    x0.record(stream)
+    for _ in range(ne):
+        e2e_step()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = x0.elapsed_time(x1) / ne
+    h2d = h_geom.numel() * h_geom.element_size() + h_net.numel() * h_net.element_size() + h_dL.numel() * 4
+    d2h = h_img.numel() * 4 + h_gg.numel() * 4 + h_gn.numel() * 4
+
+    # roofline of the dominant kernel (FP32 ALU bound)
+    fwd_u, bwd_u = fma_per_unit(sc.n_sigma, sc.n_c if sc.color == "mlp" else 0)
+    t_fwd = st["raster_fwd"][0] / max(st["raster_fwd"][1], 1)
+    t_bwd = st["raster_bwd"][0] / max(st["raster_bwd"][1], 1)
+    if t_bwd >= t_fwd:
+        kern, t_k, fl = "k_raster_bwd", t_bwd, flops(counts, bwd_u)
+    else:
+        kern, t_k, fl = "k_raster_fwd", t_fwd, flops(counts, fwd_u)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    clocks = clk.summary()
+    sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
+    achieved = fl / (t_k * 1e-3) / 1e12
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get(kern, {}).get("bytes_per_launch")
+    except Exception:
+        pass
+
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "primitives": sc.n, "views": len(cams),
+                   "resolution": f"{cams[0].width}x{cams[0].height}", "n_sigma": sc.n_sigma,
+                   "n_c": sc.n_c if sc.color == "mlp" else 0, "tile": 16, "step": "forward+backward",
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (network weights %.2f GB)" % (h_net.numel() * 4 / 1e9)},
+        "fwd_mpix_s": round(world * P / (ms_fwd * 1e-3) / 1e6, 3),
+        "fwd_ms": round(ms_fwd, 4),
+        "roofline": {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3),
+                     "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+                     "traffic": traffic,
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x sm_max_mhz of measured peaks"},
+        "e2e": {"value": round(world * P / (ms_e2e * 1e-3) / 1e6, 3), "unit": "Mpixel/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms_e2e, 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "stage_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in st.items()},
+        "work": {"keys": stats.n_keys, "candidates": counts["cand"], "hits": counts["hit"],
+                 "composited": counts["comp"], "pixels": P},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        npx, secs, cores = oracle_sample(wl, args.cpu_tiles)
+        res["cpu_baseline"] = {"value": round(npx / secs / 1e6, 6), "unit": "Mpixel/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"forward+gradient of {args.cpu_tiles} seeded 16x16 tiles per view "
+                                         f"({npx} px) plus the key stage pro-rated to the sample; {secs:.1f} s"}
+    return res
+
+
+def run_reference(args, rank, world):
+    from paper_2510_08491_gb300 import synth
+    if rank != 0:
+        return None
+    wl = synth.workload(args.workload)
+    times, pxs = [], []
+    for i in range(args.warmup + args.steps):
+        npx, secs, cores = oracle_sample(wl, args.ref_tiles, seed=i)
+        if i >= args.warmup:
+            times.append(secs)
+            pxs.append(npx)
+    value = sum(pxs) / sum(times) / 1e6
+    ms = 1e3 * sum(times) / len(times)
+    return {"metric": METRIC, "value": round(value, 6), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "step": "forward+backward (bounded sample)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_tiles} seeded 16x16 tiles per view per step"},
+            "e2e": {"value": round(value, 6), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-tiles", type=int, default=16)
+    ap.add_argument("--ref-tiles", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as D
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        D.init_process_group("nccl")
+    res = run_ours(args, rank, world) if args.impl == "ours" else run_reference(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as D
+        D.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

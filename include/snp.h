@@ -1,0 +1,242 @@
+/*
+ * snp.h -- C ABI of libsnp, a GB300 (sm_103a) tile rasterizer for splattable
+ * neural primitives (arXiv 2510.08491, "Splat the Net").
+ *
+ * What the library computes (Sec. 3.1-3.2 of the paper):
+ *   Each primitive is an ellipsoid {c + R(q) diag(s) v : |v| <= 1} with
+ *   s = exp(log_s) carrying a one-hidden-layer sine density network
+ *   (Eq. 5/6)  sigma(x) = w2 . cos(w0 (W1 u + b1)) + b2,  u = (x - c)/max(s).
+ *   For every pixel ray o + t d that enters the ellipsoid at t_in and leaves at
+ *   t_out, the closed-form line integral of sigma (Eq. 7/8) gives
+ *   alpha_hat = S(t_out) - S(t_in); the kernel opacity is
+ *   alpha = 1 - exp(-max(0, alpha_hat)) (Eq. 9); primitives are depth-sorted
+ *   per screen tile and alpha-blended front to back (Eq. 4) with their colour.
+ *
+ * Conventions fixed by this library where the paper is silent (camera model,
+ * depth key, near plane, early termination, colour network) are stated at
+ * each declaration below.
+ *
+ * Memory: every scene, image and gradient pointer passed in is DEVICE memory
+ * owned by the caller; the library never frees it.  Workspace (projection
+ * records, tile keys, tile ranges, per-pixel state saved for the backward pass)
+ * is owned by the context.  Calls are asynchronous on the given stream unless
+ * stated; `stream` is a cudaStream_t (NULL = legacy default stream).
+ *
+ * Errors: every call returns an snp_status; nothing is thrown across the ABI.
+ * snp_last_error() returns a message for the last failing call on a context.
+ * Asynchronous CUDA faults surface as SNP_ERR_CUDA on a later call.
+ */
+#ifndef SNP_H
+#define SNP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SNP_OK = 0,
+    SNP_ERR_INVALID_ARG = 1, /* bad pointer, size, mode or stale token */
+    SNP_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    SNP_ERR_CAPACITY = 3,    /* tile keys exceeded the reserved capacity (graph mode) */
+    SNP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    SNP_ERR_UNSUPPORTED = 5  /* combination of modes not built */
+} snp_status;
+
+enum { SNP_COLOR_CONST = 0, SNP_COLOR_MLP = 1 };
+enum { SNP_F32 = 0, SNP_BF16 = 1 };
+enum { SNP_FORM_STABLE = 0, SNP_FORM_NAIVE = 1 };
+
+/* Number of input features of the colour MLP besides the 3-d view direction. */
+#define SNP_FEAT_DIM 8
+/* Floats per primitive in the geometry array. */
+#define SNP_GEOM_STRIDE 16
+
+/* Pinhole camera, OpenCV frame (x right, y down, z forward).
+ *   R_wc   world -> camera rotation, row-major (rows are the camera axes).
+ *   eye    camera centre in world coordinates.
+ *   fx, fy, cx, cy  intrinsics in pixels; the ray of pixel (px, py) passes
+ *          through its centre: d = normalize(R_wc^T ((px + .5 - cx)/fx, (py + .5 - cy)/fy, 1)).
+ *   z_near a primitive is culled unless its whole bounding ellipsoid lies at
+ *          camera depth > z_near (camera z of the centre minus max(s) > z_near).
+ *   width, height  image size in pixels (1..32768). */
+typedef struct {
+    float R_wc[9];
+    float eye[3];
+    float fx, fy, cx, cy, z_near;
+    int32_t width, height;
+} snp_camera;
+
+/* Scene description (sizes and modes; no pointers).
+ *   n            number of primitives (0 allowed: renders background)
+ *   n_sigma      density network width N_sigma (1..64)
+ *   omega0       boosting frequency w0 of Eq. 6
+ *   color_mode   SNP_COLOR_CONST (rgb in the geometry array) or SNP_COLOR_MLP
+ *                (per-primitive colour MLP: z0 = [d, f] with d the unit ray
+ *                direction of the pixel and f an 8-d feature; z1 = relu(Wc1 z0 + bc1),
+ *                z2 = relu(Wc2 z1 + bc2), colour = sigmoid(Wc3 z2 + bc3); two hidden
+ *                layers of width n_c, the neural colour field of App. D.2)
+ *   n_c          colour MLP width: 32 or 64 (ignored for SNP_COLOR_CONST)
+ *   weight_dtype SNP_F32 or SNP_BF16: element type of the `net` array.  All
+ *                arithmetic is FP32 either way. */
+typedef struct {
+    int64_t n;
+    int32_t n_sigma;
+    int32_t color_mode;
+    int32_t n_c;
+    int32_t weight_dtype;
+    float omega0;
+    int32_t reserved_;
+} snp_scene_desc;
+
+/* Per-primitive network layout of the `net` array: element offsets of each
+ * field inside one primitive's record and the record stride, all multiples of 8
+ * elements (16 bytes in BF16, 32 in FP32).  Fields, row-major:
+ *   [0] W1 [n_sigma][3]  [1] b1 [n_sigma]  [2] w2 [n_sigma]  [3] b2 [1]
+ *   [4] feat [8]  [5] Wc1 [n_c][11]  [6] bc1 [n_c]  [7] Wc2 [n_c][n_c]  [8] bc2 [n_c]
+ *   [9] Wc3 [3][n_c]  [10] bc3 [3]   (colour fields only with SNP_COLOR_MLP; their
+ *   offsets are -1 otherwise).  Padding elements are ignored on input and left
+ *   untouched in gradients.  Pure function; never fails for valid sizes. */
+typedef struct {
+    int32_t off[11];
+    int32_t stride;
+} snp_net_layout;
+snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out);
+
+/* Scene parameters (device, caller-owned, read-only):
+ *   geom  float32 [n][16]: centre xyz, log-scale xyz, quaternion (w, x, y, z; need
+ *         not be normalised), constant rgb, 3 unused floats.
+ *   net   [n][stride] of weight_dtype, laid out as snp_get_net_layout says.
+ * Both 16-byte aligned. */
+typedef struct {
+    const float *geom;
+    const void *net;
+} snp_scene_ptrs;
+
+/* Gradients (device, caller-owned, float32, ACCUMULATED into: zero them first
+ * for a fresh gradient).  Same shapes as snp_scene_ptrs: geom [n][16] (the 3
+ * unused floats are untouched), net [n][stride] in float32 even when the
+ * weights are BF16.  Either pointer may be NULL to skip that group. */
+typedef struct {
+    float *geom;
+    float *net;
+} snp_grad_ptrs;
+
+/* Renderer configuration.
+ *   tile_size     screen tile edge in pixels: 8, 16 or 32 (0 = 16)
+ *   chunk         primitives staged per shared-memory batch (0 = library default)
+ *   integral_form SNP_FORM_STABLE: alpha_hat = Delta_t [b2 + sum_k w2_k cos(phi_k) sinc(theta_k)]
+ *                 (Eq. 8 rewritten with sin A - sin B = 2 cos((A+B)/2) sin((A-B)/2), finite
+ *                 as w0 W1_k . d -> 0); SNP_FORM_NAIVE: Eq. 8 literally, a difference of
+ *                 sines divided by w0 W1_k . d / max(s)
+ *   t_min         early termination: after compositing a primitive a pixel stops once
+ *                 its transmittance T = exp(-sum of composited alpha_hat) < t_min
+ *                 (0 disables; the dropped tail is at most t_min * max colour)
+ *   bg            background colour added with the final transmittance */
+typedef struct {
+    int32_t tile_size;
+    int32_t chunk;
+    int32_t integral_form;
+    float t_min;
+    float bg[3];
+    int32_t flags; /* SNP_FLAG_* bits */
+} snp_config;
+
+/* snp_config.flags: record CUDA events around every stage on the call's stream so
+ * that snp_stage_times can report per-stage device time (a few microseconds of
+ * event overhead per call). */
+#define SNP_FLAG_STAGE_TIMING 1
+
+/* Stages reported by snp_stage_times. */
+enum {
+    SNP_STAGE_PROJECT = 0,   /* k_project: bounding, culling, projection records */
+    SNP_STAGE_SCAN = 1,      /* exclusive scan of tile counts (+ key-count readback) */
+    SNP_STAGE_EMIT = 2,      /* tile-key emission */
+    SNP_STAGE_SORT = 3,      /* stable radix sort of (tile, depth) keys */
+    SNP_STAGE_RANGES = 4,    /* per-tile ranges */
+    SNP_STAGE_RASTER_FWD = 5,
+    SNP_STAGE_RASTER_BWD = 6,
+    SNP_STAGE_POST_BWD = 7,  /* per-primitive gradient post-passes */
+    SNP_N_STAGES = 8
+};
+
+/* Work counters of the last forward (read back synchronously). */
+typedef struct {
+    int64_t n_keys;       /* K: (tile, primitive) pairs after culling */
+    int64_t n_tiles;      /* tiles over all views */
+    int64_t n_pixels;     /* pixels over all views */
+    int64_t n_candidates; /* (pixel, list entry) pairs visited before termination */
+    int64_t n_hits;       /* of those, rays that enter the ellipsoid */
+    int64_t n_composited; /* of those, alpha_hat > 0 (colour evaluated and blended) */
+} snp_stats;
+
+typedef struct snp_context snp_context;
+
+/* Create a context on CUDA device `device` (it becomes current for the calling
+ * thread).  *out receives the context; free it with snp_destroy. */
+snp_status snp_create(int32_t device, snp_context **out);
+void snp_destroy(snp_context *ctx);
+
+/* Thread-safe message for the last failing call on ctx ("" if none). */
+const char *snp_last_error(const snp_context *ctx);
+
+/* Pre-allocate every workspace buffer for scenes of this description, these
+ * cameras and configuration, with room for max_keys tile keys (0 = estimate:
+ * grow on demand).  After a successful reserve no render call on the same
+ * shapes allocates device memory; a forward that would exceed max_keys returns
+ * SNP_ERR_CAPACITY instead of growing (required before stream capture). */
+snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_camera *cams, int32_t n_cams,
+                       const snp_config *cfg, int64_t max_keys);
+
+/* Forward render of n_cams views (Sec. 3.2, Eq. 4-9).
+ *   cams      host array of n_cams cameras
+ *   images    device float32, views concatenated, each [height][width][3] (HWC)
+ *   token     out: identifies this forward for snp_render_backward (the context
+ *             keeps the state of its latest forward only); may be NULL
+ * Stages: projection/bounding -> tile-key emission -> stable radix sort by
+ * (tile, depth) -> tile ranges -> per-tile rasterization.  Outside of a
+ * reservation the call synchronises once on `stream` to read back the key
+ * count. */
+snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
+                              const snp_camera *cams, int32_t n_cams, const snp_config *cfg, float *images,
+                              int64_t *token, void *stream);
+
+/* Backward of the forward identified by `token` (the scene pointers and values
+ * must be unchanged since that forward).
+ *   dL_dimages  device float32, same layout as the forward's images
+ *   grads       accumulated into (see snp_grad_ptrs)
+ * Replays each tile list front to back with the forward's per-pixel state
+ * (final optical depth, colour, number of entries walked); gradients flow to
+ * centres, log-scales, quaternions (through the normalisation), constant
+ * colours and every density and colour-MLP weight.  SNP_ERR_INVALID_ARG if a
+ * later forward replaced the saved state. */
+snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_desc *desc,
+                               const snp_scene_ptrs *scene, const float *dL_dimages, const snp_grad_ptrs *grads,
+                               void *stream);
+
+/* Work counters of the forward identified by token (synchronises the stream). */
+snp_status snp_get_stats(snp_context *ctx, int64_t token, snp_stats *out, void *stream);
+
+/* Copy the sorted tile keys ((global tile << 32) | float bits of the camera-frame
+ * depth of the centre) and values (view * n + primitive) of the forward `token`
+ * to HOST arrays of capacity cap; *k_out receives K.  Synchronous.  Used to check
+ * the ordering bit for bit.  Global tile ids number the tiles of view 0 row-major,
+ * then view 1, and so on. */
+snp_status snp_debug_keys(snp_context *ctx, int64_t token, uint64_t *keys_host, uint32_t *vals_host, int64_t cap,
+                          int64_t *k_out, void *stream);
+
+/* Device time per stage (milliseconds, summed) and number of timed calls per
+ * stage, over every call made with SNP_FLAG_STAGE_TIMING since the last reset.
+ * Synchronises with the last recorded event.  reset != 0 clears the sums after
+ * reading.  ms and calls may be NULL; otherwise they hold SNP_N_STAGES entries. */
+snp_status snp_stage_times(snp_context *ctx, double *ms, int64_t *calls, int32_t reset);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts), for accounting of work per step. */
+int64_t snp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNP_H */

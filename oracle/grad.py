@@ -106,12 +106,15 @@ def render(params: Dict[str, torch.Tensor], scene, cam, pix: np.ndarray, pix_lis
     ah = torch.where(hit, ah, torch.zeros_like(ah))
     ap = torch.relu(ah)
 
-    # colour per pair
+    # colour per pair (evaluated only where it is blended: alpha_hat > 0)
     if scene.color == "mlp":
-        z0 = torch.cat([d, params["feat"][pi]], dim=-1)
-        z1 = torch.relu(torch.einsum("qjk,qk->qj", params["Wc1"][pi], z0) + params["bc1"][pi])
-        z2 = torch.relu(torch.einsum("qjk,qk->qj", params["Wc2"][pi], z1) + params["bc2"][pi])
-        col = torch.sigmoid(torch.einsum("qjk,qk->qj", params["Wc3"][pi], z2) + params["bc3"][pi])
+        sel = torch.nonzero((ap > 0).detach()).squeeze(1)
+        ps_ = pi[sel]
+        z0 = torch.cat([d[sel], params["feat"][ps_]], dim=-1)
+        z1 = torch.relu(torch.einsum("qjk,qk->qj", params["Wc1"][ps_], z0) + params["bc1"][ps_])
+        z2 = torch.relu(torch.einsum("qjk,qk->qj", params["Wc2"][ps_], z1) + params["bc2"][ps_])
+        c_sel = torch.sigmoid(torch.einsum("qjk,qk->qj", params["Wc3"][ps_], z2) + params["bc3"][ps_])
+        col = torch.zeros(len(pi), 3, dtype=F64).index_put((sel,), c_sel)
     else:
         col = params["rgb"][pi]
 
@@ -187,7 +190,8 @@ def grads(scene, cam, pix, pix_list, list_off, list_prim, dL_dC: np.ndarray, t_m
     params = scene_tensors(scene, True)
     rgb = render(params, scene, cam, pix, pix_list, list_off, list_prim, t_min, bg)
     L = (rgb * torch.tensor(np.asarray(dL_dC, np.float64), dtype=F64)).sum()
-    L.backward()
+    if L.requires_grad:
+        L.backward()
     out = {}
     for k, t in params.items():
         out[k] = np.zeros(t.shape) if t.grad is None else t.grad.numpy().copy()

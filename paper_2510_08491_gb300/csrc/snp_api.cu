@@ -1,0 +1,605 @@
+// snp_api.cu -- the C ABI declared in include/snp.h: context, workspace,
+// forward/backward orchestration on one stream.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "snp.h"
+#include "snp_common.cuh"
+#include "snp_internal.h"
+
+using namespace snp;
+
+std::atomic<long long> snp::g_launches{0};
+
+namespace {
+
+// CUDA events around stages; elapsed times are collected lazily.
+struct StageTimer {
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Pending> pending;
+    double ms[SNP_N_STAGES] = {};
+    int64_t calls[SNP_N_STAGES] = {};
+    cudaEvent_t open_ev = nullptr;
+    int open_stage = -1;
+
+    cudaEvent_t get()
+    {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(int stage, cudaStream_t st)
+    {
+        open_ev = get();
+        open_stage = stage;
+        cudaEventRecord(open_ev, st);
+    }
+    void end(cudaStream_t st)
+    {
+        if (open_stage < 0) return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, st);
+        pending.push_back({open_stage, open_ev, b});
+        open_stage = -1;
+        if (pending.size() > 4096) collect();
+    }
+    void collect()
+    {
+        if (pending.empty()) return;
+        cudaEventSynchronize(pending.back().b);
+        for (auto &p : pending) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+                ms[p.stage] += t;
+                calls[p.stage] += 1;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void destroy()
+    {
+        collect();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+int round8(int x) { return (x + 7) & ~7; }
+
+void layout_of(const snp_scene_desc &d, snp_net_layout &L)
+{
+    int off = 0;
+    const int ns = d.n_sigma;
+    for (int k = 0; k < 11; ++k) L.off[k] = -1;
+    L.off[0] = off; off += round8(3 * ns);
+    L.off[1] = off; off += round8(ns);
+    L.off[2] = off; off += round8(ns);
+    L.off[3] = off; off += 8;
+    if (d.color_mode == SNP_COLOR_MLP) {
+        const int nc = d.n_c;
+        L.off[4] = off; off += round8(kFeat);
+        L.off[5] = off; off += round8(nc * (3 + kFeat));
+        L.off[6] = off; off += round8(nc);
+        L.off[7] = off; off += round8(nc * nc);
+        L.off[8] = off; off += round8(nc);
+        L.off[9] = off; off += round8(3 * nc);
+        L.off[10] = off; off += 8;
+    }
+    L.stride = off;
+}
+
+int tile_bits(int64_t tiles)
+{
+    int b = 1;
+    while (((int64_t)1 << b) < tiles) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct snp_context {
+    int device = 0;
+    std::mutex mu;
+    char err[512] = {0};
+    bool reserved = false;
+    // device workspace
+    Buf views, rec, trect, counts, offsets, scan_tmp, keys, vals, keys_alt, vals_alt, hist, hist_scan, ranges,
+        px_state, px_nwalk, stats, small, g_view, g_h0;
+    // pinned host staging
+    View *h_views = nullptr;
+    uint32_t *h_small = nullptr;
+    cudaEvent_t ev_views = nullptr;
+    // state of the latest forward
+    int64_t token = 0;
+    int64_t K = 0, key_cap = 0;
+    bool keys_in_alt = false;
+    int n_views = 0;
+    int64_t n = 0, n_tiles = 0, n_pixels = 0;
+    snp_scene_desc desc{};
+    snp_config cfg{};
+    int ts = 16, chunk = 0;
+    StageTimer timer;
+    bool timing = false;
+};
+
+#define STAGE_BEGIN(k) \
+    if (ctx->timing) ctx->timer.begin((k), st)
+#define STAGE_END() \
+    if (ctx->timing) ctx->timer.end(st)
+
+static snp_status fail(snp_context *c, snp_status s, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return fail(ctx, SNP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static snp_status ensure(snp_context *ctx, Buf &b, size_t bytes, const char *name)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return SNP_OK;
+    if (ctx->reserved)
+        return fail(ctx, SNP_ERR_CAPACITY, "workspace '%s' needs %zu bytes, reserved %zu", name, bytes, b.bytes);
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) return fail(ctx, SNP_ERR_CUDA, "cudaMalloc(%s, %zu): %s", name, want, cudaGetErrorString(e));
+    b.bytes = want;
+    return SNP_OK;
+}
+
+#define ENS(buf, bytes)                                            \
+    do {                                                           \
+        snp_status s_ = ensure(ctx, ctx->buf, (bytes), #buf);      \
+        if (s_ != SNP_OK) return s_;                               \
+    } while (0)
+
+static snp_status check_desc(snp_context *ctx, const snp_scene_desc *d)
+{
+    if (!d) return fail(ctx, SNP_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n < 0 || d->n > (int64_t)1 << 28) return fail(ctx, SNP_ERR_INVALID_ARG, "n out of range: %lld", (long long)d->n);
+    if (d->n_sigma < 1 || d->n_sigma > 64) return fail(ctx, SNP_ERR_INVALID_ARG, "n_sigma out of range: %d", d->n_sigma);
+    if (d->color_mode != SNP_COLOR_CONST && d->color_mode != SNP_COLOR_MLP)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "bad color_mode %d", d->color_mode);
+    if (d->color_mode == SNP_COLOR_MLP && d->n_c != 32 && d->n_c != 64)
+        return fail(ctx, SNP_ERR_UNSUPPORTED, "n_c must be 32 or 64, got %d", d->n_c);
+    if (d->weight_dtype != SNP_F32 && d->weight_dtype != SNP_BF16)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "bad weight_dtype %d", d->weight_dtype);
+    return SNP_OK;
+}
+
+static snp_status check_cams(snp_context *ctx, const snp_camera *cams, int n_cams)
+{
+    if (!cams || n_cams < 1 || n_cams > kMaxViews)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "need 1..%d cameras, got %d", kMaxViews, n_cams);
+    for (int v = 0; v < n_cams; ++v) {
+        const snp_camera &c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768)
+            return fail(ctx, SNP_ERR_INVALID_ARG, "camera %d: bad size %dx%d", v, c.width, c.height);
+        if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !(c.z_near > 0.0f))
+            return fail(ctx, SNP_ERR_INVALID_ARG, "camera %d: fx, fy, z_near must be > 0", v);
+    }
+    return SNP_OK;
+}
+
+// Fill the pinned view table for these cameras; returns tiles and pixels.
+static snp_status build_views(snp_context *ctx, const snp_camera *cams, int n_cams, int ts, int64_t *tiles,
+                              int64_t *pixels)
+{
+    if (ctx->ev_views) CK(cudaEventSynchronize(ctx->ev_views));
+    int64_t t = 0, p = 0;
+    for (int v = 0; v < n_cams; ++v) {
+        View &V = ctx->h_views[v];
+        const snp_camera &c = cams[v];
+        memcpy(V.R, c.R_wc, sizeof(V.R));
+        memcpy(V.eye, c.eye, sizeof(V.eye));
+        V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy; V.z_near = c.z_near;
+        V.width = c.width; V.height = c.height;
+        V.tiles_x = (c.width + ts - 1) / ts;
+        V.tiles_y = (c.height + ts - 1) / ts;
+        V.tile_off = (int32_t)t;
+        V.pad_ = 0;
+        V.pix_off = p;
+        t += (int64_t)V.tiles_x * V.tiles_y;
+        p += (int64_t)c.width * c.height;
+    }
+    if (t >= ((int64_t)1 << 31)) return fail(ctx, SNP_ERR_INVALID_ARG, "too many tiles");
+    *tiles = t;
+    *pixels = p;
+    return SNP_OK;
+}
+
+static void fill_args(RasterArgs &a, const snp_context *ctx, const snp_scene_desc *d, const snp_scene_ptrs *sc,
+                      const uint32_t *sorted_vals)
+{
+    memset(&a, 0, sizeof(a));
+    snp_net_layout L;
+    layout_of(*d, L);
+    a.rec = (const float *)ctx->rec.p;
+    a.vals = sorted_vals;
+    a.ranges = (const uint2 *)ctx->ranges.p;
+    a.net = sc->net;
+    a.views = (const View *)ctx->views.p;
+    a.n_views = ctx->n_views;
+    a.n_sigma = d->n_sigma;
+    a.n = d->n;
+    a.n_tiles = ctx->n_tiles;
+    a.off_W1 = L.off[0]; a.off_b1 = L.off[1]; a.off_w2 = L.off[2]; a.off_b2 = L.off[3];
+    a.off_feat = L.off[4]; a.off_Wc1 = L.off[5]; a.off_bc1 = L.off[6]; a.off_Wc2 = L.off[7];
+    a.off_bc2 = L.off[8]; a.off_Wc3 = L.off[9]; a.off_bc3 = L.off[10];
+    a.stride = L.stride;
+    a.omega0 = d->omega0;
+    a.t_min = ctx->cfg.t_min;
+    for (int k = 0; k < 3; ++k) a.bg[k] = ctx->cfg.bg[k];
+    a.chunk = ctx->chunk;
+}
+
+extern "C" {
+
+snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out)
+{
+    if (!desc || !out) return SNP_ERR_INVALID_ARG;
+    if (check_desc(nullptr, desc) != SNP_OK) return SNP_ERR_INVALID_ARG;
+    layout_of(*desc, *out);
+    return SNP_OK;
+}
+
+snp_status snp_create(int32_t device, snp_context **out)
+{
+    if (!out) return SNP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SNP_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return SNP_ERR_CUDA;
+    snp_context *ctx = new snp_context();
+    ctx->device = device;
+    if (cudaMallocHost((void **)&ctx->h_views, sizeof(View) * kMaxViews) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->h_small, 64) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_views, cudaEventDisableTiming) != cudaSuccess) {
+        snp_destroy(ctx);
+        return SNP_ERR_CUDA;
+    }
+    *out = ctx;
+    return SNP_OK;
+}
+
+void snp_destroy(snp_context *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    Buf *bufs[] = {&ctx->views, &ctx->rec, &ctx->trect, &ctx->counts, &ctx->offsets, &ctx->scan_tmp, &ctx->keys,
+                   &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
+                   &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->h_views) cudaFreeHost(ctx->h_views);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    if (ctx->ev_views) cudaEventDestroy(ctx->ev_views);
+    ctx->timer.destroy();
+    delete ctx;
+}
+
+const char *snp_last_error(const snp_context *ctx) { return ctx ? ctx->err : "null context"; }
+
+static snp_status ensure_keys(snp_context *ctx, int64_t K)
+{
+    ENS(keys, (size_t)K * 8);
+    ENS(keys_alt, (size_t)K * 8);
+    ENS(vals, (size_t)K * 4);
+    ENS(vals_alt, (size_t)K * 4);
+    const int64_t hw = sort_hist_words(K);
+    ENS(hist, (size_t)hw * 4);
+    ENS(hist_scan, (size_t)hw * 4);
+    return SNP_OK;
+}
+
+static snp_status ensure_frame(snp_context *ctx, int64_t n, int n_views, int64_t tiles, int64_t pixels,
+                               const snp_scene_desc *d)
+{
+    const int64_t vn = n * n_views;
+    ENS(views, sizeof(View) * kMaxViews);
+    ENS(rec, (size_t)vn * kRecFloats * 4);
+    ENS(trect, (size_t)vn * 16);
+    ENS(counts, (size_t)vn * 4);
+    ENS(offsets, (size_t)vn * 4);
+    ENS(ranges, (size_t)tiles * 8);
+    ENS(px_state, (size_t)pixels * 16);
+    ENS(px_nwalk, (size_t)pixels * 4);
+    ENS(stats, 64);
+    ENS(small, 64);
+    (void)d;
+    return SNP_OK;
+}
+
+static snp_status ensure_scan_tmp(snp_context *ctx, int64_t vn, int64_t key_bound)
+{
+    int64_t w = scan_temp_words(vn);
+    const int64_t hw = scan_temp_words(sort_hist_words(key_bound));
+    if (hw > w) w = hw;
+    ENS(scan_tmp, (size_t)(w + 16) * 4);
+    return SNP_OK;
+}
+
+snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_camera *cams, int32_t n_cams,
+                       const snp_config *cfg, int64_t max_keys)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    if ((s = check_cams(ctx, cams, n_cams)) != SNP_OK) return s;
+    const int ts = cfg && cfg->tile_size ? cfg->tile_size : 16;
+    int64_t tiles, pixels;
+    ctx->reserved = false;
+    if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) return s;
+    if (max_keys <= 0) max_keys = 4 * desc->n * n_cams + 1024;
+    if ((s = ensure_frame(ctx, desc->n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
+    if ((s = ensure_keys(ctx, max_keys)) != SNP_OK) return s;
+    if ((s = ensure_scan_tmp(ctx, desc->n * n_cams, max_keys)) != SNP_OK) return s;
+    {
+        const int nc = desc->color_mode == SNP_COLOR_MLP ? desc->n_c : 1;
+        ENS(g_view, (size_t)desc->n * n_cams * 16 * 4);
+        ENS(g_h0, (size_t)desc->n * nc * 4);
+    }
+    ctx->key_cap = max_keys;
+    ctx->reserved = true;
+    return SNP_OK;
+}
+
+snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
+                              const snp_camera *cams, int32_t n_cams, const snp_config *cfg, float *images,
+                              int64_t *token, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    if ((s = check_cams(ctx, cams, n_cams)) != SNP_OK) return s;
+    if (!scene || !images || (desc->n > 0 && (!scene->geom || !scene->net)))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "null scene or image pointer");
+    if (((uintptr_t)scene->geom & 15) || ((uintptr_t)scene->net & 15))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "scene arrays must be 16-byte aligned");
+    snp_config c{};
+    c.tile_size = 16;
+    c.t_min = 1e-4f;
+    if (cfg) c = *cfg;
+    if (c.tile_size == 0) c.tile_size = 16;
+    if (c.tile_size != 16) return fail(ctx, SNP_ERR_UNSUPPORTED, "tile_size %d not built", c.tile_size);
+    if (c.integral_form != SNP_FORM_STABLE && c.integral_form != SNP_FORM_NAIVE)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "bad integral_form %d", c.integral_form);
+    if (!(c.t_min >= 0.0f) || !(c.t_min < 1.0f)) return fail(ctx, SNP_ERR_INVALID_ARG, "t_min must be in [0, 1)");
+    const int chunk = c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false);
+    if (chunk > 256 || raster_fwd_smem(desc->color_mode, desc->n_c, desc->n_sigma, chunk) > 200 * 1024)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "chunk %d too large", chunk);
+
+    const int ts = c.tile_size;
+    int64_t tiles, pixels;
+    if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) return s;
+    const int64_t n = desc->n, vn = n * n_cams;
+    if ((s = ensure_frame(ctx, n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
+    ctx->token++;  // invalidates the previous forward's state from here on
+    ctx->n_views = n_cams;
+    ctx->n = n;
+    ctx->n_tiles = tiles;
+    ctx->n_pixels = pixels;
+    ctx->desc = *desc;
+    ctx->cfg = c;
+    ctx->ts = ts;
+    ctx->chunk = chunk;
+
+    CK(cudaMemcpyAsync(ctx->views.p, ctx->h_views, sizeof(View) * n_cams, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->ev_views, st));
+    uint32_t *d_total = (uint32_t *)ctx->small.p;
+    int32_t *d_flags = (int32_t *)((char *)ctx->small.p + 16);
+
+    int64_t key_bound;
+    if (!ctx->reserved) {
+        if ((s = ensure_scan_tmp(ctx, vn, 0)) != SNP_OK) return s;
+    }
+    ctx->timing = (c.flags & SNP_FLAG_STAGE_TIMING) != 0;
+    STAGE_BEGIN(SNP_STAGE_PROJECT);
+    launch_project((const float *)scene->geom, n, (const View *)ctx->views.p, n_cams, ts, (float *)ctx->rec.p,
+                   (int4 *)ctx->trect.p, (uint32_t *)ctx->counts.p, st);
+    STAGE_END();
+    STAGE_BEGIN(SNP_STAGE_SCAN);
+    scan_u32((const uint32_t *)ctx->counts.p, (uint32_t *)ctx->offsets.p, vn, d_total, (uint32_t *)ctx->scan_tmp.p,
+             st);
+    STAGE_END();
+    if (!ctx->reserved) {
+        CK(cudaMemcpyAsync(ctx->h_small, d_total, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        key_bound = ctx->h_small[0];
+        if ((s = ensure_keys(ctx, key_bound)) != SNP_OK) return s;
+        if ((s = ensure_scan_tmp(ctx, vn, key_bound)) != SNP_OK) return s;
+        ctx->K = key_bound;
+    } else {
+        key_bound = ctx->key_cap;
+        ctx->K = -1;  // known on the device only
+    }
+    CK(cudaMemsetAsync(d_flags, 0, 4, st));
+    STAGE_BEGIN(SNP_STAGE_EMIT);
+    launch_emit((const int4 *)ctx->trect.p, (const uint32_t *)ctx->counts.p, (const uint32_t *)ctx->offsets.p,
+                (const float *)ctx->rec.p, n, (const View *)ctx->views.p, n_cams, (uint64_t *)ctx->keys.p,
+                (uint32_t *)ctx->vals.p, key_bound, d_flags, st);
+    STAGE_END();
+    const int nbits = 32 + tile_bits(tiles);
+    STAGE_BEGIN(SNP_STAGE_SORT);
+    ctx->keys_in_alt = radix_sort((uint64_t *)ctx->keys.p, (uint32_t *)ctx->vals.p, (uint64_t *)ctx->keys_alt.p,
+                                  (uint32_t *)ctx->vals_alt.p, d_total, key_bound, nbits, (uint32_t *)ctx->hist.p,
+                                  (uint32_t *)ctx->hist_scan.p, (uint32_t *)ctx->scan_tmp.p, st);
+    STAGE_END();
+    const uint64_t *skeys = (const uint64_t *)(ctx->keys_in_alt ? ctx->keys_alt.p : ctx->keys.p);
+    const uint32_t *svals = (const uint32_t *)(ctx->keys_in_alt ? ctx->vals_alt.p : ctx->vals.p);
+    STAGE_BEGIN(SNP_STAGE_RANGES);
+    CK(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)tiles * 8, st));
+    launch_tile_ranges(skeys, d_total, key_bound, (uint2 *)ctx->ranges.p, st);
+    STAGE_END();
+    CK(cudaMemsetAsync(ctx->stats.p, 0, 24, st));
+
+    RasterArgs a;
+    fill_args(a, ctx, desc, scene, svals);
+    a.image = images;
+    a.px_state = (float4 *)ctx->px_state.p;
+    a.px_nwalk = (uint32_t *)ctx->px_nwalk.p;
+    a.stats = (unsigned long long *)ctx->stats.p;
+    STAGE_BEGIN(SNP_STAGE_RASTER_FWD);
+    s = launch_raster_fwd(a, desc->color_mode, desc->n_c, c.integral_form, desc->weight_dtype == SNP_BF16, ts, st);
+    STAGE_END();
+    if (s != SNP_OK) return fail(ctx, s, "raster forward launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    CK(cudaGetLastError());
+    if (token) *token = ctx->token;
+    return SNP_OK;
+}
+
+snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_desc *desc,
+                               const snp_scene_ptrs *scene, const float *dL_dimages, const snp_grad_ptrs *grads,
+                               void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    if (token != ctx->token || token == 0)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "stale token %lld (latest forward is %lld)", (long long)token,
+                    (long long)ctx->token);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    if (desc->n != ctx->desc.n || desc->n_sigma != ctx->desc.n_sigma || desc->color_mode != ctx->desc.color_mode ||
+        desc->n_c != ctx->desc.n_c || desc->weight_dtype != ctx->desc.weight_dtype)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "scene description differs from the forward's");
+    if (!scene || !dL_dimages || !grads) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    const int64_t n = desc->n, vn = n * ctx->n_views;
+    const int nc = desc->color_mode == SNP_COLOR_MLP ? desc->n_c : 1;
+    ENS(g_view, (size_t)vn * 16 * 4);
+    ENS(g_h0, (size_t)n * nc * 4);
+    CK(cudaMemsetAsync(ctx->g_view.p, 0, (size_t)vn * 16 * 4, st));
+    CK(cudaMemsetAsync(ctx->g_h0.p, 0, (size_t)n * nc * 4, st));
+    const uint32_t *svals = (const uint32_t *)(ctx->keys_in_alt ? ctx->vals_alt.p : ctx->vals.p);
+    RasterArgs a;
+    fill_args(a, ctx, desc, scene, svals);
+    a.px_state = (float4 *)ctx->px_state.p;
+    a.px_nwalk = (uint32_t *)ctx->px_nwalk.p;
+    a.dL_dimage = dL_dimages;
+    a.g_net = grads->net;
+    a.g_view = (float *)ctx->g_view.p;
+    a.g_h0 = (float *)ctx->g_h0.p;
+    a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true);
+    if (ctx->cfg.chunk > 0 && ctx->cfg.chunk < a.chunk) a.chunk = ctx->cfg.chunk;
+    STAGE_BEGIN(SNP_STAGE_RASTER_BWD);
+    s = launch_raster_bwd(a, desc->color_mode, desc->n_c, ctx->cfg.integral_form, desc->weight_dtype == SNP_BF16,
+                          ctx->ts, st);
+    STAGE_END();
+    if (s != SNP_OK) return fail(ctx, s, "raster backward launch failed");
+    STAGE_BEGIN(SNP_STAGE_POST_BWD);
+    if (grads->geom)
+        launch_project_bwd((const float *)scene->geom, n, (const View *)ctx->views.p, ctx->n_views,
+                           (const float *)ctx->g_view.p, grads->geom, st);
+    if (grads->net && desc->color_mode == SNP_COLOR_MLP)
+        launch_color_post(scene->net, desc->weight_dtype == SNP_BF16, n, desc->n_c, a.off_feat, a.off_Wc1,
+                          a.off_bc1, a.stride, (const float *)ctx->g_h0.p, grads->net, st);
+    STAGE_END();
+    CK(cudaGetLastError());
+    return SNP_OK;
+}
+
+snp_status snp_stage_times(snp_context *ctx, double *ms, int64_t *calls, int32_t reset)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->device));
+    ctx->timer.collect();
+    for (int k = 0; k < SNP_N_STAGES; ++k) {
+        if (ms) ms[k] = ctx->timer.ms[k];
+        if (calls) calls[k] = ctx->timer.calls[k];
+        if (reset) {
+            ctx->timer.ms[k] = 0.0;
+            ctx->timer.calls[k] = 0;
+        }
+    }
+    return SNP_OK;
+}
+
+int64_t snp_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+snp_status snp_get_stats(snp_context *ctx, int64_t token, snp_stats *out, void *stream)
+{
+    if (!ctx || !out) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (token != ctx->token || token == 0) return fail(ctx, SNP_ERR_INVALID_ARG, "stale token");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long h[3];
+    CK(cudaMemcpyAsync(h, ctx->stats.p, 24, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_small, ctx->small.p, 32, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->n_keys = ctx->h_small[0];
+    out->n_tiles = ctx->n_tiles;
+    out->n_pixels = ctx->n_pixels;
+    out->n_candidates = (int64_t)h[0];
+    out->n_hits = (int64_t)h[1];
+    out->n_composited = (int64_t)h[2];
+    if (ctx->h_small[4] != 0) return fail(ctx, SNP_ERR_CAPACITY, "tile keys exceeded the reserved capacity");
+    return SNP_OK;
+}
+
+snp_status snp_debug_keys(snp_context *ctx, int64_t token, uint64_t *keys_host, uint32_t *vals_host, int64_t cap,
+                          int64_t *k_out, void *stream)
+{
+    if (!ctx || !k_out) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (token != ctx->token || token == 0) return fail(ctx, SNP_ERR_INVALID_ARG, "stale token");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->h_small, ctx->small.p, 32, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int64_t K = ctx->h_small[0];
+    *k_out = K;
+    if (ctx->h_small[4] != 0) return fail(ctx, SNP_ERR_CAPACITY, "tile keys exceeded the reserved capacity");
+    if (K > cap) return fail(ctx, SNP_ERR_INVALID_ARG, "host capacity %lld < K %lld", (long long)cap, (long long)K);
+    if (K > 0) {
+        const void *kp = ctx->keys_in_alt ? ctx->keys_alt.p : ctx->keys.p;
+        const void *vp = ctx->keys_in_alt ? ctx->vals_alt.p : ctx->vals.p;
+        if (keys_host) CK(cudaMemcpyAsync(keys_host, kp, (size_t)K * 8, cudaMemcpyDeviceToHost, st));
+        if (vals_host) CK(cudaMemcpyAsync(vals_host, vp, (size_t)K * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return SNP_OK;
+}
+
+}  // extern "C"

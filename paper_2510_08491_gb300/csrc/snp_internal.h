@@ -1,0 +1,78 @@
+// snp_internal.h -- host-side declarations shared by the libsnp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "snp.h"
+
+namespace snp {
+
+// Kernels launched by this library in this process (snp_kernel_launches).
+extern std::atomic<long long> g_launches;
+inline void note_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+struct View;
+struct NetLayout;
+
+// snp_prep.cu
+void launch_project(const float *geom, int64_t n, const View *views, int n_views, int ts, float *rec, int4 *trect,
+                    uint32_t *counts, cudaStream_t st);
+int64_t scan_temp_words(int64_t n);
+void scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total, uint32_t *tmp, cudaStream_t st);
+void launch_emit(const int4 *trect, const uint32_t *counts, const uint32_t *offsets, const float *rec, int64_t n,
+                 const View *views, int n_views, uint64_t *keys, uint32_t *vals, int64_t cap, int32_t *flags,
+                 cudaStream_t st);
+int64_t sort_hist_words(int64_t n_bound);
+bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_n,
+                int64_t n_bound, int nbits, uint32_t *hist, uint32_t *hist_scan, uint32_t *scan_tmp,
+                cudaStream_t st);
+void launch_tile_ranges(const uint64_t *keys, const uint32_t *d_n, int64_t n_bound, uint2 *ranges, cudaStream_t st);
+
+// Arguments of the per-tile rasterizer (forward and backward).
+struct RasterArgs {
+    const float *rec;         // [V*n][kRecFloats]
+    const uint32_t *vals;     // sorted values (view * n + primitive)
+    const uint2 *ranges;      // [n_tiles]
+    const void *net;          // [n][stride] weights
+    const View *views;
+    int32_t n_views;
+    int32_t n_sigma;
+    int64_t n;
+    int64_t n_tiles;
+    const int32_t *lay;       // unused on device (layout passed by value below)
+    int32_t off_W1, off_b1, off_w2, off_b2, off_feat, off_Wc1, off_bc1, off_Wc2, off_bc2, off_Wc3, off_bc3;
+    int32_t stride;
+    float omega0;
+    float t_min;
+    float bg[3];
+    int32_t chunk;
+    // forward outputs / saved state
+    float *image;             // concatenated HWC views
+    float4 *px_state;         // [P]: composited colour (no background) xyz, optical depth w
+    uint32_t *px_nwalk;       // [P]: list entries walked up to the last composited one
+    unsigned long long *stats;  // [3]: candidates, hits, composited
+    // backward inputs / outputs
+    const float *dL_dimage;   // concatenated HWC views
+    float *g_net;             // [n][stride] float32
+    float *g_view;            // [V*n][16] per (view, primitive) geometry intermediates
+    float *g_h0;              // [n][n_c] gradient of the folded first-layer bias
+};
+
+// snp_raster_fwd.cu / snp_raster_bwd.cu
+snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
+                             cudaStream_t st);
+snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
+                             cudaStream_t st);
+size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk);
+int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward);
+
+// snp_grad.cu
+void launch_project_bwd(const float *geom, int64_t n, const View *views, int n_views, const float *g_view,
+                        float *g_geom, cudaStream_t st);
+void launch_color_post(const void *net, int bf16, int64_t n, int n_c, int off_feat, int off_Wc1, int off_bc1,
+                       int stride, const float *g_h0, float *g_net, cudaStream_t st);
+
+}  // namespace snp

@@ -1,0 +1,444 @@
+// snp_raster_bwd.cu -- backward per-tile rasterizer.
+//
+// One CTA per 16 x 16 tile, one thread per pixel.  Each pixel replays its list
+// front to back up to the number of entries the forward walked, recomputing
+// alpha_hat, alpha and the colour of every composited entry.  With the forward's
+// final colour C (no background) and optical depth tau_f:
+//   C = sum_i c_i alpha_i T_i + T_f bg,  T_i = exp(-sum_{j<i} alpha_hat_j),
+//   dC/dc_i = alpha_i T_i,
+//   dC/dalpha_hat_i = T_{i+1} c_i - R_i - T_f bg,  R_i = sum_{j>i} c_j alpha_j T_j = C - prefix_i,
+// which needs no division by (1 - alpha).  The chain rule then runs through the
+// colour MLP, the closed-form integral (stable or literal Eq. 8) and the ray /
+// ellipsoid geometry down to the projection record.  Per-pair gradients are
+// reduced across each warp by a 32-value reduce-scatter, accumulated per list
+// entry in shared memory across the warps, and added to the caller's gradient
+// arrays with one global atomic per parameter per (tile, primitive).
+#include "snp_raster.cuh"
+
+namespace snp {
+
+constexpr int kGvFloats = 20;  // per (view, primitive) geometry gradient record
+
+// Per-entry gradient accumulator layout (floats).
+__host__ __device__ constexpr int ga_geo(int ns) { return round4(5 * ns + 1); }
+__host__ __device__ constexpr int ga_bc3(int ns) { return ga_geo(ns) + kGvFloats; }
+__host__ __device__ constexpr int ga_col(int ns) { return ga_bc3(ns) + 4; }
+// colour: C1G [nc][4] (Wc1[j][0..2], h0_j), W2G [nc][nc], W3G [nc][4] (Wc3[0..2][j], bc2_j)
+__host__ __device__ constexpr int grad_stride(int ns, int nc)
+{
+    return nc == 0 ? ga_col(ns) : ga_col(ns) + 4 * nc + nc * nc + 4 * nc;
+}
+
+template <int NC>
+__device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int64_t prim, int64_t vprim, int vg,
+                                            int tid, int nt)
+{
+    const int ns = a.n_sigma;
+    const int64_t nb = prim * a.stride;
+    for (int q = tid; q < vg; q += nt) {
+        const float val = acc[q];
+        if (val == 0.0f) continue;
+        acc[q] = 0.0f;
+        if (q < ga_geo(ns)) {
+            if (!a.g_net) continue;
+            int64_t dst;
+            if (q < 3 * ns) dst = nb + a.off_W1 + q;
+            else if (q < 4 * ns) dst = nb + a.off_b1 + (q - 3 * ns);
+            else if (q < 5 * ns) dst = nb + a.off_w2 + (q - 4 * ns);
+            else if (q == 5 * ns) dst = nb + a.off_b2;
+            else continue;
+            atomicAdd(a.g_net + dst, val);
+        } else if (q < ga_bc3(ns)) {
+            atomicAdd(a.g_view + vprim * kGvFloats + (q - ga_geo(ns)), val);
+        } else if (q < ga_col(ns)) {
+            const int r = q - ga_bc3(ns);
+            if (a.g_net && r < 3) atomicAdd(a.g_net + nb + a.off_bc3 + r, val);
+        } else if constexpr (NC > 0) {
+            int t = q - ga_col(ns);
+            if (t < 4 * NC) {
+                const int j = t >> 2, r = t & 3;
+                if (r < 3) {
+                    if (a.g_net) atomicAdd(a.g_net + nb + a.off_Wc1 + j * (3 + kFeat) + r, val);
+                } else {
+                    atomicAdd(a.g_h0 + prim * NC + j, val);
+                }
+            } else if ((t -= 4 * NC) < NC * NC) {
+                if (a.g_net) atomicAdd(a.g_net + nb + a.off_Wc2 + t, val);
+            } else {
+                t -= NC * NC;
+                const int j = t >> 2, r = t & 3;
+                if (a.g_net) {
+                    if (r < 3) atomicAdd(a.g_net + nb + a.off_Wc3 + r * NC + j, val);
+                    else atomicAdd(a.g_net + nb + a.off_bc2 + j, val);
+                }
+            }
+        }
+    }
+}
+
+template <int NC, int FORM, bool BF16>
+__global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(RasterArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    __shared__ uint32_t s_gid[kMaxChunk];
+    __shared__ int s_view;
+    __shared__ uint32_t s_maxwalk;
+
+    const int tile = blockIdx.x;
+    if (threadIdx.x == 0) {
+        s_view = find_view(a.views, a.n_views, tile);
+        s_maxwalk = 0;
+    }
+    __syncthreads();
+    const int v = s_view;
+    const View &V = a.views[v];
+    const int lt = tile - V.tile_off;
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    int lx, ly;
+    tile_pixel16(threadIdx.x, lx, ly);
+    const int px = tx * 16 + lx, py = ty * 16 + ly;
+    const bool inside = px < V.width && py < V.height;
+    const float3 d = pixel_ray(V, px, py);
+    const uint2 rg = a.ranges[tile];
+    const int ns = a.n_sigma;
+    const int es = entry_stride(ns, NC);
+    const int vg = grad_stride(ns, NC);
+    const int64_t vn = (int64_t)v * a.n;
+    const float w0 = a.omega0;
+    float *acc = sm + a.chunk * es;
+    for (int q = threadIdx.x; q < a.chunk * vg; q += blockDim.x) acc[q] = 0.0f;
+
+    const int64_t p = V.pix_off + (int64_t)py * V.width + px;
+    float3 Cf = make_float3(0.f, 0.f, 0.f), dL = make_float3(0.f, 0.f, 0.f);
+    float tau_f = 0.0f;
+    uint32_t nwalk = 0;
+    if (inside) {
+        const float4 s4 = a.px_state[p];
+        Cf = make_float3(s4.x, s4.y, s4.z);
+        tau_f = s4.w;
+        nwalk = a.px_nwalk[p];
+        dL = make_float3(a.dL_dimage[3 * p + 0], a.dL_dimage[3 * p + 1], a.dL_dimage[3 * p + 2]);
+        atomicMax(&s_maxwalk, nwalk);
+    }
+    const float bgdot = __expf(-tau_f) * (dL.x * a.bg[0] + dL.y * a.bg[1] + dL.z * a.bg[2]);
+    float tau = 0.0f;
+    float3 pref = make_float3(0.f, 0.f, 0.f);
+    const unsigned lane = lane_id();
+    __syncthreads();
+    const uint32_t maxwalk = s_maxwalk;
+
+    for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += a.chunk) {
+        const int cnt = min((int)(rg.y - c0), a.chunk);
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) s_gid[threadIdx.x] = a.vals[c0 + threadIdx.x];
+        __syncthreads();
+        stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
+        __syncthreads();
+        for (int e = 0; e < cnt; ++e) {
+            const uint32_t pos = c0 - rg.x + e;
+            const float *R = sm + e * es;
+            const float *D = R + kRecFloats;
+            const float *Cb = D + den_stride(ns);
+            float *A = acc + e * vg;
+            Hit h;
+            bool contrib = false;
+            float ah = 0.0f;
+            if (pos < nwalk && intersect(R, d, h)) {
+                ah = integral<FORM>(R, D, ns, d, h);
+                contrib = ah > 0.0f;
+            }
+            if (!__any_sync(0xffffffffu, contrib)) continue;
+
+            // ---- compositing replay
+            float3 col = make_float3(0.f, 0.f, 0.f);
+            float g_ah = 0.0f;
+            float3 g_c = make_float3(0.f, 0.f, 0.f);
+            if (contrib) {
+                if constexpr (NC == 0)
+                    col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
+                else
+                    col = mlp_color<NC>(Cb, d);
+                const float Ti = __expf(-tau);
+                const float wgt = Ti * (1.0f - __expf(-ah));
+                const float tn = tau + ah;
+                const float Tn = __expf(-tn);
+                pref.x = fmaf(wgt, col.x, pref.x);
+                pref.y = fmaf(wgt, col.y, pref.y);
+                pref.z = fmaf(wgt, col.z, pref.z);
+                g_ah = dL.x * (Tn * col.x - (Cf.x - pref.x)) + dL.y * (Tn * col.y - (Cf.y - pref.y)) +
+                       dL.z * (Tn * col.z - (Cf.z - pref.z)) - bgdot;
+                g_c = make_float3(dL.x * wgt, dL.y * wgt, dL.z * wgt);
+                tau = tn;
+            } else {
+                // benign geometry for lanes that only take part in the warp reductions
+                h.tm = 0.0f; h.half = 1.0f; h.dp = make_float3(1.f, 0.f, 0.f); h.p = make_float3(0.f, 0.f, 0.f);
+                h.A = 1.0f; h.B = 0.0f; h.iA = 1.0f; h.h2 = 1.0f;
+            }
+
+            // ---- density (closed-form integral) and geometry
+            const float inv_m = R[kRecInvM];
+            const float3 ocm = make_float3(R[kRecOcm + 0], R[kRecOcm + 1], R[kRecOcm + 2]);
+            const float4 *W = reinterpret_cast<const float4 *>(D);
+            const float *w2 = D + 4 * ns;
+            const float b2 = w2[ns];
+            float3 g_u = make_float3(0.f, 0.f, 0.f), g_ocm = make_float3(0.f, 0.f, 0.f);
+            float g_hm = 0.0f, S = b2, g_invm = 0.0f, g_tm = 0.0f, g_half = 0.0f, g_b2;
+            const float tmm = h.tm * inv_m, hm = h.half * inv_m, dt = 2.0f * h.half;
+            const float tin = h.tm - h.half, tout = h.tm + h.half;
+            const float3 u = make_float3(fmaf(tmm, d.x, ocm.x), fmaf(tmm, d.y, ocm.y), fmaf(tmm, d.z, ocm.z));
+            const float gS = g_ah * dt;
+            float g_tout = 0.0f, g_tin = 0.0f;
+            if constexpr (FORM == 0) {
+                g_b2 = gS;
+            } else {
+                g_b2 = g_ah * (tout - tin);
+                g_tout = g_ah * b2;
+                g_tin = -g_ah * b2;
+            }
+            for (int k0 = 0; k0 < ns; k0 += 6) {
+                float vv[32];
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) {
+                    const int k = k0 + kk;
+                    float gw[3] = {0.f, 0.f, 0.f}, gb1 = 0.0f, gw2 = 0.0f;
+                    if (k < ns) {
+                        const float4 w = W[k];
+                        const float wk = w2[k];
+                        const float g = fmaf(w.x, d.x, fmaf(w.y, d.y, w.z * d.z));
+                        if constexpr (FORM == 0) {
+                            const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
+                            const float th = g * hm;
+                            float sp, cp, st, ct;
+                            __sincosf(ph, &sp, &cp);
+                            __sincosf(th, &st, &ct);
+                            const float t2 = th * th;
+                            const float sc = fabsf(th) < 0.05f ? fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f)
+                                                               : __fdividef(st, th);
+                            const float scp = sincf_deriv(th, st, ct);
+                            S = fmaf(wk * cp, sc, S);
+                            const float gphi = -gS * wk * sp * sc;
+                            const float gth = gS * wk * cp * scp;
+                            gw2 = gS * cp * sc;
+                            gw[0] = w0 * fmaf(gphi, u.x, gth * hm * d.x);
+                            gw[1] = w0 * fmaf(gphi, u.y, gth * hm * d.y);
+                            gw[2] = w0 * fmaf(gphi, u.z, gth * hm * d.z);
+                            gb1 = w0 * gphi;
+                            g_u.x = fmaf(gphi, w.x, g_u.x);
+                            g_u.y = fmaf(gphi, w.y, g_u.y);
+                            g_u.z = fmaf(gphi, w.z, g_u.z);
+                            g_hm = fmaf(gth, g, g_hm);
+                        } else {
+                            const float ak = g * inv_m;
+                            const float psi = fmaf(w.x, ocm.x, fmaf(w.y, ocm.y, fmaf(w.z, ocm.z, w.w)));
+                            float s1, c1, s0, c0v;
+                            __sincosf(fmaf(ak, tout, psi), &s1, &c1);
+                            __sincosf(fmaf(ak, tin, psi), &s0, &c0v);
+                            const float ia = __fdividef(1.0f, ak);
+                            gw2 = g_ah * (s1 - s0) * ia;
+                            const float gpsi = g_ah * wk * (c1 - c0v) * ia;
+                            const float ga = g_ah * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
+                            gw[0] = w0 * fmaf(gpsi, ocm.x, ga * inv_m * d.x);
+                            gw[1] = w0 * fmaf(gpsi, ocm.y, ga * inv_m * d.y);
+                            gw[2] = w0 * fmaf(gpsi, ocm.z, ga * inv_m * d.z);
+                            gb1 = w0 * gpsi;
+                            g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
+                            g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
+                            g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
+                            g_invm = fmaf(ga, g, g_invm);
+                            g_tout = fmaf(g_ah * wk, c1, g_tout);
+                            g_tin = fmaf(-g_ah * wk, c0v, g_tin);
+                        }
+                    }
+                    vv[5 * kk + 0] = gw[0];
+                    vv[5 * kk + 1] = gw[1];
+                    vv[5 * kk + 2] = gw[2];
+                    vv[5 * kk + 3] = gb1;
+                    vv[5 * kk + 4] = gw2;
+                }
+                vv[30] = 0.0f;
+                vv[31] = 0.0f;
+                const float r = warp_reduce_scatter32(vv);
+                const int kk = lane / 5, c = lane - 5 * kk, k = k0 + kk;
+                if (lane < 30 && k < ns && r != 0.0f) {
+                    const int dst = c < 3 ? 3 * k + c : (c == 3 ? 3 * ns + k : 4 * ns + k);
+                    atomicAdd(A + dst, r);
+                }
+            }
+            if constexpr (FORM == 0) {
+                const float gud = g_u.x * d.x + g_u.y * d.y + g_u.z * d.z;
+                g_half = 2.0f * g_ah * S + g_hm * inv_m;
+                g_invm = g_hm * h.half + gud * h.tm;
+                g_tm = gud * inv_m;
+                g_ocm = g_u;
+            } else {
+                g_tm = g_tout + g_tin;
+                g_half = g_tout - g_tin;
+            }
+            // half = sqrt(h2 / A): tm, half -> closest point, A, B -> Minv d, op
+            const float gx = __fdividef(g_half, 2.0f * h.half);
+            const float g_h2 = gx * h.iA;
+            float g_iA = gx * h.h2;
+            const float3 g_p = make_float3(-2.0f * g_h2 * h.p.x, -2.0f * g_h2 * h.p.y, -2.0f * g_h2 * h.p.z);
+            float3 g_op = g_p;
+            g_tm += g_p.x * h.dp.x + g_p.y * h.dp.y + g_p.z * h.dp.z;
+            float3 g_dp = make_float3(h.tm * g_p.x, h.tm * g_p.y, h.tm * g_p.z);
+            const float g_B = -g_tm * h.iA;
+            g_iA -= g_tm * h.B;
+            const float g_A = -g_iA * h.iA * h.iA;
+            const float3 op = make_float3(R[kRecOp + 0], R[kRecOp + 1], R[kRecOp + 2]);
+            g_dp.x = fmaf(2.0f * g_A, h.dp.x, fmaf(g_B, op.x, g_dp.x));
+            g_dp.y = fmaf(2.0f * g_A, h.dp.y, fmaf(g_B, op.y, g_dp.y));
+            g_dp.z = fmaf(2.0f * g_A, h.dp.z, fmaf(g_B, op.z, g_dp.z));
+            g_op.x = fmaf(g_B, h.dp.x, g_op.x);
+            g_op.y = fmaf(g_B, h.dp.y, g_op.y);
+            g_op.z = fmaf(g_B, h.dp.z, g_op.z);
+
+            float3 g_a3 = make_float3(0.f, 0.f, 0.f);
+            if constexpr (NC > 0) {
+                g_a3 = make_float3(g_c.x * col.x * (1.0f - col.x), g_c.y * col.y * (1.0f - col.y),
+                                   g_c.z * col.z * (1.0f - col.z));
+            }
+            {
+                float vv[32];
+                vv[0] = g_dp.x * d.x; vv[1] = g_dp.x * d.y; vv[2] = g_dp.x * d.z;
+                vv[3] = g_dp.y * d.x; vv[4] = g_dp.y * d.y; vv[5] = g_dp.y * d.z;
+                vv[6] = g_dp.z * d.x; vv[7] = g_dp.z * d.y; vv[8] = g_dp.z * d.z;
+                vv[9] = g_op.x; vv[10] = g_op.y; vv[11] = g_op.z;
+                vv[12] = g_ocm.x; vv[13] = g_ocm.y; vv[14] = g_ocm.z;
+                vv[15] = g_invm;
+                vv[16] = NC == 0 ? g_c.x : 0.0f;
+                vv[17] = NC == 0 ? g_c.y : 0.0f;
+                vv[18] = NC == 0 ? g_c.z : 0.0f;
+                vv[19] = 0.0f;
+                vv[20] = g_b2;
+                vv[21] = g_a3.x; vv[22] = g_a3.y; vv[23] = g_a3.z;
+#pragma unroll
+                for (int q = 24; q < 32; ++q) vv[q] = 0.0f;
+                const float r = warp_reduce_scatter32(vv);
+                if (r != 0.0f) {
+                    if (lane < 20) atomicAdd(A + ga_geo(ns) + lane, r);
+                    else if (lane == 20) atomicAdd(A + 5 * ns, r);
+                    else if (lane < 24) atomicAdd(A + ga_bc3(ns) + (lane - 21), r);
+                }
+            }
+
+            // ---- colour MLP backward
+            if constexpr (NC > 0) {
+                const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
+                const float *W2 = Cb + cb_W2(NC);
+                const float *B2 = Cb + cb_B2(NC);
+                const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
+                float *AC1 = A + ga_col(ns);
+                float *AW2 = AC1 + 4 * NC;
+                float *AW3 = AW2 + NC * NC;
+                float z1[NC], gz1[NC];
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    const float4 w = C1[j];
+                    z1[j] = fmaxf(fmaf(w.x, d.x, fmaf(w.y, d.y, fmaf(w.z, d.z, w.w))), 0.0f);
+                    gz1[j] = 0.0f;
+                }
+                for (int j0 = 0; j0 < NC; j0 += 8) {
+                    float v4[32];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = j0 + jj;
+                        const float4 *row = reinterpret_cast<const float4 *>(W2 + j * NC);
+                        float a2 = B2[j];
+#pragma unroll
+                        for (int k = 0; k < NC / 4; ++k) {
+                            const float4 w = row[k];
+                            a2 = fmaf(w.x, z1[4 * k + 0], a2);
+                            a2 = fmaf(w.y, z1[4 * k + 1], a2);
+                            a2 = fmaf(w.z, z1[4 * k + 2], a2);
+                            a2 = fmaf(w.w, z1[4 * k + 3], a2);
+                        }
+                        const float z2 = fmaxf(a2, 0.0f);
+                        const float4 w3 = C3[j];
+                        const float gz2 = fmaf(w3.x, g_a3.x, fmaf(w3.y, g_a3.y, w3.z * g_a3.z));
+                        const float ga2 = a2 > 0.0f ? gz2 : 0.0f;
+#pragma unroll
+                        for (int s = 0; s < NC / 32; ++s) {
+                            float vv[32];
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) vv[i] = ga2 * z1[32 * s + i];
+                            const float r = warp_reduce_scatter32(vv);
+                            if (r != 0.0f) atomicAdd(AW2 + j * NC + 32 * s + lane, r);
+                        }
+#pragma unroll
+                        for (int k = 0; k < NC / 4; ++k) {
+                            const float4 w = row[k];
+                            gz1[4 * k + 0] = fmaf(w.x, ga2, gz1[4 * k + 0]);
+                            gz1[4 * k + 1] = fmaf(w.y, ga2, gz1[4 * k + 1]);
+                            gz1[4 * k + 2] = fmaf(w.z, ga2, gz1[4 * k + 2]);
+                            gz1[4 * k + 3] = fmaf(w.w, ga2, gz1[4 * k + 3]);
+                        }
+                        v4[4 * jj + 0] = g_a3.x * z2;
+                        v4[4 * jj + 1] = g_a3.y * z2;
+                        v4[4 * jj + 2] = g_a3.z * z2;
+                        v4[4 * jj + 3] = ga2;
+                    }
+                    const float r = warp_reduce_scatter32(v4);
+                    if (r != 0.0f) atomicAdd(AW3 + 4 * j0 + lane, r);
+                }
+#pragma unroll
+                for (int j0 = 0; j0 < NC; j0 += 8) {
+                    float vv[32];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = j0 + jj;
+                        const float ga1 = z1[j] > 0.0f ? gz1[j] : 0.0f;
+                        vv[4 * jj + 0] = ga1 * d.x;
+                        vv[4 * jj + 1] = ga1 * d.y;
+                        vv[4 * jj + 2] = ga1 * d.z;
+                        vv[4 * jj + 3] = ga1;
+                    }
+                    const float r = warp_reduce_scatter32(vv);
+                    if (r != 0.0f) atomicAdd(AC1 + 4 * j0 + lane, r);
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = 0; e < cnt; ++e) {
+            const int64_t gid = s_gid[e];
+            flush_entry<NC>(a, acc + e * vg, gid - vn, gid, vg, threadIdx.x, blockDim.x);
+        }
+    }
+}
+
+template <int NC, int FORM, bool BF16>
+static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
+{
+    const size_t smem = (size_t)a.chunk * (entry_stride(a.n_sigma, NC) + grad_stride(a.n_sigma, NC)) * sizeof(float);
+    if (smem > 200 * 1024) return SNP_ERR_INVALID_ARG;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_raster_bwd<NC, FORM, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    if (a.n_tiles <= 0) return SNP_OK;
+    k_raster_bwd<NC, FORM, BF16><<<(unsigned)a.n_tiles, kRasterThreads, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SNP_OK : SNP_ERR_CUDA;
+}
+
+template <int NC>
+static snp_status dispatch_bwd(const RasterArgs &a, int form, int bf16, cudaStream_t st)
+{
+    if (form == SNP_FORM_STABLE)
+        return bf16 ? run_bwd<NC, 0, true>(a, st) : run_bwd<NC, 0, false>(a, st);
+    return bf16 ? run_bwd<NC, 1, true>(a, st) : run_bwd<NC, 1, false>(a, st);
+}
+
+snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
+                             cudaStream_t st)
+{
+    if (ts != 16) return SNP_ERR_UNSUPPORTED;
+    if (color_mode == SNP_COLOR_CONST) return dispatch_bwd<0>(a, form, bf16, st);
+    if (n_c == 32) return dispatch_bwd<32>(a, form, bf16, st);
+    if (n_c == 64) return dispatch_bwd<64>(a, form, bf16, st);
+    return SNP_ERR_UNSUPPORTED;
+}
+
+}  // namespace snp

@@ -1,0 +1,33 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/snp.h declares.
+
+No compute call is made (no GPU needed)."""
+import ctypes
+
+from paper_2510_08491_gb300 import _lib as L
+
+
+def test_header_declares_the_boundary():
+    syms = L.header_symbols()
+    for s in ("snp_create", "snp_destroy", "snp_render_forward", "snp_render_backward", "snp_reserve",
+              "snp_debug_keys", "snp_get_stats", "snp_last_error", "snp_get_net_layout"):
+        assert s in syms
+
+
+def test_library_exports_every_header_symbol():
+    from paper_2510_08491_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for s in L.header_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_net_layout_is_aligned_and_complete():
+    offs, stride = L.net_layout(16, L.COLOR_MLP, 32)
+    sizes = [48, 16, 16, 1, 8, 32 * 11, 32, 32 * 32, 32, 96, 3]
+    assert all(o % 8 == 0 for o in offs) and stride % 8 == 0
+    spans = sorted(zip(offs, sizes))
+    for (o1, s1), (o2, _) in zip(spans, spans[1:]):
+        assert o1 + s1 <= o2
+    assert spans[-1][0] + spans[-1][1] <= stride
+    offs_c, stride_c = L.net_layout(8, L.COLOR_CONST, 0)
+    assert offs_c[4:] == [-1] * 7 and stride_c == 24 + 8 + 8 + 8

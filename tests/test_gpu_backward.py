@@ -1,0 +1,113 @@
+"""GPU parity of the backward pass through the C ABI against the FP64 gradient oracle.
+
+Bar: per parameter group, |g - g*| <= 1e-3 (|g*| + rms(g*)) elementwise and
+||g - g*|| / ||g*|| <= 1e-3, for centres, log-scales, quaternions, constant
+colours and every density / colour-MLP weight.  dL/dC is a seeded random image;
+pixels whose termination step FP32 may decide differently from FP64 get dL = 0.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2510_08491_gb300 import synth
+from gpu_util import grad_rel_errors
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2510_08491_gb300 import build
+    build.build()
+    from paper_2510_08491_gb300.render import Renderer
+    return Renderer(0)
+
+
+def _gpu_grads(R, scene, cams, dL, form=0, t_min=1e-4, bg=(0.0, 0.0, 0.0)):
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene, unpack_geom_grad, unpack_net_grad
+    ps = pack_scene(scene)
+    cfg = L.make_config(form=form, t_min=t_min, bg=bg)
+    R.forward(ps, cams, cfg)
+    g_geom = torch.zeros_like(ps.geom)
+    g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device=ps.net.device)
+    R.backward(ps, torch.tensor(dL, dtype=torch.float32, device="cuda"), g_geom, g_net)
+    torch.cuda.synchronize()
+    g = unpack_geom_grad(g_geom)
+    g.update(unpack_net_grad(ps, g_net, scene))
+    return g
+
+
+def _oracle_grads(O, scene, cams, dL_views, t_min=1e-4, bg=(0.0, 0.0, 0.0), ts=16):
+    from oracle import grad as G
+    tl = O.tile_keys(scene, cams, ts)
+    lp = (tl.vals.astype(np.int64) % scene.n).astype(np.int32)
+    total = None
+    for v, cam in enumerate(cams):
+        pix = np.arange(cam.n_pixels, dtype=np.int32)
+        gt = tl.view_tile_off[v] + O.pixel_tile(cam, ts, pix)
+        _, g = G.grads(scene, cam, pix, gt, tl.tile_off, lp, dL_views[v], t_min, bg)
+        total = g if total is None else {k: total[k] + g[k] for k in g}
+    return total
+
+
+def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0)):
+    """Seeded dL/dC, zero on pixels whose termination decision is a near-tie."""
+    rng = np.random.default_rng(seed)
+    imgs, tl, outs = O.render_image(scene, cams, 16, t_min, bg)
+    per_view = []
+    for cam, o in zip(cams, outs):
+        d = rng.normal(size=(cam.n_pixels, 3))
+        d[o.flags != 0] = 0.0
+        per_view.append(d)
+    return per_view
+
+
+def _check(g, gref, fields):
+    errs = grad_rel_errors(g, {k: gref[k] for k in fields})
+    bad = {k: v for k, v in errs.items() if v[0] > GRAD_TOL or v[1] > GRAD_TOL}
+    assert not bad, f"gradient mismatch: {bad}"
+    return errs
+
+
+def test_const_colour_tiny(R, oracle_lib):
+    O = oracle_lib
+    wl = synth.workload("tiny64_128px")
+    dLv = _dl(O, wl.scene, wl.cameras, 1)
+    g = _gpu_grads(R, wl.scene, wl.cameras, np.concatenate(dLv))
+    gref = _oracle_grads(O, wl.scene, wl.cameras, dLv)
+    _check(g, gref, ["centers", "log_scales", "quats", "rgb", "W1", "b1", "w2", "b2"])
+
+
+def test_mlp_fd_subset_scene(R, oracle_lib):
+    """2,000 primitives with the differentiation workload's distributions, 64 x 64, ring camera k=0."""
+    O = oracle_lib
+    sc = synth.make_scene(2000, seed=0, center_half=3.0, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
+    cams = synth.ring_cameras(1, 8.0, 64, 64)
+    dLv = _dl(O, sc, cams, 2)
+    g = _gpu_grads(R, sc, cams, np.concatenate(dLv))
+    gref = _oracle_grads(O, sc, cams, dLv)
+    _check(g, gref, sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
+
+
+def test_mlp_denser_multiview(R, oracle_lib):
+    O = oracle_lib
+    sc = synth.make_scene(1200, seed=3, center_half=1.5, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
+    cams = [synth.look_at_camera((0.0, 0.5, 6.0), (0, 0, 0), 72, 56),
+            synth.look_at_camera((6.0, 0.0, 0.0), (0, 0, 0), 50, 61)]
+    dLv = _dl(O, sc, cams, 3, bg=(0.2, 0.1, 0.3))
+    g = _gpu_grads(R, sc, cams, np.concatenate(dLv), bg=(0.2, 0.1, 0.3))
+    gref = _oracle_grads(O, sc, cams, dLv, bg=(0.2, 0.1, 0.3))
+    _check(g, gref, sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
+
+
+def test_mlp64_ns32_bf16(R, oracle_lib):
+    O = oracle_lib
+    sc = synth.make_scene(800, seed=8, center_half=1.5, n_sigma=32, omega0=5.0, color="mlp", n_c=64).to_bf16()
+    cams = [synth.look_at_camera((0.0, 0.0, 6.0), (0, 0, 0), 64, 48)]
+    dLv = _dl(O, sc, cams, 4)
+    g = _gpu_grads(R, sc, cams, np.concatenate(dLv))
+    gref = _oracle_grads(O, sc, cams, dLv)
+    _check(g, gref, sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
