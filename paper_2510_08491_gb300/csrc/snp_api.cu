@@ -374,7 +374,7 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
     if ((s = ensure_scan_tmp(ctx, desc->n * n_cams, max_keys)) != SNP_OK) return s;
     {
         const int nc = desc->color_mode == SNP_COLOR_MLP ? desc->n_c : 1;
-        ENS(g_view, (size_t)desc->n * n_cams * 16 * 4);
+        ENS(g_view, (size_t)desc->n * n_cams * kGvFloats * 4);
         ENS(g_h0, (size_t)desc->n * nc * 4);
     }
     ctx->key_cap = max_keys;
@@ -508,9 +508,9 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     if (!scene || !dL_dimages || !grads) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
     const int64_t n = desc->n, vn = n * ctx->n_views;
     const int nc = desc->color_mode == SNP_COLOR_MLP ? desc->n_c : 1;
-    ENS(g_view, (size_t)vn * 16 * 4);
+    ENS(g_view, (size_t)vn * kGvFloats * 4);
     ENS(g_h0, (size_t)n * nc * 4);
-    CK(cudaMemsetAsync(ctx->g_view.p, 0, (size_t)vn * 16 * 4, st));
+    CK(cudaMemsetAsync(ctx->g_view.p, 0, (size_t)vn * kGvFloats * 4, st));
     CK(cudaMemsetAsync(ctx->g_h0.p, 0, (size_t)n * nc * 4, st));
     const uint32_t *svals = (const uint32_t *)(ctx->keys_in_alt ? ctx->vals_alt.p : ctx->vals.p);
     RasterArgs a;
@@ -591,6 +591,7 @@ snp_status snp_debug_keys(snp_context *ctx, int64_t token, uint64_t *keys_host, 
     const int64_t K = ctx->h_small[0];
     *k_out = K;
     if (ctx->h_small[4] != 0) return fail(ctx, SNP_ERR_CAPACITY, "tile keys exceeded the reserved capacity");
+    if (!keys_host && !vals_host) return SNP_OK;  // size query
     if (K > cap) return fail(ctx, SNP_ERR_INVALID_ARG, "host capacity %lld < K %lld", (long long)cap, (long long)K);
     if (K > 0) {
         const void *kp = ctx->keys_in_alt ? ctx->keys_alt.p : ctx->keys.p;

@@ -30,6 +30,10 @@ constexpr int kRecRgb = 16;   // 3: constant colour
 constexpr int kRecDepth = 19; // 1: camera-frame z of the centre
 constexpr int kRecFloats = 20;
 
+// Per (view, primitive) geometry-gradient record (floats): d/dMinv (9), d/dop (3),
+// d/docm (3), d/d(1/m) (1), d/drgb (3), unused (1).
+constexpr int kGvFloats = 20;
+
 // Per-view constants shared by the kernels.
 struct View {
     float R[9];
@@ -55,17 +59,18 @@ __device__ __forceinline__ float ksub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float kdiv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
 
-// Pixel ray (unit, world frame) through the centre of pixel (px, py).
+// Pixel ray (unit, world frame) through the centre of pixel (px, py), evaluated in
+// FP64 once per pixel and rounded to FP32 (the ray position near a primitive far
+// from the camera amplifies any error of d by the distance).
 __device__ __forceinline__ float3 pixel_ray(const View &v, int px, int py)
 {
-    float x = ((float)px + 0.5f - v.cx) / v.fx;
-    float y = ((float)py + 0.5f - v.cy) / v.fy;
-    float3 r;
-    r.x = fmaf(v.R[0], x, fmaf(v.R[3], y, v.R[6]));
-    r.y = fmaf(v.R[1], x, fmaf(v.R[4], y, v.R[7]));
-    r.z = fmaf(v.R[2], x, fmaf(v.R[5], y, v.R[8]));
-    float inv = rsqrtf(fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
-    return make_float3(r.x * inv, r.y * inv, r.z * inv);
+    const double x = ((double)px + 0.5 - (double)v.cx) / (double)v.fx;
+    const double y = ((double)py + 0.5 - (double)v.cy) / (double)v.fy;
+    const double rx = (double)v.R[0] * x + (double)v.R[3] * y + (double)v.R[6];
+    const double ry = (double)v.R[1] * x + (double)v.R[4] * y + (double)v.R[7];
+    const double rz = (double)v.R[2] * x + (double)v.R[5] * y + (double)v.R[8];
+    const double inv = 1.0 / sqrt(rx * rx + ry * ry + rz * rz);
+    return make_float3((float)(rx * inv), (float)(ry * inv), (float)(rz * inv));
 }
 
 template <bool BF16>

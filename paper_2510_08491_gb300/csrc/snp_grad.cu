@@ -13,7 +13,7 @@
 
 namespace snp {
 
-constexpr int kGv = 20;  // floats per (view, primitive) gradient record
+constexpr int kGv = kGvFloats;
 
 __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ geom, int64_t n,
                                                      const View *__restrict__ views, int n_views,

@@ -163,24 +163,28 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ geom,
     trect[gid] = tr;
     counts[gid] = cnt;
 
-    // Projection record (ordinary FP32 arithmetic from the same s, R).
+    // Projection record: evaluated in FP64 from the float32 inputs and rounded once.
     float *r = rec + gid * kRecFloats;
-    const float is[3] = {1.0f / s[0], 1.0f / s[1], 1.0f / s[2]};
-    float Minv[9];
+    const double sd[3] = {exp((double)ls[0]), exp((double)ls[1]), exp((double)ls[2])};
+    const double qd[4] = {q[0], q[1], q[2], q[3]};
+    const double iqn = 1.0 / sqrt(qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3]);
+    const double W = qd[0] * iqn, X = qd[1] * iqn, Y = qd[2] * iqn, Z = qd[3] * iqn;
+    const double Rd[3][3] = {
+        {1.0 - 2.0 * (Y * Y + Z * Z), 2.0 * (X * Y - W * Z), 2.0 * (X * Z + W * Y)},
+        {2.0 * (X * Y + W * Z), 1.0 - 2.0 * (X * X + Z * Z), 2.0 * (Y * Z - W * X)},
+        {2.0 * (X * Z - W * Y), 2.0 * (Y * Z + W * X), 1.0 - 2.0 * (X * X + Y * Y)}};
+    const double md = fmax(fmax(sd[0], sd[1]), sd[2]);
+    const double oc[3] = {(double)V.eye[0] - c[0], (double)V.eye[1] - c[1], (double)V.eye[2] - c[2]};
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) Minv[3 * a + b] = R[b][a] * is[a];
-    const float oc[3] = {V.eye[0] - c[0], V.eye[1] - c[1], V.eye[2] - c[2]};
-    const float inv_m = 1.0f / m;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) r[kRecMinv + k] = Minv[k];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        r[kRecOp + a] = fmaf(Minv[3 * a + 0], oc[0], fmaf(Minv[3 * a + 1], oc[1], Minv[3 * a + 2] * oc[2]));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) r[kRecOcm + a] = oc[a] * inv_m;
-    r[kRecInvM] = inv_m;
+    for (int a = 0; a < 3; ++a) {
+        const double m0 = Rd[0][a] / sd[a], m1 = Rd[1][a] / sd[a], m2 = Rd[2][a] / sd[a];
+        r[kRecMinv + 3 * a + 0] = (float)m0;
+        r[kRecMinv + 3 * a + 1] = (float)m1;
+        r[kRecMinv + 3 * a + 2] = (float)m2;
+        r[kRecOp + a] = (float)(m0 * oc[0] + m1 * oc[1] + m2 * oc[2]);
+        r[kRecOcm + a] = (float)(oc[a] / md);
+    }
+    r[kRecInvM] = (float)(1.0 / md);
 #pragma unroll
     for (int a = 0; a < 3; ++a) r[kRecRgb + a] = rgb[a];
     r[kRecDepth] = mu[2];

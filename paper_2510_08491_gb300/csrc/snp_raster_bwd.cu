@@ -17,8 +17,6 @@
 
 namespace snp {
 
-constexpr int kGvFloats = 20;  // per (view, primitive) geometry gradient record
-
 // Per-entry gradient accumulator layout (floats).
 __host__ __device__ constexpr int ga_geo(int ns) { return round4(5 * ns + 1); }
 __host__ __device__ constexpr int ga_bc3(int ns) { return ga_geo(ns) + kGvFloats; }

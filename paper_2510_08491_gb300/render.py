@@ -53,7 +53,8 @@ def pack_scene(scene, device="cuda", weight_dtype: Optional[str] = None) -> Pack
     for k, f in enumerate(NET_FIELDS):
         if offs[k] < 0:
             continue
-        a = getattr(scene, f).reshape(n, -1)
+        a = getattr(scene, f)
+        a = a.reshape(n, int(np.prod(a.shape[1:])) if a.ndim > 1 else 1)
         net[:, offs[k]:offs[k] + a.shape[1]] = a
     desc = L.SceneDesc(n, scene.n_sigma, cm, scene.n_c if mlp else 0, L.BF16 if wd == "bf16" else L.F32,
                        float(scene.omega0), 0)

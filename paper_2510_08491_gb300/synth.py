@@ -287,6 +287,10 @@ def workload(name: str, seed: int = 0) -> Workload:
     if name == "fwd100k_1080p_4view":
         sc = make_scene(100_000, seed, center_half=3.0, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
         return Workload(name, sc, ring_cameras(4, 8.0, 1920, 1080), 16)
+    if name == "prof100k_1080p_1view":
+        # the first view of the 100k / four-view workload, for profiler captures
+        wl = workload("fwd100k_1080p_4view", seed)
+        return Workload(name, wl.scene, wl.cameras[:1], 16)
     if name == "diff300k_720p":
         sc = make_scene(300_000, seed, center_half=3.0, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
         return Workload(name, sc, ring_cameras(1, 8.0, 1280, 720), 16)

@@ -2,8 +2,15 @@
 
 Bar: per parameter group, |g - g*| <= 1e-3 (|g*| + rms(g*)) elementwise and
 ||g - g*|| / ||g*|| <= 1e-3, for centres, log-scales, quaternions, constant
-colours and every density / colour-MLP weight.  dL/dC is a seeded random image;
-pixels whose termination step FP32 may decide differently from FP64 get dL = 0.
+colours and every density / colour-MLP weight.  dL/dC is a seeded random image.
+Two kinds of pixel get dL = 0 because FP32 cannot decide them like FP64:
+pixels whose termination step is a near-tie (|T - T_min| < 1% T_min), and
+pixels whose ray passes within |h^2| < SIL_EPS of some candidate's silhouette
+(h^2 = 1 - |closest point|^2 in unit-sphere coordinates).  At the silhouette the
+chord length is sqrt(h^2 / A), so the exact derivative of alpha_hat with respect
+to the geometry grows like 1 / sqrt(h^2), while FP32 evaluates h^2 with an
+absolute error near 1e-5 (the ray position near a primitive 8 units from the
+camera carries an FP32 representation error of ~1e-6 world units).
 """
 import numpy as np
 import pytest
@@ -15,6 +22,7 @@ from gpu_util import grad_rel_errors
 pytestmark = pytest.mark.gpu
 
 GRAD_TOL = 1e-3
+SIL_EPS = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -53,20 +61,45 @@ def _oracle_grads(O, scene, cams, dL_views, t_min=1e-4, bg=(0.0, 0.0, 0.0), ts=1
     return total
 
 
-def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0)):
-    """Seeded dL/dC, zero on pixels whose termination decision is a near-tie."""
+def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0), sil_eps=SIL_EPS):
+    """Seeded dL/dC, zero on near-tie termination pixels and near-silhouette pixels."""
+    from oracle import grad as G
     rng = np.random.default_rng(seed)
     imgs, tl, outs = O.render_image(scene, cams, 16, t_min, bg)
+    lp = (tl.vals.astype(np.int64) % scene.n).astype(np.int32)
     per_view = []
-    for cam, o in zip(cams, outs):
+    for v, (cam, o) in enumerate(zip(cams, outs)):
         d = rng.normal(size=(cam.n_pixels, 3))
         d[o.flags != 0] = 0.0
+        if sil_eps > 0:
+            pix = np.arange(cam.n_pixels, dtype=np.int32)
+            gt = tl.view_tile_off[v] + O.pixel_tile(cam, 16, pix)
+            lens = tl.tile_off[gt + 1] - tl.tile_off[gt]
+            owner = np.repeat(np.arange(cam.n_pixels), lens)
+            _, h2, _, _ = G.pair_diagnostics(scene, cam, pix, gt, tl.tile_off, lp)
+            near = np.zeros(cam.n_pixels, bool)
+            near[owner[np.abs(h2) < sil_eps]] = True
+            d[near] = 0.0
         per_view.append(d)
     return per_view
 
 
+def test_report_silhouette_band(R, oracle_lib):
+    """Diagnostic (no assertion): gradient error versus the silhouette band on the dense scene."""
+    O = oracle_lib
+    sc = synth.make_scene(1200, seed=3, center_half=1.5, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
+    cams = [synth.look_at_camera((0.0, 0.5, 6.0), (0, 0, 0), 72, 56)]
+    for eps in (0.0, 1e-4, 1e-3, 1e-2, 3e-2):
+        dLv = _dl(O, sc, cams, 3, sil_eps=eps)
+        g = _gpu_grads(R, sc, cams, np.concatenate(dLv))
+        gref = _oracle_grads(O, sc, cams, dLv)
+        errs = grad_rel_errors(g, {k: gref[k] for k in ("centers", "log_scales", "quats", "W1", "Wc2")})
+        print("sil_eps", eps, {k: (f"{a:.1e}", f"{b:.1e}") for k, (a, b) in errs.items()})
+
+
 def _check(g, gref, fields):
     errs = grad_rel_errors(g, {k: gref[k] for k in fields})
+    print({k: (f"{a:.1e}", f"{b:.1e}") for k, (a, b) in errs.items()})
     bad = {k: v for k, v in errs.items() if v[0] > GRAD_TOL or v[1] > GRAD_TOL}
     assert not bad, f"gradient mismatch: {bad}"
     return errs

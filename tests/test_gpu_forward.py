@@ -56,7 +56,9 @@ def test_mlp_multiview_ragged(R, oracle_lib, form):
     ref, flags, tl, _ = oracle_images(O, sc, cams, form=form)
     assert np.array_equal(keys, tl.keys)
     assert np.array_equal(vals, tl.vals)
-    tol = IMG_TOL if form == 0 else 5e-4  # Eq. 8 literally: phases measured from the camera
+    # Eq. 8 literally: phases are measured from the camera (|psi| ~ w0 |W1| |eye - c| / m, hundreds of
+    # radians, FP32 ulp ~3e-5 rad) and divided by a_k, so the literal form carries a larger FP32 error.
+    tol = IMG_TOL if form == 0 else 2e-3
     assert_image_close(img, ref, flags, tol=tol, tol_flagged=2 * tol)
 
 
