@@ -171,7 +171,9 @@ class TileLists:
     records: List[KeyRecords]
 
 
-def tile_keys(scene, cams: Sequence, ts: int, cs: Optional[CScene] = None) -> TileLists:
+def emission_keys(scene, cams: Sequence, ts: int, cs: Optional[CScene] = None):
+    """Tile keys and values in emission order (view, primitive, tile row, tile column),
+    before sorting; also returns the per-view key records and view tile offsets."""
     cs = cs or CScene(scene)
     n = scene.n
     keys_all, vals_all, recs = [], [], []
@@ -200,6 +202,11 @@ def tile_keys(scene, cams: Sequence, ts: int, cs: Optional[CScene] = None) -> Ti
         vto.append(vto[-1] + tx_n * ty_n)
     keys = np.concatenate(keys_all) if keys_all else np.zeros(0, np.uint64)
     vals = np.concatenate(vals_all) if vals_all else np.zeros(0, np.uint32)
+    return keys, vals, recs, vto
+
+
+def tile_keys(scene, cams: Sequence, ts: int, cs: Optional[CScene] = None) -> TileLists:
+    keys, vals, recs, vto = emission_keys(scene, cams, ts, cs)
     order = np.argsort(keys, kind="stable")
     keys = keys[order]
     vals = vals[order]
