@@ -407,7 +407,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         return fail(ctx, SNP_ERR_INVALID_ARG, "bad integral_form %d", c.integral_form);
     if (!(c.t_min >= 0.0f) || !(c.t_min < 1.0f)) return fail(ctx, SNP_ERR_INVALID_ARG, "t_min must be in [0, 1)");
     const int chunk = c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false);
-    if (chunk > 256 || raster_fwd_smem(desc->color_mode, desc->n_c, desc->n_sigma, chunk) > 200 * 1024)
+    if (chunk > 64 || raster_fwd_smem(desc->color_mode, desc->n_c, desc->n_sigma, chunk) > 220 * 1024)
         return fail(ctx, SNP_ERR_INVALID_ARG, "chunk %d too large", chunk);
 
     const int ts = c.tile_size;

@@ -68,6 +68,7 @@ snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int f
                              cudaStream_t st);
 size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk);
 int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward);
+int raster_bwd_default_chunk(int nc, int n_sigma);
 
 // snp_grad.cu
 void launch_project_bwd(const float *geom, int64_t n, const View *views, int n_views, const float *g_view,

@@ -210,6 +210,63 @@ __device__ __forceinline__ float3 mlp_color(const float *C, float3 d, float *z1_
     return make_float3(sigmoidf_fast(c0), sigmoidf_fast(c1), sigmoidf_fast(c2));
 }
 
+// Entry/exit test only (h^2 > 0), the same arithmetic as intersect().
+__device__ __forceinline__ bool hit_test(const float *R, float3 d)
+{
+    Hit h;
+    const float4 r0 = reinterpret_cast<const float4 *>(R)[0];
+    const float4 r1 = reinterpret_cast<const float4 *>(R)[1];
+    const float4 r2 = reinterpret_cast<const float4 *>(R)[2];
+    h.dp.x = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
+    h.dp.y = fmaf(r0.w, d.x, fmaf(r1.x, d.y, r1.y * d.z));
+    h.dp.z = fmaf(r1.z, d.x, fmaf(r1.w, d.y, r2.x * d.z));
+    h.A = fmaf(h.dp.x, h.dp.x, fmaf(h.dp.y, h.dp.y, h.dp.z * h.dp.z));
+    h.B = fmaf(r2.y, h.dp.x, fmaf(r2.z, h.dp.y, r2.w * h.dp.z));
+    h.iA = __fdividef(1.0f, h.A);
+    h.tm = -h.B * h.iA;
+    h.p.x = fmaf(h.tm, h.dp.x, r2.y);
+    h.p.y = fmaf(h.tm, h.dp.y, r2.z);
+    h.p.z = fmaf(h.tm, h.dp.z, r2.w);
+    h.h2 = 1.0f - fmaf(h.p.x, h.p.x, fmaf(h.p.y, h.p.y, h.p.z * h.p.z));
+    return h.h2 > 0.0f;
+}
+
+// Warp-aggregated append of `val` to list[] for the lanes with pred set.
+__device__ __forceinline__ void list_append(bool pred, uint16_t val, int *count, uint16_t *list)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (m == 0) return;
+    const unsigned lane = lane_id();
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+// Exclusive prefix of count[0..n) into pre[0..n] (one warp; n <= 64).
+__device__ __forceinline__ void warp_prefix64(const int *count, int n, int *pre)
+{
+    const unsigned lane = lane_id();
+    int a = (int)lane < n ? count[lane] : 0;
+    int b = (int)lane + 32 < n ? count[lane + 32] : 0;
+    int x = a, y = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int xa = __shfl_up_sync(0xffffffffu, x, o);
+        const int yb = __shfl_up_sync(0xffffffffu, y, o);
+        if ((int)lane >= o) {
+            x += xa;
+            y += yb;
+        }
+    }
+    const int tot_a = __shfl_sync(0xffffffffu, x, 31);
+    if ((int)lane < n) pre[lane] = x - a;
+    if ((int)lane + 32 < n) pre[lane + 32] = tot_a + y - b;
+    if (lane == 0) pre[n] = tot_a + __shfl_sync(0xffffffffu, y, 31);
+    else __shfl_sync(0xffffffffu, y, 31);
+}
+
 // Pixel of thread `tid` inside a 16 x 16 tile: warps cover 8 x 4 blocks.
 __device__ __forceinline__ void tile_pixel16(int tid, int &lx, int &ly)
 {

@@ -74,17 +74,275 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
     }
 }
 
+// Gradient of one (pixel, primitive) pair, reduced across the warp into the
+// entry's shared-memory accumulator A.  All 32 lanes call it together; lanes
+// without a pair pass contrib = false (their contributions are zero).
+template <int NC, int FORM>
+__device__ __forceinline__ void pair_backward(const float *R, const float *D, const float *Cb, int ns, float w0,
+                                              float3 d, bool contrib, float g_ah, float3 g_c, float3 col,
+                                              float *A)
+{
+    const unsigned lane = lane_id();
+    Hit h;
+    if (!contrib || !intersect(R, d, h)) {
+        // benign geometry for lanes that only take part in the warp reductions
+        h.tm = 0.0f; h.half = 1.0f; h.dp = make_float3(1.f, 0.f, 0.f); h.p = make_float3(0.f, 0.f, 0.f);
+        h.A = 1.0f; h.B = 0.0f; h.iA = 1.0f; h.h2 = 1.0f;
+        g_ah = 0.0f;
+        g_c = make_float3(0.f, 0.f, 0.f);
+        col = make_float3(0.f, 0.f, 0.f);
+    }
+    // ---- density (closed-form integral) and geometry
+    const float inv_m = R[kRecInvM];
+    const float3 ocm = make_float3(R[kRecOcm + 0], R[kRecOcm + 1], R[kRecOcm + 2]);
+    const float4 *W = reinterpret_cast<const float4 *>(D);
+    const float *w2 = D + 4 * ns;
+    const float b2 = w2[ns];
+    float3 g_u = make_float3(0.f, 0.f, 0.f), g_ocm = make_float3(0.f, 0.f, 0.f);
+    float g_hm = 0.0f, S = b2, g_invm = 0.0f, g_tm = 0.0f, g_half = 0.0f, g_b2;
+    const float tmm = h.tm * inv_m, hm = h.half * inv_m, dt = 2.0f * h.half;
+    const float tin = h.tm - h.half, tout = h.tm + h.half;
+    const float3 u = make_float3(fmaf(tmm, d.x, ocm.x), fmaf(tmm, d.y, ocm.y), fmaf(tmm, d.z, ocm.z));
+    const float gS = g_ah * dt;
+    float g_tout = 0.0f, g_tin = 0.0f;
+    if constexpr (FORM == 0) {
+        g_b2 = gS;
+    } else {
+        g_b2 = g_ah * (tout - tin);
+        g_tout = g_ah * b2;
+        g_tin = -g_ah * b2;
+    }
+    for (int k0 = 0; k0 < ns; k0 += 6) {
+        float vv[32];
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) {
+            const int k = k0 + kk;
+            float gw[3] = {0.f, 0.f, 0.f}, gb1 = 0.0f, gw2 = 0.0f;
+            if (k < ns) {
+                const float4 w = W[k];
+                const float wk = w2[k];
+                const float g = fmaf(w.x, d.x, fmaf(w.y, d.y, w.z * d.z));
+                if constexpr (FORM == 0) {
+                    const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
+                    const float th = g * hm;
+                    float sp, cp, st, ct;
+                    __sincosf(ph, &sp, &cp);
+                    __sincosf(th, &st, &ct);
+                    const float t2 = th * th;
+                    const float sc = fabsf(th) < 0.05f ? fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f)
+                                                       : __fdividef(st, th);
+                    const float scp = sincf_deriv(th, st, ct);
+                    S = fmaf(wk * cp, sc, S);
+                    const float gphi = -gS * wk * sp * sc;
+                    const float gth = gS * wk * cp * scp;
+                    gw2 = gS * cp * sc;
+                    gw[0] = w0 * fmaf(gphi, u.x, gth * hm * d.x);
+                    gw[1] = w0 * fmaf(gphi, u.y, gth * hm * d.y);
+                    gw[2] = w0 * fmaf(gphi, u.z, gth * hm * d.z);
+                    gb1 = w0 * gphi;
+                    g_u.x = fmaf(gphi, w.x, g_u.x);
+                    g_u.y = fmaf(gphi, w.y, g_u.y);
+                    g_u.z = fmaf(gphi, w.z, g_u.z);
+                    g_hm = fmaf(gth, g, g_hm);
+                } else {
+                    const float ak = g * inv_m;
+                    const float psi = fmaf(w.x, ocm.x, fmaf(w.y, ocm.y, fmaf(w.z, ocm.z, w.w)));
+                    float s1, c1, s0, c0v;
+                    __sincosf(fmaf(ak, tout, psi), &s1, &c1);
+                    __sincosf(fmaf(ak, tin, psi), &s0, &c0v);
+                    const float ia = g_ah != 0.0f ? __fdividef(1.0f, ak) : 0.0f;
+                    gw2 = g_ah * (s1 - s0) * ia;
+                    const float gpsi = g_ah * wk * (c1 - c0v) * ia;
+                    const float ga = g_ah * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
+                    gw[0] = w0 * fmaf(gpsi, ocm.x, ga * inv_m * d.x);
+                    gw[1] = w0 * fmaf(gpsi, ocm.y, ga * inv_m * d.y);
+                    gw[2] = w0 * fmaf(gpsi, ocm.z, ga * inv_m * d.z);
+                    gb1 = w0 * gpsi;
+                    g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
+                    g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
+                    g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
+                    g_invm = fmaf(ga, g, g_invm);
+                    g_tout = fmaf(g_ah * wk, c1, g_tout);
+                    g_tin = fmaf(-g_ah * wk, c0v, g_tin);
+                }
+            }
+            vv[5 * kk + 0] = gw[0];
+            vv[5 * kk + 1] = gw[1];
+            vv[5 * kk + 2] = gw[2];
+            vv[5 * kk + 3] = gb1;
+            vv[5 * kk + 4] = gw2;
+        }
+        vv[30] = 0.0f;
+        vv[31] = 0.0f;
+        const float r = warp_reduce_scatter32(vv);
+        const int kk = lane / 5, c = lane - 5 * kk, k = k0 + kk;
+        if (lane < 30 && k < ns && r != 0.0f) {
+            const int dst = c < 3 ? 3 * k + c : (c == 3 ? 3 * ns + k : 4 * ns + k);
+            atomicAdd(A + dst, r);
+        }
+    }
+    if constexpr (FORM == 0) {
+        const float gud = g_u.x * d.x + g_u.y * d.y + g_u.z * d.z;
+        g_half = 2.0f * g_ah * S + g_hm * inv_m;
+        g_invm = g_hm * h.half + gud * h.tm;
+        g_tm = gud * inv_m;
+        g_ocm = g_u;
+    } else {
+        g_tm = g_tout + g_tin;
+        g_half = g_tout - g_tin;
+    }
+    // half = sqrt(h2 / A): tm, half -> closest point, A, B -> Minv d, op
+    const float gx = __fdividef(g_half, 2.0f * h.half);
+    const float g_h2 = gx * h.iA;
+    float g_iA = gx * h.h2;
+    const float3 g_p = make_float3(-2.0f * g_h2 * h.p.x, -2.0f * g_h2 * h.p.y, -2.0f * g_h2 * h.p.z);
+    float3 g_op = g_p;
+    g_tm += g_p.x * h.dp.x + g_p.y * h.dp.y + g_p.z * h.dp.z;
+    float3 g_dp = make_float3(h.tm * g_p.x, h.tm * g_p.y, h.tm * g_p.z);
+    const float g_B = -g_tm * h.iA;
+    g_iA -= g_tm * h.B;
+    const float g_A = -g_iA * h.iA * h.iA;
+    const float3 op = make_float3(R[kRecOp + 0], R[kRecOp + 1], R[kRecOp + 2]);
+    g_dp.x = fmaf(2.0f * g_A, h.dp.x, fmaf(g_B, op.x, g_dp.x));
+    g_dp.y = fmaf(2.0f * g_A, h.dp.y, fmaf(g_B, op.y, g_dp.y));
+    g_dp.z = fmaf(2.0f * g_A, h.dp.z, fmaf(g_B, op.z, g_dp.z));
+    g_op.x = fmaf(g_B, h.dp.x, g_op.x);
+    g_op.y = fmaf(g_B, h.dp.y, g_op.y);
+    g_op.z = fmaf(g_B, h.dp.z, g_op.z);
+
+    float3 g_a3 = make_float3(0.f, 0.f, 0.f);
+    if constexpr (NC > 0) {
+        g_a3 = make_float3(g_c.x * col.x * (1.0f - col.x), g_c.y * col.y * (1.0f - col.y),
+                           g_c.z * col.z * (1.0f - col.z));
+    }
+    {
+        float vv[32];
+        vv[0] = g_dp.x * d.x; vv[1] = g_dp.x * d.y; vv[2] = g_dp.x * d.z;
+        vv[3] = g_dp.y * d.x; vv[4] = g_dp.y * d.y; vv[5] = g_dp.y * d.z;
+        vv[6] = g_dp.z * d.x; vv[7] = g_dp.z * d.y; vv[8] = g_dp.z * d.z;
+        vv[9] = g_op.x; vv[10] = g_op.y; vv[11] = g_op.z;
+        vv[12] = g_ocm.x; vv[13] = g_ocm.y; vv[14] = g_ocm.z;
+        vv[15] = g_invm;
+        vv[16] = NC == 0 ? g_c.x : 0.0f;
+        vv[17] = NC == 0 ? g_c.y : 0.0f;
+        vv[18] = NC == 0 ? g_c.z : 0.0f;
+        vv[19] = 0.0f;
+        vv[20] = g_b2;
+        vv[21] = g_a3.x; vv[22] = g_a3.y; vv[23] = g_a3.z;
+#pragma unroll
+        for (int q = 24; q < 32; ++q) vv[q] = 0.0f;
+        const float r = warp_reduce_scatter32(vv);
+        if (r != 0.0f) {
+            if (lane < 20) atomicAdd(A + ga_geo(ns) + lane, r);
+            else if (lane == 20) atomicAdd(A + 5 * ns, r);
+            else if (lane < 24) atomicAdd(A + ga_bc3(ns) + (lane - 21), r);
+        }
+    }
+
+    // ---- colour MLP backward
+    if constexpr (NC > 0) {
+        const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
+        const float *W2 = Cb + cb_W2(NC);
+        const float *B2 = Cb + cb_B2(NC);
+        const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
+        float *AC1 = A + ga_col(ns);
+        float *AW2 = AC1 + 4 * NC;
+        float *AW3 = AW2 + NC * NC;
+        float z1[NC], gz1[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const float4 w = C1[j];
+            z1[j] = fmaxf(fmaf(w.x, d.x, fmaf(w.y, d.y, fmaf(w.z, d.z, w.w))), 0.0f);
+            gz1[j] = 0.0f;
+        }
+        for (int j0 = 0; j0 < NC; j0 += 8) {
+            float v4[32];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = j0 + jj;
+                const float4 *row = reinterpret_cast<const float4 *>(W2 + j * NC);
+                float a2 = B2[j];
+#pragma unroll
+                for (int k = 0; k < NC / 4; ++k) {
+                    const float4 w = row[k];
+                    a2 = fmaf(w.x, z1[4 * k + 0], a2);
+                    a2 = fmaf(w.y, z1[4 * k + 1], a2);
+                    a2 = fmaf(w.z, z1[4 * k + 2], a2);
+                    a2 = fmaf(w.w, z1[4 * k + 3], a2);
+                }
+                const float z2 = fmaxf(a2, 0.0f);
+                const float4 w3 = C3[j];
+                const float gz2 = fmaf(w3.x, g_a3.x, fmaf(w3.y, g_a3.y, w3.z * g_a3.z));
+                const float ga2 = a2 > 0.0f ? gz2 : 0.0f;
+#pragma unroll
+                for (int s = 0; s < NC / 32; ++s) {
+                    float vv[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) vv[i] = ga2 * z1[32 * s + i];
+                    const float r = warp_reduce_scatter32(vv);
+                    if (r != 0.0f) atomicAdd(AW2 + j * NC + 32 * s + lane, r);
+                }
+#pragma unroll
+                for (int k = 0; k < NC / 4; ++k) {
+                    const float4 w = row[k];
+                    gz1[4 * k + 0] = fmaf(w.x, ga2, gz1[4 * k + 0]);
+                    gz1[4 * k + 1] = fmaf(w.y, ga2, gz1[4 * k + 1]);
+                    gz1[4 * k + 2] = fmaf(w.z, ga2, gz1[4 * k + 2]);
+                    gz1[4 * k + 3] = fmaf(w.w, ga2, gz1[4 * k + 3]);
+                }
+                v4[4 * jj + 0] = g_a3.x * z2;
+                v4[4 * jj + 1] = g_a3.y * z2;
+                v4[4 * jj + 2] = g_a3.z * z2;
+                v4[4 * jj + 3] = ga2;
+            }
+            const float r = warp_reduce_scatter32(v4);
+            if (r != 0.0f) atomicAdd(AW3 + 4 * j0 + lane, r);
+        }
+#pragma unroll
+        for (int j0 = 0; j0 < NC; j0 += 8) {
+            float vv[32];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = j0 + jj;
+                const float ga1 = z1[j] > 0.0f ? gz1[j] : 0.0f;
+                vv[4 * jj + 0] = ga1 * d.x;
+                vv[4 * jj + 1] = ga1 * d.y;
+                vv[4 * jj + 2] = ga1 * d.z;
+                vv[4 * jj + 3] = ga1;
+            }
+            const float r = warp_reduce_scatter32(vv);
+            if (r != 0.0f) atomicAdd(AC1 + 4 * j0 + lane, r);
+        }
+    }
+}
+
 template <int NC, int FORM, bool BF16>
-__global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(RasterArgs a)
+__global__ void __launch_bounds__(kRasterThreads, 1) k_raster_bwd(RasterArgs a)
 {
     extern __shared__ float4 smem4[];
-    float *sm = reinterpret_cast<float *>(smem4);
+    constexpr int NT = kRasterThreads;
+    const int CH = a.chunk;
+    const int ns = a.n_sigma;
+    const int es = entry_stride(ns, NC);
+    const int vg = grad_stride(ns, NC);
+    float4 *s_d = smem4;                                   // [NT] pixel rays
+    float *sm = reinterpret_cast<float *>(smem4 + NT);     // [CH][es] staged entries
+    float *acc = sm + CH * es;                             // [CH][vg] per-entry gradient sums
+    float *s_ah = acc + CH * vg;                           // [CH][NT] alpha_hat, then dL/dalpha_hat
+    float *s_w = s_ah + CH * NT;                           // [CH][NT] weights (-1: not composited)
+    float *s_tn = s_w + CH * NT;                           // [CH][NT] transmittance after the entry
+    float *s_col = s_tn + CH * NT;                         // [3][CH][NT] colours
+    float *s_gc = s_col + 3 * CH * NT;                     // [3][CH][NT] dL/dcolour
+    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_gc + 3 * CH * NT);  // [CH][NT]
+    uint16_t *s_al = s_hl + CH * NT;                       // [CH][NT]
     __shared__ uint32_t s_gid[kMaxChunk];
+    __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65];
     __shared__ int s_view;
     __shared__ uint32_t s_maxwalk;
 
+    const int tid = threadIdx.x;
     const int tile = blockIdx.x;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         s_view = find_view(a.views, a.n_views, tile);
         s_maxwalk = 0;
     }
@@ -94,18 +352,15 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(RasterArgs a)
     const int lt = tile - V.tile_off;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
     int lx, ly;
-    tile_pixel16(threadIdx.x, lx, ly);
+    tile_pixel16(tid, lx, ly);
     const int px = tx * 16 + lx, py = ty * 16 + ly;
     const bool inside = px < V.width && py < V.height;
     const float3 d = pixel_ray(V, px, py);
+    s_d[tid] = make_float4(d.x, d.y, d.z, 0.0f);
     const uint2 rg = a.ranges[tile];
-    const int ns = a.n_sigma;
-    const int es = entry_stride(ns, NC);
-    const int vg = grad_stride(ns, NC);
     const int64_t vn = (int64_t)v * a.n;
     const float w0 = a.omega0;
-    float *acc = sm + a.chunk * es;
-    for (int q = threadIdx.x; q < a.chunk * vg; q += blockDim.x) acc[q] = 0.0f;
+    for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
 
     const int64_t p = V.pix_off + (int64_t)py * V.width + px;
     float3 Cf = make_float3(0.f, 0.f, 0.f), dL = make_float3(0.f, 0.f, 0.f);
@@ -123,296 +378,160 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(RasterArgs a)
     float tau = 0.0f;
     float3 pref = make_float3(0.f, 0.f, 0.f);
     const unsigned lane = lane_id();
+    const int wid = tid >> 5;
     __syncthreads();
     const uint32_t maxwalk = s_maxwalk;
 
-    for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += a.chunk) {
-        const int cnt = min((int)(rg.y - c0), a.chunk);
+    for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += CH) {
+        const int cnt = min((int)(rg.y - c0), CH);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) s_gid[threadIdx.x] = a.vals[c0 + threadIdx.x];
+        if (tid < cnt) {
+            s_gid[tid] = a.vals[c0 + tid];
+            s_nh[tid] = 0;
+            s_na[tid] = 0;
+        }
         __syncthreads();
         stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
         __syncthreads();
+
+        // P1: hits among the entries this pixel walked in the forward
         for (int e = 0; e < cnt; ++e) {
             const uint32_t pos = c0 - rg.x + e;
-            const float *R = sm + e * es;
-            const float *D = R + kRecFloats;
-            const float *Cb = D + den_stride(ns);
-            float *A = acc + e * vg;
-            Hit h;
-            bool contrib = false;
-            float ah = 0.0f;
-            if (pos < nwalk && intersect(R, d, h)) {
-                ah = integral<FORM>(R, D, ns, d, h);
-                contrib = ah > 0.0f;
+            const bool hit = pos < nwalk && hit_test(sm + e * es, d);
+            s_ah[e * NT + tid] = 0.0f;
+            list_append(hit, (uint16_t)tid, &s_nh[e], s_hl + e * NT);
+        }
+        __syncthreads();
+        if (tid < 32) warp_prefix64(s_nh, cnt, s_ph);
+        __syncthreads();
+        // P2: alpha_hat of every hit
+        {
+            const int nh = s_ph[cnt];
+            int e = 0;
+            for (int q = tid; q < nh; q += NT) {
+                while (q >= s_ph[e + 1]) ++e;
+                const int pix = s_hl[e * NT + (q - s_ph[e])];
+                const float *R = sm + e * es;
+                const float4 dd = s_d[pix];
+                const float3 dv = make_float3(dd.x, dd.y, dd.z);
+                Hit h;
+                float ah = 0.0f;
+                if (intersect(R, dv, h)) ah = integral<FORM>(R, R + kRecFloats, ns, dv, h);
+                s_ah[e * NT + pix] = ah;
             }
-            if (!__any_sync(0xffffffffu, contrib)) continue;
-
-            // ---- compositing replay
-            float3 col = make_float3(0.f, 0.f, 0.f);
-            float g_ah = 0.0f;
-            float3 g_c = make_float3(0.f, 0.f, 0.f);
-            if (contrib) {
-                if constexpr (NC == 0)
-                    col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
-                else
-                    col = mlp_color<NC>(Cb, d);
+        }
+        __syncthreads();
+        // P3: replay of the compositing weights
+        for (int e = 0; e < cnt; ++e) {
+            const uint32_t pos = c0 - rg.x + e;
+            const float ah = s_ah[e * NT + tid];
+            const bool act = pos < nwalk && ah > 0.0f;
+            if (act) {
                 const float Ti = __expf(-tau);
-                const float wgt = Ti * (1.0f - __expf(-ah));
-                const float tn = tau + ah;
-                const float Tn = __expf(-tn);
-                pref.x = fmaf(wgt, col.x, pref.x);
-                pref.y = fmaf(wgt, col.y, pref.y);
-                pref.z = fmaf(wgt, col.z, pref.z);
-                g_ah = dL.x * (Tn * col.x - (Cf.x - pref.x)) + dL.y * (Tn * col.y - (Cf.y - pref.y)) +
-                       dL.z * (Tn * col.z - (Cf.z - pref.z)) - bgdot;
-                g_c = make_float3(dL.x * wgt, dL.y * wgt, dL.z * wgt);
-                tau = tn;
+                s_w[e * NT + tid] = Ti * (1.0f - __expf(-ah));
+                tau += ah;
+                s_tn[e * NT + tid] = __expf(-tau);
             } else {
-                // benign geometry for lanes that only take part in the warp reductions
-                h.tm = 0.0f; h.half = 1.0f; h.dp = make_float3(1.f, 0.f, 0.f); h.p = make_float3(0.f, 0.f, 0.f);
-                h.A = 1.0f; h.B = 0.0f; h.iA = 1.0f; h.h2 = 1.0f;
+                s_w[e * NT + tid] = -1.0f;
             }
-
-            // ---- density (closed-form integral) and geometry
-            const float inv_m = R[kRecInvM];
-            const float3 ocm = make_float3(R[kRecOcm + 0], R[kRecOcm + 1], R[kRecOcm + 2]);
-            const float4 *W = reinterpret_cast<const float4 *>(D);
-            const float *w2 = D + 4 * ns;
-            const float b2 = w2[ns];
-            float3 g_u = make_float3(0.f, 0.f, 0.f), g_ocm = make_float3(0.f, 0.f, 0.f);
-            float g_hm = 0.0f, S = b2, g_invm = 0.0f, g_tm = 0.0f, g_half = 0.0f, g_b2;
-            const float tmm = h.tm * inv_m, hm = h.half * inv_m, dt = 2.0f * h.half;
-            const float tin = h.tm - h.half, tout = h.tm + h.half;
-            const float3 u = make_float3(fmaf(tmm, d.x, ocm.x), fmaf(tmm, d.y, ocm.y), fmaf(tmm, d.z, ocm.z));
-            const float gS = g_ah * dt;
-            float g_tout = 0.0f, g_tin = 0.0f;
-            if constexpr (FORM == 0) {
-                g_b2 = gS;
-            } else {
-                g_b2 = g_ah * (tout - tin);
-                g_tout = g_ah * b2;
-                g_tin = -g_ah * b2;
+            list_append(act, (uint16_t)tid, &s_na[e], s_al + e * NT);
+        }
+        __syncthreads();
+        if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
+        __syncthreads();
+        // P4: colour of every composited pair
+        {
+            const int na = s_pa[cnt];
+            int e = 0;
+            for (int q = tid; q < na; q += NT) {
+                while (q >= s_pa[e + 1]) ++e;
+                const int pix = s_al[e * NT + (q - s_pa[e])];
+                const float *R = sm + e * es;
+                float3 col;
+                if constexpr (NC == 0) {
+                    col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
+                } else {
+                    const float4 dd = s_d[pix];
+                    col = mlp_color<NC>(R + kRecFloats + den_stride(ns), make_float3(dd.x, dd.y, dd.z));
+                }
+                s_col[(0 * CH + e) * NT + pix] = col.x;
+                s_col[(1 * CH + e) * NT + pix] = col.y;
+                s_col[(2 * CH + e) * NT + pix] = col.z;
             }
-            for (int k0 = 0; k0 < ns; k0 += 6) {
-                float vv[32];
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk) {
-                    const int k = k0 + kk;
-                    float gw[3] = {0.f, 0.f, 0.f}, gb1 = 0.0f, gw2 = 0.0f;
-                    if (k < ns) {
-                        const float4 w = W[k];
-                        const float wk = w2[k];
-                        const float g = fmaf(w.x, d.x, fmaf(w.y, d.y, w.z * d.z));
-                        if constexpr (FORM == 0) {
-                            const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
-                            const float th = g * hm;
-                            float sp, cp, st, ct;
-                            __sincosf(ph, &sp, &cp);
-                            __sincosf(th, &st, &ct);
-                            const float t2 = th * th;
-                            const float sc = fabsf(th) < 0.05f ? fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f)
-                                                               : __fdividef(st, th);
-                            const float scp = sincf_deriv(th, st, ct);
-                            S = fmaf(wk * cp, sc, S);
-                            const float gphi = -gS * wk * sp * sc;
-                            const float gth = gS * wk * cp * scp;
-                            gw2 = gS * cp * sc;
-                            gw[0] = w0 * fmaf(gphi, u.x, gth * hm * d.x);
-                            gw[1] = w0 * fmaf(gphi, u.y, gth * hm * d.y);
-                            gw[2] = w0 * fmaf(gphi, u.z, gth * hm * d.z);
-                            gb1 = w0 * gphi;
-                            g_u.x = fmaf(gphi, w.x, g_u.x);
-                            g_u.y = fmaf(gphi, w.y, g_u.y);
-                            g_u.z = fmaf(gphi, w.z, g_u.z);
-                            g_hm = fmaf(gth, g, g_hm);
-                        } else {
-                            const float ak = g * inv_m;
-                            const float psi = fmaf(w.x, ocm.x, fmaf(w.y, ocm.y, fmaf(w.z, ocm.z, w.w)));
-                            float s1, c1, s0, c0v;
-                            __sincosf(fmaf(ak, tout, psi), &s1, &c1);
-                            __sincosf(fmaf(ak, tin, psi), &s0, &c0v);
-                            const float ia = __fdividef(1.0f, ak);
-                            gw2 = g_ah * (s1 - s0) * ia;
-                            const float gpsi = g_ah * wk * (c1 - c0v) * ia;
-                            const float ga = g_ah * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
-                            gw[0] = w0 * fmaf(gpsi, ocm.x, ga * inv_m * d.x);
-                            gw[1] = w0 * fmaf(gpsi, ocm.y, ga * inv_m * d.y);
-                            gw[2] = w0 * fmaf(gpsi, ocm.z, ga * inv_m * d.z);
-                            gb1 = w0 * gpsi;
-                            g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
-                            g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
-                            g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
-                            g_invm = fmaf(ga, g, g_invm);
-                            g_tout = fmaf(g_ah * wk, c1, g_tout);
-                            g_tin = fmaf(-g_ah * wk, c0v, g_tin);
-                        }
-                    }
-                    vv[5 * kk + 0] = gw[0];
-                    vv[5 * kk + 1] = gw[1];
-                    vv[5 * kk + 2] = gw[2];
-                    vv[5 * kk + 3] = gb1;
-                    vv[5 * kk + 4] = gw2;
-                }
-                vv[30] = 0.0f;
-                vv[31] = 0.0f;
-                const float r = warp_reduce_scatter32(vv);
-                const int kk = lane / 5, c = lane - 5 * kk, k = k0 + kk;
-                if (lane < 30 && k < ns && r != 0.0f) {
-                    const int dst = c < 3 ? 3 * k + c : (c == 3 ? 3 * ns + k : 4 * ns + k);
-                    atomicAdd(A + dst, r);
-                }
+        }
+        __syncthreads();
+        // P5: dL/dalpha_hat = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg and dL/dc_i = w_i dL
+        for (int e = 0; e < cnt; ++e) {
+            const float w = s_w[e * NT + tid];
+            if (w >= 0.0f) {
+                const float3 col = make_float3(s_col[(0 * CH + e) * NT + tid], s_col[(1 * CH + e) * NT + tid],
+                                               s_col[(2 * CH + e) * NT + tid]);
+                const float Tn = s_tn[e * NT + tid];
+                pref.x = fmaf(w, col.x, pref.x);
+                pref.y = fmaf(w, col.y, pref.y);
+                pref.z = fmaf(w, col.z, pref.z);
+                s_ah[e * NT + tid] = dL.x * (Tn * col.x - (Cf.x - pref.x)) + dL.y * (Tn * col.y - (Cf.y - pref.y)) +
+                                     dL.z * (Tn * col.z - (Cf.z - pref.z)) - bgdot;
+                s_gc[(0 * CH + e) * NT + tid] = dL.x * w;
+                s_gc[(1 * CH + e) * NT + tid] = dL.y * w;
+                s_gc[(2 * CH + e) * NT + tid] = dL.z * w;
             }
-            if constexpr (FORM == 0) {
-                const float gud = g_u.x * d.x + g_u.y * d.y + g_u.z * d.z;
-                g_half = 2.0f * g_ah * S + g_hm * inv_m;
-                g_invm = g_hm * h.half + gud * h.tm;
-                g_tm = gud * inv_m;
-                g_ocm = g_u;
-            } else {
-                g_tm = g_tout + g_tin;
-                g_half = g_tout - g_tin;
-            }
-            // half = sqrt(h2 / A): tm, half -> closest point, A, B -> Minv d, op
-            const float gx = __fdividef(g_half, 2.0f * h.half);
-            const float g_h2 = gx * h.iA;
-            float g_iA = gx * h.h2;
-            const float3 g_p = make_float3(-2.0f * g_h2 * h.p.x, -2.0f * g_h2 * h.p.y, -2.0f * g_h2 * h.p.z);
-            float3 g_op = g_p;
-            g_tm += g_p.x * h.dp.x + g_p.y * h.dp.y + g_p.z * h.dp.z;
-            float3 g_dp = make_float3(h.tm * g_p.x, h.tm * g_p.y, h.tm * g_p.z);
-            const float g_B = -g_tm * h.iA;
-            g_iA -= g_tm * h.B;
-            const float g_A = -g_iA * h.iA * h.iA;
-            const float3 op = make_float3(R[kRecOp + 0], R[kRecOp + 1], R[kRecOp + 2]);
-            g_dp.x = fmaf(2.0f * g_A, h.dp.x, fmaf(g_B, op.x, g_dp.x));
-            g_dp.y = fmaf(2.0f * g_A, h.dp.y, fmaf(g_B, op.y, g_dp.y));
-            g_dp.z = fmaf(2.0f * g_A, h.dp.z, fmaf(g_B, op.z, g_dp.z));
-            g_op.x = fmaf(g_B, h.dp.x, g_op.x);
-            g_op.y = fmaf(g_B, h.dp.y, g_op.y);
-            g_op.z = fmaf(g_B, h.dp.z, g_op.z);
-
-            float3 g_a3 = make_float3(0.f, 0.f, 0.f);
-            if constexpr (NC > 0) {
-                g_a3 = make_float3(g_c.x * col.x * (1.0f - col.x), g_c.y * col.y * (1.0f - col.y),
-                                   g_c.z * col.z * (1.0f - col.z));
-            }
-            {
-                float vv[32];
-                vv[0] = g_dp.x * d.x; vv[1] = g_dp.x * d.y; vv[2] = g_dp.x * d.z;
-                vv[3] = g_dp.y * d.x; vv[4] = g_dp.y * d.y; vv[5] = g_dp.y * d.z;
-                vv[6] = g_dp.z * d.x; vv[7] = g_dp.z * d.y; vv[8] = g_dp.z * d.z;
-                vv[9] = g_op.x; vv[10] = g_op.y; vv[11] = g_op.z;
-                vv[12] = g_ocm.x; vv[13] = g_ocm.y; vv[14] = g_ocm.z;
-                vv[15] = g_invm;
-                vv[16] = NC == 0 ? g_c.x : 0.0f;
-                vv[17] = NC == 0 ? g_c.y : 0.0f;
-                vv[18] = NC == 0 ? g_c.z : 0.0f;
-                vv[19] = 0.0f;
-                vv[20] = g_b2;
-                vv[21] = g_a3.x; vv[22] = g_a3.y; vv[23] = g_a3.z;
-#pragma unroll
-                for (int q = 24; q < 32; ++q) vv[q] = 0.0f;
-                const float r = warp_reduce_scatter32(vv);
-                if (r != 0.0f) {
-                    if (lane < 20) atomicAdd(A + ga_geo(ns) + lane, r);
-                    else if (lane == 20) atomicAdd(A + 5 * ns, r);
-                    else if (lane < 24) atomicAdd(A + ga_bc3(ns) + (lane - 21), r);
-                }
-            }
-
-            // ---- colour MLP backward
-            if constexpr (NC > 0) {
-                const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
-                const float *W2 = Cb + cb_W2(NC);
-                const float *B2 = Cb + cb_B2(NC);
-                const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
-                float *AC1 = A + ga_col(ns);
-                float *AW2 = AC1 + 4 * NC;
-                float *AW3 = AW2 + NC * NC;
-                float z1[NC], gz1[NC];
-#pragma unroll
-                for (int j = 0; j < NC; ++j) {
-                    const float4 w = C1[j];
-                    z1[j] = fmaxf(fmaf(w.x, d.x, fmaf(w.y, d.y, fmaf(w.z, d.z, w.w))), 0.0f);
-                    gz1[j] = 0.0f;
-                }
-                for (int j0 = 0; j0 < NC; j0 += 8) {
-                    float v4[32];
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int j = j0 + jj;
-                        const float4 *row = reinterpret_cast<const float4 *>(W2 + j * NC);
-                        float a2 = B2[j];
-#pragma unroll
-                        for (int k = 0; k < NC / 4; ++k) {
-                            const float4 w = row[k];
-                            a2 = fmaf(w.x, z1[4 * k + 0], a2);
-                            a2 = fmaf(w.y, z1[4 * k + 1], a2);
-                            a2 = fmaf(w.z, z1[4 * k + 2], a2);
-                            a2 = fmaf(w.w, z1[4 * k + 3], a2);
-                        }
-                        const float z2 = fmaxf(a2, 0.0f);
-                        const float4 w3 = C3[j];
-                        const float gz2 = fmaf(w3.x, g_a3.x, fmaf(w3.y, g_a3.y, w3.z * g_a3.z));
-                        const float ga2 = a2 > 0.0f ? gz2 : 0.0f;
-#pragma unroll
-                        for (int s = 0; s < NC / 32; ++s) {
-                            float vv[32];
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) vv[i] = ga2 * z1[32 * s + i];
-                            const float r = warp_reduce_scatter32(vv);
-                            if (r != 0.0f) atomicAdd(AW2 + j * NC + 32 * s + lane, r);
-                        }
-#pragma unroll
-                        for (int k = 0; k < NC / 4; ++k) {
-                            const float4 w = row[k];
-                            gz1[4 * k + 0] = fmaf(w.x, ga2, gz1[4 * k + 0]);
-                            gz1[4 * k + 1] = fmaf(w.y, ga2, gz1[4 * k + 1]);
-                            gz1[4 * k + 2] = fmaf(w.z, ga2, gz1[4 * k + 2]);
-                            gz1[4 * k + 3] = fmaf(w.w, ga2, gz1[4 * k + 3]);
-                        }
-                        v4[4 * jj + 0] = g_a3.x * z2;
-                        v4[4 * jj + 1] = g_a3.y * z2;
-                        v4[4 * jj + 2] = g_a3.z * z2;
-                        v4[4 * jj + 3] = ga2;
-                    }
-                    const float r = warp_reduce_scatter32(v4);
-                    if (r != 0.0f) atomicAdd(AW3 + 4 * j0 + lane, r);
-                }
-#pragma unroll
-                for (int j0 = 0; j0 < NC; j0 += 8) {
-                    float vv[32];
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int j = j0 + jj;
-                        const float ga1 = z1[j] > 0.0f ? gz1[j] : 0.0f;
-                        vv[4 * jj + 0] = ga1 * d.x;
-                        vv[4 * jj + 1] = ga1 * d.y;
-                        vv[4 * jj + 2] = ga1 * d.z;
-                        vv[4 * jj + 3] = ga1;
-                    }
-                    const float r = warp_reduce_scatter32(vv);
-                    if (r != 0.0f) atomicAdd(AC1 + 4 * j0 + lane, r);
-                }
+        }
+        if (tid < cnt) s_nb[tid] = (s_na[tid] + 31) >> 5;
+        __syncthreads();
+        if (tid < 32) warp_prefix64(s_nb, cnt, s_pb);
+        __syncthreads();
+        // P6: per-pair gradients in warp batches of one entry each
+        {
+            const int nb = s_pb[cnt];
+            int e = 0;
+            for (int b = wid; b < nb; b += NT / 32) {
+                while (b >= s_pb[e + 1]) ++e;
+                const int k = (b - s_pb[e]) * 32 + (int)lane;
+                const bool valid = k < s_na[e];
+                const int pix = valid ? s_al[e * NT + k] : 0;
+                const float4 dd = s_d[pix];
+                const float *R = sm + e * es;
+                const float3 g_c = make_float3(s_gc[(0 * CH + e) * NT + pix], s_gc[(1 * CH + e) * NT + pix],
+                                               s_gc[(2 * CH + e) * NT + pix]);
+                const float3 col = make_float3(s_col[(0 * CH + e) * NT + pix], s_col[(1 * CH + e) * NT + pix],
+                                               s_col[(2 * CH + e) * NT + pix]);
+                pair_backward<NC, FORM>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0,
+                                        make_float3(dd.x, dd.y, dd.z), valid, s_ah[e * NT + pix], g_c, col,
+                                        acc + e * vg);
             }
         }
         __syncthreads();
         for (int e = 0; e < cnt; ++e) {
             const int64_t gid = s_gid[e];
-            flush_entry<NC>(a, acc + e * vg, gid - vn, gid, vg, threadIdx.x, blockDim.x);
+            flush_entry<NC>(a, acc + e * vg, gid - vn, gid, vg, tid, NT);
         }
     }
+    (void)lane;
+}
+
+static size_t bwd_smem_bytes(int nc, int ns, int chunk)
+{
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 +
+                             (size_t)kRasterThreads * (9 * 4 + 2 * 2);
+    return kRasterThreads * 16 + (size_t)chunk * per_entry;
+}
+
+int raster_bwd_default_chunk(int nc, int ns)
+{
+    int ch = 8;
+    while (ch > 1 && bwd_smem_bytes(nc, ns, ch) > 200 * 1024) --ch;
+    return ch;
 }
 
 template <int NC, int FORM, bool BF16>
 static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
 {
-    const size_t smem = (size_t)a.chunk * (entry_stride(a.n_sigma, NC) + grad_stride(a.n_sigma, NC)) * sizeof(float);
-    if (smem > 200 * 1024) return SNP_ERR_INVALID_ARG;
+    const size_t smem = bwd_smem_bytes(NC, a.n_sigma, a.chunk);
+    if (smem > 220 * 1024 || a.chunk > 64) return SNP_ERR_INVALID_ARG;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_raster_bwd<NC, FORM, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_raster_bwd<NC, FORM, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr_set = true;
     }
     if (a.n_tiles <= 0) return SNP_OK;
