@@ -215,6 +215,17 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
                                const snp_scene_ptrs *scene, const float *dL_dimages, const snp_grad_ptrs *grads,
                                void *stream);
 
+/* Autotuner: times forward (and, when with_backward != 0, backward) of this scene
+ * and these cameras for tile sizes 8, 16, 32 and two staging chunk sizes each,
+ * with CUDA events on `stream`, and writes the fastest configuration to *best
+ * (other fields copied from *base) and its time per call to *best_ms.
+ * Allocates its own temporary image, loss-gradient and gradient buffers (an
+ * offline call: not for stream capture).  Leaves the context's latest-forward
+ * state undefined (render again before a backward). */
+snp_status snp_autotune(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
+                        const snp_camera *cams, int32_t n_cams, const snp_config *base, int32_t with_backward,
+                        snp_config *best, float *best_ms, void *stream);
+
 /* Work counters of the forward identified by token (synchronises the stream). */
 snp_status snp_get_stats(snp_context *ctx, int64_t token, snp_stats *out, void *stream);
 

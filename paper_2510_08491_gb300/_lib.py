@@ -79,6 +79,8 @@ _SIGS = {
     "snp_debug_keys": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
                        C.c_void_p],
     "snp_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32],
+    "snp_autotune": [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(ScenePtrs), C.POINTER(Camera), C.c_int32,
+                     C.POINTER(Config), C.c_int32, C.POINTER(Config), C.POINTER(C.c_float), C.c_void_p],
 }
 FLAG_STAGE_TIMING = 1
 STAGES = ("project", "scan", "emit", "sort", "ranges", "raster_fwd", "raster_bwd", "post_bwd")

@@ -126,7 +126,7 @@ struct snp_context {
     bool reserved = false;
     // device workspace
     Buf views, rec, trect, counts, offsets, scan_tmp, keys, vals, keys_alt, vals_alt, hist, hist_scan, ranges,
-        px_state, px_nwalk, stats, small, g_view, g_h0;
+        px_state, px_nwalk, stats, small, g_view, g_h0, qkeys, qvals, qkeys_alt, qvals_alt, qhist, qhist_scan;
     // pinned host staging
     View *h_views = nullptr;
     uint32_t *h_small = nullptr;
@@ -140,9 +140,18 @@ struct snp_context {
     snp_scene_desc desc{};
     snp_config cfg{};
     int ts = 16, chunk = 0;
+    bool queue_in_alt = false;
     StageTimer timer;
     bool timing = false;
+    // cameras of the reservation (a captured forward must use exactly these)
+    snp_camera res_cams[kMaxViews];
+    int res_n_cams = 0, res_ts = 16;
+    int64_t res_tiles = 0, res_pixels = 0;
 };
+
+// Offsets inside the small device buffer.
+constexpr size_t kSmallTotal = 0, kSmallFlags = 16, kSmallTiles = 32, kSmallWork = 48, kSmallNsort = 64,
+                 kSmallBytes = 256;
 
 #define STAGE_BEGIN(k) \
     if (ctx->timing) ctx->timer.begin((k), st)
@@ -304,7 +313,8 @@ void snp_destroy(snp_context *ctx)
     cudaDeviceSynchronize();
     Buf *bufs[] = {&ctx->views, &ctx->rec, &ctx->trect, &ctx->counts, &ctx->offsets, &ctx->scan_tmp, &ctx->keys,
                    &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
-                   &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0};
+                   &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0,
+                   &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_views) cudaFreeHost(ctx->h_views);
@@ -341,16 +351,24 @@ static snp_status ensure_frame(snp_context *ctx, int64_t n, int n_views, int64_t
     ENS(px_state, (size_t)pixels * 16);
     ENS(px_nwalk, (size_t)pixels * 4);
     ENS(stats, 64);
-    ENS(small, 64);
+    ENS(small, kSmallBytes);
+    ENS(qkeys, (size_t)tiles * 8);
+    ENS(qkeys_alt, (size_t)tiles * 8);
+    ENS(qvals, (size_t)tiles * 4);
+    ENS(qvals_alt, (size_t)tiles * 4);
+    ENS(qhist, (size_t)sort_hist_words(tiles) * 4);
+    ENS(qhist_scan, (size_t)sort_hist_words(tiles) * 4);
     (void)d;
     return SNP_OK;
 }
 
-static snp_status ensure_scan_tmp(snp_context *ctx, int64_t vn, int64_t key_bound)
+static snp_status ensure_scan_tmp(snp_context *ctx, int64_t vn, int64_t key_bound, int64_t tiles)
 {
     int64_t w = scan_temp_words(vn);
     const int64_t hw = scan_temp_words(sort_hist_words(key_bound));
     if (hw > w) w = hw;
+    const int64_t tw = scan_temp_words(sort_hist_words(tiles));
+    if (tw > w) w = tw;
     ENS(scan_tmp, (size_t)(w + 16) * 4);
     return SNP_OK;
 }
@@ -365,13 +383,21 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
     if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
     if ((s = check_cams(ctx, cams, n_cams)) != SNP_OK) return s;
     const int ts = cfg && cfg->tile_size ? cfg->tile_size : 16;
+    if (ts != 8 && ts != 16 && ts != 32) return fail(ctx, SNP_ERR_UNSUPPORTED, "tile_size %d not built", ts);
     int64_t tiles, pixels;
     ctx->reserved = false;
     if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) return s;
     if (max_keys <= 0) max_keys = 4 * desc->n * n_cams + 1024;
     if ((s = ensure_frame(ctx, desc->n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
     if ((s = ensure_keys(ctx, max_keys)) != SNP_OK) return s;
-    if ((s = ensure_scan_tmp(ctx, desc->n * n_cams, max_keys)) != SNP_OK) return s;
+    if ((s = ensure_scan_tmp(ctx, desc->n * n_cams, max_keys, tiles)) != SNP_OK) return s;
+    // the view table of the reserved cameras stays on the device for captured forwards
+    CK(cudaMemcpy(ctx->views.p, ctx->h_views, sizeof(View) * n_cams, cudaMemcpyHostToDevice));
+    memcpy(ctx->res_cams, cams, sizeof(snp_camera) * n_cams);
+    ctx->res_n_cams = n_cams;
+    ctx->res_ts = ts;
+    ctx->res_tiles = tiles;
+    ctx->res_pixels = pixels;
     {
         const int nc = desc->color_mode == SNP_COLOR_MLP ? desc->n_c : 1;
         ENS(g_view, (size_t)desc->n * n_cams * kGvFloats * 4);
@@ -402,17 +428,33 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     c.t_min = 1e-4f;
     if (cfg) c = *cfg;
     if (c.tile_size == 0) c.tile_size = 16;
-    if (c.tile_size != 16) return fail(ctx, SNP_ERR_UNSUPPORTED, "tile_size %d not built", c.tile_size);
+    if (c.tile_size != 8 && c.tile_size != 16 && c.tile_size != 32)
+        return fail(ctx, SNP_ERR_UNSUPPORTED, "tile_size %d not built", c.tile_size);
     if (c.integral_form != SNP_FORM_STABLE && c.integral_form != SNP_FORM_NAIVE)
         return fail(ctx, SNP_ERR_INVALID_ARG, "bad integral_form %d", c.integral_form);
     if (!(c.t_min >= 0.0f) || !(c.t_min < 1.0f)) return fail(ctx, SNP_ERR_INVALID_ARG, "t_min must be in [0, 1)");
-    const int chunk = c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false);
-    if (chunk > 64 || raster_fwd_smem(desc->color_mode, desc->n_c, desc->n_sigma, chunk) > 220 * 1024)
+    const int ts = c.tile_size;
+    const int chunk =
+        c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts);
+    if (chunk > 64 || raster_fwd_smem(desc->color_mode, desc->n_c, desc->n_sigma, chunk, ts) > 220 * 1024)
         return fail(ctx, SNP_ERR_INVALID_ARG, "chunk %d too large", chunk);
 
-    const int ts = c.tile_size;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
     int64_t tiles, pixels;
-    if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) return s;
+    if (capturing) {
+        // no host synchronisation and no upload: use the reservation's device view table
+        if (!ctx->reserved)
+            return fail(ctx, SNP_ERR_INVALID_ARG, "a forward under stream capture needs snp_reserve first");
+        if (n_cams != ctx->res_n_cams || memcmp(cams, ctx->res_cams, sizeof(snp_camera) * n_cams) != 0 ||
+            ts != ctx->res_ts)
+            return fail(ctx, SNP_ERR_INVALID_ARG, "a captured forward must use the reserved cameras and tile size");
+        tiles = ctx->res_tiles;
+        pixels = ctx->res_pixels;
+    } else if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) {
+        return s;
+    }
     const int64_t n = desc->n, vn = n * n_cams;
     if ((s = ensure_frame(ctx, n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
     ctx->token++;  // invalidates the previous forward's state from here on
@@ -425,16 +467,20 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     ctx->ts = ts;
     ctx->chunk = chunk;
 
-    CK(cudaMemcpyAsync(ctx->views.p, ctx->h_views, sizeof(View) * n_cams, cudaMemcpyHostToDevice, st));
-    CK(cudaEventRecord(ctx->ev_views, st));
-    uint32_t *d_total = (uint32_t *)ctx->small.p;
-    int32_t *d_flags = (int32_t *)((char *)ctx->small.p + 16);
+    if (!capturing) {
+        CK(cudaMemcpyAsync(ctx->views.p, ctx->h_views, sizeof(View) * n_cams, cudaMemcpyHostToDevice, st));
+        CK(cudaEventRecord(ctx->ev_views, st));
+    }
+    uint32_t *d_total = (uint32_t *)((char *)ctx->small.p + kSmallTotal);
+    int32_t *d_flags = (int32_t *)((char *)ctx->small.p + kSmallFlags);
+    uint32_t *d_tiles = (uint32_t *)((char *)ctx->small.p + kSmallTiles);
+    int *d_work = (int *)((char *)ctx->small.p + kSmallWork);
 
     int64_t key_bound;
     if (!ctx->reserved) {
-        if ((s = ensure_scan_tmp(ctx, vn, 0)) != SNP_OK) return s;
+        if ((s = ensure_scan_tmp(ctx, vn, 0, tiles)) != SNP_OK) return s;
     }
-    ctx->timing = (c.flags & SNP_FLAG_STAGE_TIMING) != 0;
+    ctx->timing = (c.flags & SNP_FLAG_STAGE_TIMING) != 0 && !capturing;
     STAGE_BEGIN(SNP_STAGE_PROJECT);
     launch_project((const float *)scene->geom, n, (const View *)ctx->views.p, n_cams, ts, (float *)ctx->rec.p,
                    (int4 *)ctx->trect.p, (uint32_t *)ctx->counts.p, st);
@@ -448,7 +494,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         CK(cudaStreamSynchronize(st));
         key_bound = ctx->h_small[0];
         if ((s = ensure_keys(ctx, key_bound)) != SNP_OK) return s;
-        if ((s = ensure_scan_tmp(ctx, vn, key_bound)) != SNP_OK) return s;
+        if ((s = ensure_scan_tmp(ctx, vn, key_bound, tiles)) != SNP_OK) return s;
         ctx->K = key_bound;
     } else {
         key_bound = ctx->key_cap;
@@ -459,18 +505,26 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     launch_emit((const int4 *)ctx->trect.p, (const uint32_t *)ctx->counts.p, (const uint32_t *)ctx->offsets.p,
                 (const float *)ctx->rec.p, n, (const View *)ctx->views.p, n_cams, (uint64_t *)ctx->keys.p,
                 (uint32_t *)ctx->vals.p, key_bound, d_flags, st);
+    uint32_t *d_nsort = (uint32_t *)((char *)ctx->small.p + kSmallNsort);
+    launch_clamp_count(d_total, key_bound, d_nsort, st);
     STAGE_END();
     const int nbits = 32 + tile_bits(tiles);
     STAGE_BEGIN(SNP_STAGE_SORT);
     ctx->keys_in_alt = radix_sort((uint64_t *)ctx->keys.p, (uint32_t *)ctx->vals.p, (uint64_t *)ctx->keys_alt.p,
-                                  (uint32_t *)ctx->vals_alt.p, d_total, key_bound, nbits, (uint32_t *)ctx->hist.p,
+                                  (uint32_t *)ctx->vals_alt.p, d_nsort, key_bound, nbits, (uint32_t *)ctx->hist.p,
                                   (uint32_t *)ctx->hist_scan.p, (uint32_t *)ctx->scan_tmp.p, st);
     STAGE_END();
     const uint64_t *skeys = (const uint64_t *)(ctx->keys_in_alt ? ctx->keys_alt.p : ctx->keys.p);
     const uint32_t *svals = (const uint32_t *)(ctx->keys_in_alt ? ctx->vals_alt.p : ctx->vals.p);
     STAGE_BEGIN(SNP_STAGE_RANGES);
     CK(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)tiles * 8, st));
-    launch_tile_ranges(skeys, d_total, key_bound, (uint2 *)ctx->ranges.p, st);
+    launch_tile_ranges(skeys, d_nsort, key_bound, (uint2 *)ctx->ranges.p, st);
+    // persistent raster work queue: tiles by decreasing list length
+    launch_tile_queue((const uint2 *)ctx->ranges.p, tiles, (uint64_t *)ctx->qkeys.p, (uint32_t *)ctx->qvals.p,
+                      d_tiles, st);
+    ctx->queue_in_alt = radix_sort((uint64_t *)ctx->qkeys.p, (uint32_t *)ctx->qvals.p, (uint64_t *)ctx->qkeys_alt.p,
+                                   (uint32_t *)ctx->qvals_alt.p, d_tiles, tiles, 32, (uint32_t *)ctx->qhist.p,
+                                   (uint32_t *)ctx->qhist_scan.p, (uint32_t *)ctx->scan_tmp.p, st);
     STAGE_END();
     CK(cudaMemsetAsync(ctx->stats.p, 0, 24, st));
 
@@ -480,6 +534,9 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     a.px_state = (float4 *)ctx->px_state.p;
     a.px_nwalk = (uint32_t *)ctx->px_nwalk.p;
     a.stats = (unsigned long long *)ctx->stats.p;
+    a.work_counter = d_work;
+    a.queue = (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p);
+    CK(cudaMemsetAsync(d_work, 0, 4, st));
     STAGE_BEGIN(SNP_STAGE_RASTER_FWD);
     s = launch_raster_fwd(a, desc->color_mode, desc->n_c, c.integral_form, desc->weight_dtype == SNP_BF16, ts, st);
     STAGE_END();
@@ -521,8 +578,12 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     a.g_net = grads->net;
     a.g_view = (float *)ctx->g_view.p;
     a.g_h0 = (float *)ctx->g_h0.p;
-    a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true);
+    a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true, ctx->ts);
     if (ctx->cfg.chunk > 0 && ctx->cfg.chunk < a.chunk) a.chunk = ctx->cfg.chunk;
+    int *d_work = (int *)((char *)ctx->small.p + kSmallWork);
+    a.work_counter = d_work;
+    a.queue = (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p);
+    CK(cudaMemsetAsync(d_work, 0, 4, st));
     STAGE_BEGIN(SNP_STAGE_RASTER_BWD);
     s = launch_raster_bwd(a, desc->color_mode, desc->n_c, ctx->cfg.integral_form, desc->weight_dtype == SNP_BF16,
                           ctx->ts, st);
@@ -537,6 +598,94 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
                           a.off_bc1, a.stride, (const float *)ctx->g_h0.p, grads->net, st);
     STAGE_END();
     CK(cudaGetLastError());
+    return SNP_OK;
+}
+
+}  // extern "C"
+
+__global__ void k_fill_f32(float *p, int64_t n, float v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+extern "C" {
+
+snp_status snp_autotune(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
+                        const snp_camera *cams, int32_t n_cams, const snp_config *base, int32_t with_backward,
+                        snp_config *best, float *best_ms, void *stream)
+{
+    if (!ctx || !desc || !scene || !cams || !best || !best_ms) return SNP_ERR_INVALID_ARG;
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    if ((s = check_cams(ctx, cams, n_cams)) != SNP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    snp_config b{};
+    b.t_min = 1e-4f;
+    if (base) b = *base;
+    b.flags &= ~SNP_FLAG_STAGE_TIMING;
+    int64_t pixels = 0;
+    for (int v = 0; v < n_cams; ++v) pixels += (int64_t)cams[v].width * cams[v].height;
+    snp_net_layout L;
+    layout_of(*desc, L);
+    float *img = nullptr, *dL = nullptr, *gg = nullptr, *gn = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (img) cudaFree(img);
+        if (dL) cudaFree(dL);
+        if (gg) cudaFree(gg);
+        if (gn) cudaFree(gn);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&img, (size_t)pixels * 12 + 16) != cudaSuccess ||
+        cudaMalloc(&dL, (size_t)pixels * 12 + 16) != cudaSuccess ||
+        (with_backward && cudaMalloc(&gg, (size_t)desc->n * SNP_GEOM_STRIDE * 4 + 16) != cudaSuccess) ||
+        (with_backward && cudaMalloc(&gn, (size_t)desc->n * L.stride * 4 + 16) != cudaSuccess) ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, SNP_ERR_CUDA, "autotune: allocation failed");
+    }
+    k_fill_f32<<<(unsigned)((pixels * 3 + 255) / 256), 256, 0, st>>>(dL, pixels * 3, 1e-3f);
+    note_launch();
+    snp_grad_ptrs gp{gg, gn};
+    float best_t = 1e30f;
+    snp_config best_c = b;
+    const int sizes[3] = {8, 16, 32};
+    for (int ti = 0; ti < 3; ++ti) {
+        const int ts = sizes[ti];
+        const int dch = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts);
+        const int chunks[2] = {dch, dch / 2 > 0 ? dch / 2 : 1};
+        for (int ci = 0; ci < (chunks[1] == chunks[0] ? 1 : 2); ++ci) {
+            snp_config c = b;
+            c.tile_size = ts;
+            c.chunk = chunks[ci];
+            float t = 0.0f;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                int64_t tok = 0;
+                if (rep == 1) cudaEventRecord(e0, st);
+                ok = snp_render_forward(ctx, desc, scene, cams, n_cams, &c, img, &tok, stream) == SNP_OK;
+                if (ok && with_backward) ok = snp_render_backward(ctx, tok, desc, scene, dL, &gp, stream) == SNP_OK;
+            }
+            if (!ok) continue;  // e.g. a chunk the shared memory cannot hold
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cleanup();
+                return fail(ctx, SNP_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+            cudaEventElapsedTime(&t, e0, e1);
+            t *= 0.5f;
+            if (t < best_t) {
+                best_t = t;
+                best_c = c;
+            }
+        }
+    }
+    cleanup();
+    if (best_t >= 1e30f) return fail(ctx, SNP_ERR_UNSUPPORTED, "autotune: no configuration ran");
+    *best = best_c;
+    *best_ms = best_t;
     return SNP_OK;
 }
 

@@ -29,6 +29,7 @@ int64_t sort_hist_words(int64_t n_bound);
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_n,
                 int64_t n_bound, int nbits, uint32_t *hist, uint32_t *hist_scan, uint32_t *scan_tmp,
                 cudaStream_t st);
+void launch_clamp_count(const uint32_t *total, int64_t cap, uint32_t *out, cudaStream_t st);
 void launch_tile_ranges(const uint64_t *keys, const uint32_t *d_n, int64_t n_bound, uint2 *ranges, cudaStream_t st);
 
 // Arguments of the per-tile rasterizer (forward and backward).
@@ -59,16 +60,27 @@ struct RasterArgs {
     float *g_net;             // [n][stride] float32
     float *g_view;            // [V*n][16] per (view, primitive) geometry intermediates
     float *g_h0;              // [n][n_c] gradient of the folded first-layer bias
+    // persistent scheduling
+    int *work_counter;        // next queue item (zeroed before each launch)
+    const uint32_t *queue;    // tile ids ordered by decreasing list length (NULL: 0..n_tiles-1)
 };
 
-// snp_raster_fwd.cu / snp_raster_bwd.cu
+// snp_raster_*.cu
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
 snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
-size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk);
-int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward);
-int raster_bwd_default_chunk(int nc, int n_sigma);
+size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);
+size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);
+int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts);
+snp_status launch_fwd_ts8(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
+snp_status launch_fwd_ts16(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
+snp_status launch_fwd_ts32(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
+snp_status launch_bwd_ts8(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
+snp_status launch_bwd_ts16(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
+snp_status launch_bwd_ts32(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
+void launch_tile_queue(const uint2 *ranges, int64_t n_tiles, uint64_t *qkeys, uint32_t *qvals, uint32_t *d_n,
+                       cudaStream_t st);
 
 // snp_grad.cu
 void launch_project_bwd(const float *geom, int64_t n, const View *views, int n_views, const float *g_view,

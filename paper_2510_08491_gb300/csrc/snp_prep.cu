@@ -484,6 +484,20 @@ void launch_emit(const int4 *trect, const uint32_t *counts, const uint32_t *offs
     note_launch();
 }
 
+// Number of keys the sort and the ranges may touch: the emitted total, clamped to
+// the key capacity (an overflow is flagged by k_emit and reported on the host).
+__global__ void k_clamp_count(const uint32_t *__restrict__ total, int64_t cap, uint32_t *__restrict__ out)
+{
+    const uint32_t t = *total;
+    *out = (int64_t)t > cap ? (uint32_t)cap : t;
+}
+
+void launch_clamp_count(const uint32_t *total, int64_t cap, uint32_t *out, cudaStream_t st)
+{
+    k_clamp_count<<<1, 1, 0, st>>>(total, cap, out);
+    note_launch();
+}
+
 void launch_tile_ranges(const uint64_t *keys, const uint32_t *d_n, int64_t n_bound, uint2 *ranges, cudaStream_t st)
 {
     if (n_bound <= 0) return;

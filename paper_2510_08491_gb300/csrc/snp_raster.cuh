@@ -267,12 +267,27 @@ __device__ __forceinline__ void warp_prefix64(const int *count, int n, int *pre)
     else __shfl_sync(0xffffffffu, y, 31);
 }
 
-// Pixel of thread `tid` inside a 16 x 16 tile: warps cover 8 x 4 blocks.
-__device__ __forceinline__ void tile_pixel16(int tid, int &lx, int &ly)
+// Tile shapes: TS x TS pixels, NT threads, PPT pixels per thread.  Warps always
+// cover 8 x 4 pixel blocks; pixel slot = k * NT + tid for the thread's k-th pixel.
+template <int TS>
+struct TileCfg {
+    static constexpr int NPIX = TS * TS;
+    static constexpr int NT = TS == 8 ? 64 : 256;
+    static constexpr int PPT = NPIX / NT;
+    static constexpr int MIN_BLOCKS = TS == 8 ? 4 : 2;
+};
+
+template <int TS>
+__device__ __forceinline__ void tile_pixel(int tid, int k, int &lx, int &ly)
 {
     const int w = tid >> 5, l = tid & 31;
-    lx = (w & 1) * 8 + (l & 7);
-    ly = (w >> 1) * 4 + (l >> 3);
+    if constexpr (TS == 8) {
+        lx = l & 7;
+        ly = w * 4 + (l >> 3);
+    } else {
+        lx = (w & 1) * 8 + (l & 7) + (TS == 32 ? (k & 1) * 16 : 0);
+        ly = (w >> 1) * 4 + (l >> 3) + (TS == 32 ? (k >> 1) * 16 : 0);
+    }
 }
 
 __device__ __forceinline__ int find_view(const View *views, int n_views, int tile)

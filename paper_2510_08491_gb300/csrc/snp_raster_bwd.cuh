@@ -1,6 +1,7 @@
 // snp_raster_bwd.cu -- backward per-tile rasterizer.
 //
-// One CTA per 16 x 16 tile, one thread per pixel.  Each pixel replays its list
+// Persistent CTAs take tiles from the same length-ordered queue as the forward.
+// Each pixel replays its list
 // front to back up to the number of entries the forward walked, recomputing
 // alpha_hat, alpha and the colour of every composited entry.  With the forward's
 // final colour C (no background) and optical depth tau_f:
@@ -13,6 +14,8 @@
 // reduced across each warp by a 32-value reduce-scatter, accumulated per list
 // entry in shared memory across the warps, and added to the caller's gradient
 // arrays with one global atomic per parameter per (tile, primitive).
+#pragma once
+
 #include "snp_raster.cuh"
 
 namespace snp {
@@ -316,246 +319,234 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
     }
 }
 
-template <int NC, int FORM, bool BF16>
-__global__ void __launch_bounds__(kRasterThreads, 1) k_raster_bwd(RasterArgs a)
+template <int TS>
+__host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk)
 {
+    constexpr int NPIX = TileCfg<TS>::NPIX;
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 + (size_t)NPIX * (9 * 4 + 2 * 2);
+    return NPIX * 16 + (size_t)chunk * per_entry;
+}
+
+template <int TS, int NC, int FORM, bool BF16>
+__global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
+{
+    constexpr int NT = TileCfg<TS>::NT;
+    constexpr int NPIX = TileCfg<TS>::NPIX;
+    constexpr int PPT = TileCfg<TS>::PPT;
     extern __shared__ float4 smem4[];
-    constexpr int NT = kRasterThreads;
     const int CH = a.chunk;
     const int ns = a.n_sigma;
     const int es = entry_stride(ns, NC);
     const int vg = grad_stride(ns, NC);
-    float4 *s_d = smem4;                                   // [NT] pixel rays
-    float *sm = reinterpret_cast<float *>(smem4 + NT);     // [CH][es] staged entries
+    float4 *s_d = smem4;                                   // [NPIX] pixel rays
+    float *sm = reinterpret_cast<float *>(smem4 + NPIX);   // [CH][es] staged entries
     float *acc = sm + CH * es;                             // [CH][vg] per-entry gradient sums
-    float *s_ah = acc + CH * vg;                           // [CH][NT] alpha_hat, then dL/dalpha_hat
-    float *s_w = s_ah + CH * NT;                           // [CH][NT] weights (-1: not composited)
-    float *s_tn = s_w + CH * NT;                           // [CH][NT] transmittance after the entry
-    float *s_col = s_tn + CH * NT;                         // [3][CH][NT] colours
-    float *s_gc = s_col + 3 * CH * NT;                     // [3][CH][NT] dL/dcolour
-    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_gc + 3 * CH * NT);  // [CH][NT]
-    uint16_t *s_al = s_hl + CH * NT;                       // [CH][NT]
+    float *s_ah = acc + CH * vg;                           // [CH][NPIX] alpha_hat, then dL/dalpha_hat
+    float *s_w = s_ah + CH * NPIX;                         // [CH][NPIX] weights (-1: not composited)
+    float *s_tn = s_w + CH * NPIX;                         // [CH][NPIX] transmittance after the entry
+    float *s_col = s_tn + CH * NPIX;                       // [3][CH][NPIX] colours
+    float *s_gc = s_col + 3 * CH * NPIX;                   // [3][CH][NPIX] dL/dcolour
+    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_gc + 3 * CH * NPIX);  // [CH][NPIX]
+    uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
     __shared__ uint32_t s_gid[kMaxChunk];
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65];
-    __shared__ int s_view;
+    __shared__ int s_view, s_item;
     __shared__ uint32_t s_maxwalk;
 
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
-    if (tid == 0) {
-        s_view = find_view(a.views, a.n_views, tile);
-        s_maxwalk = 0;
-    }
-    __syncthreads();
-    const int v = s_view;
-    const View &V = a.views[v];
-    const int lt = tile - V.tile_off;
-    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-    int lx, ly;
-    tile_pixel16(tid, lx, ly);
-    const int px = tx * 16 + lx, py = ty * 16 + ly;
-    const bool inside = px < V.width && py < V.height;
-    const float3 d = pixel_ray(V, px, py);
-    s_d[tid] = make_float4(d.x, d.y, d.z, 0.0f);
-    const uint2 rg = a.ranges[tile];
-    const int64_t vn = (int64_t)v * a.n;
+    const unsigned lane = lane_id();
+    const int wid = tid >> 5;
     const float w0 = a.omega0;
     for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
 
-    const int64_t p = V.pix_off + (int64_t)py * V.width + px;
-    float3 Cf = make_float3(0.f, 0.f, 0.f), dL = make_float3(0.f, 0.f, 0.f);
-    float tau_f = 0.0f;
-    uint32_t nwalk = 0;
-    if (inside) {
-        const float4 s4 = a.px_state[p];
-        Cf = make_float3(s4.x, s4.y, s4.z);
-        tau_f = s4.w;
-        nwalk = a.px_nwalk[p];
-        dL = make_float3(a.dL_dimage[3 * p + 0], a.dL_dimage[3 * p + 1], a.dL_dimage[3 * p + 2]);
-        atomicMax(&s_maxwalk, nwalk);
-    }
-    const float bgdot = __expf(-tau_f) * (dL.x * a.bg[0] + dL.y * a.bg[1] + dL.z * a.bg[2]);
-    float tau = 0.0f;
-    float3 pref = make_float3(0.f, 0.f, 0.f);
-    const unsigned lane = lane_id();
-    const int wid = tid >> 5;
-    __syncthreads();
-    const uint32_t maxwalk = s_maxwalk;
-
-    for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += CH) {
-        const int cnt = min((int)(rg.y - c0), CH);
-        __syncthreads();
-        if (tid < cnt) {
-            s_gid[tid] = a.vals[c0 + tid];
-            s_nh[tid] = 0;
-            s_na[tid] = 0;
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(a.work_counter, 1);
+            s_maxwalk = 0;
         }
         __syncthreads();
-        stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
+        const int item = s_item;
+        if (item >= a.n_tiles) break;
+        const int tile = a.queue ? (int)a.queue[item] : item;
+        if (tid == 0) s_view = find_view(a.views, a.n_views, tile);
         __syncthreads();
-
-        // P1: hits among the entries this pixel walked in the forward
-        for (int e = 0; e < cnt; ++e) {
-            const uint32_t pos = c0 - rg.x + e;
-            const bool hit = pos < nwalk && hit_test(sm + e * es, d);
-            s_ah[e * NT + tid] = 0.0f;
-            list_append(hit, (uint16_t)tid, &s_nh[e], s_hl + e * NT);
-        }
-        __syncthreads();
-        if (tid < 32) warp_prefix64(s_nh, cnt, s_ph);
-        __syncthreads();
-        // P2: alpha_hat of every hit
-        {
-            const int nh = s_ph[cnt];
-            int e = 0;
-            for (int q = tid; q < nh; q += NT) {
-                while (q >= s_ph[e + 1]) ++e;
-                const int pix = s_hl[e * NT + (q - s_ph[e])];
-                const float *R = sm + e * es;
-                const float4 dd = s_d[pix];
-                const float3 dv = make_float3(dd.x, dd.y, dd.z);
-                Hit h;
-                float ah = 0.0f;
-                if (intersect(R, dv, h)) ah = integral<FORM>(R, R + kRecFloats, ns, dv, h);
-                s_ah[e * NT + pix] = ah;
+        const int v = s_view;
+        const View &V = a.views[v];
+        const int lt = tile - V.tile_off;
+        const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+        float3 d[PPT], Cf[PPT], dL[PPT], pref[PPT];
+        float tau[PPT], bgdot[PPT];
+        uint32_t nwalk[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            int lx, ly;
+            tile_pixel<TS>(tid, k, lx, ly);
+            const int px = tx * TS + lx, py = ty * TS + ly;
+            const bool inside = px < V.width && py < V.height;
+            d[k] = pixel_ray(V, px, py);
+            s_d[k * NT + tid] = make_float4(d[k].x, d[k].y, d[k].z, 0.0f);
+            Cf[k] = make_float3(0.f, 0.f, 0.f);
+            dL[k] = make_float3(0.f, 0.f, 0.f);
+            pref[k] = make_float3(0.f, 0.f, 0.f);
+            float tau_f = 0.0f;
+            nwalk[k] = 0;
+            if (inside) {
+                const int64_t p = V.pix_off + (int64_t)py * V.width + px;
+                const float4 s4 = a.px_state[p];
+                Cf[k] = make_float3(s4.x, s4.y, s4.z);
+                tau_f = s4.w;
+                nwalk[k] = a.px_nwalk[p];
+                dL[k] = make_float3(a.dL_dimage[3 * p + 0], a.dL_dimage[3 * p + 1], a.dL_dimage[3 * p + 2]);
+                atomicMax(&s_maxwalk, nwalk[k]);
             }
+            bgdot[k] = __expf(-tau_f) * (dL[k].x * a.bg[0] + dL[k].y * a.bg[1] + dL[k].z * a.bg[2]);
+            tau[k] = 0.0f;
         }
+        const uint2 rg = a.ranges[tile];
+        const int64_t vn = (int64_t)v * a.n;
         __syncthreads();
-        // P3: replay of the compositing weights
-        for (int e = 0; e < cnt; ++e) {
-            const uint32_t pos = c0 - rg.x + e;
-            const float ah = s_ah[e * NT + tid];
-            const bool act = pos < nwalk && ah > 0.0f;
-            if (act) {
-                const float Ti = __expf(-tau);
-                s_w[e * NT + tid] = Ti * (1.0f - __expf(-ah));
-                tau += ah;
-                s_tn[e * NT + tid] = __expf(-tau);
-            } else {
-                s_w[e * NT + tid] = -1.0f;
+        const uint32_t maxwalk = s_maxwalk;
+
+        for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += CH) {
+            const int cnt = min((int)(rg.y - c0), CH);
+            __syncthreads();
+            if (tid < cnt) {
+                s_gid[tid] = a.vals[c0 + tid];
+                s_nh[tid] = 0;
+                s_na[tid] = 0;
             }
-            list_append(act, (uint16_t)tid, &s_na[e], s_al + e * NT);
-        }
-        __syncthreads();
-        if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
-        __syncthreads();
-        // P4: colour of every composited pair
-        {
-            const int na = s_pa[cnt];
-            int e = 0;
-            for (int q = tid; q < na; q += NT) {
-                while (q >= s_pa[e + 1]) ++e;
-                const int pix = s_al[e * NT + (q - s_pa[e])];
-                const float *R = sm + e * es;
-                float3 col;
-                if constexpr (NC == 0) {
-                    col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
-                } else {
-                    const float4 dd = s_d[pix];
-                    col = mlp_color<NC>(R + kRecFloats + den_stride(ns), make_float3(dd.x, dd.y, dd.z));
+            __syncthreads();
+            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
+            __syncthreads();
+
+            // P1: hits among the entries this pixel walked in the forward
+            for (int e = 0; e < cnt; ++e) {
+                const uint32_t pos = c0 - rg.x + e;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const bool hit = pos < nwalk[k] && hit_test(sm + e * es, d[k]);
+                    s_ah[e * NPIX + k * NT + tid] = 0.0f;
+                    list_append(hit, (uint16_t)(k * NT + tid), &s_nh[e], s_hl + e * NPIX);
                 }
-                s_col[(0 * CH + e) * NT + pix] = col.x;
-                s_col[(1 * CH + e) * NT + pix] = col.y;
-                s_col[(2 * CH + e) * NT + pix] = col.z;
+            }
+            __syncthreads();
+            if (tid < 32) warp_prefix64(s_nh, cnt, s_ph);
+            __syncthreads();
+            // P2: alpha_hat of every hit
+            {
+                const int nh = s_ph[cnt];
+                int e = 0;
+                for (int q = tid; q < nh; q += NT) {
+                    while (q >= s_ph[e + 1]) ++e;
+                    const int pix = s_hl[e * NPIX + (q - s_ph[e])];
+                    const float *R = sm + e * es;
+                    const float4 dd = s_d[pix];
+                    const float3 dv = make_float3(dd.x, dd.y, dd.z);
+                    Hit h;
+                    float ah = 0.0f;
+                    if (intersect(R, dv, h)) ah = integral<FORM>(R, R + kRecFloats, ns, dv, h);
+                    s_ah[e * NPIX + pix] = ah;
+                }
+            }
+            __syncthreads();
+            // P3: replay of the compositing weights
+            for (int e = 0; e < cnt; ++e) {
+                const uint32_t pos = c0 - rg.x + e;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const int slot = k * NT + tid;
+                    const float ah = s_ah[e * NPIX + slot];
+                    const bool act = pos < nwalk[k] && ah > 0.0f;
+                    if (act) {
+                        const float Ti = __expf(-tau[k]);
+                        s_w[e * NPIX + slot] = Ti * (1.0f - __expf(-ah));
+                        tau[k] += ah;
+                        s_tn[e * NPIX + slot] = __expf(-tau[k]);
+                    } else {
+                        s_w[e * NPIX + slot] = -1.0f;
+                    }
+                    list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
+                }
+            }
+            __syncthreads();
+            if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
+            __syncthreads();
+            // P4: colour of every composited pair
+            {
+                const int na = s_pa[cnt];
+                int e = 0;
+                for (int q = tid; q < na; q += NT) {
+                    while (q >= s_pa[e + 1]) ++e;
+                    const int pix = s_al[e * NPIX + (q - s_pa[e])];
+                    const float *R = sm + e * es;
+                    float3 col;
+                    if constexpr (NC == 0) {
+                        col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
+                    } else {
+                        const float4 dd = s_d[pix];
+                        col = mlp_color<NC>(R + kRecFloats + den_stride(ns), make_float3(dd.x, dd.y, dd.z));
+                    }
+                    s_col[(0 * CH + e) * NPIX + pix] = col.x;
+                    s_col[(1 * CH + e) * NPIX + pix] = col.y;
+                    s_col[(2 * CH + e) * NPIX + pix] = col.z;
+                }
+            }
+            __syncthreads();
+            // P5: dL/dalpha_hat = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg and dL/dc_i = w_i dL
+            for (int e = 0; e < cnt; ++e) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const int slot = k * NT + tid;
+                    const float w = s_w[e * NPIX + slot];
+                    if (w >= 0.0f) {
+                        const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + slot],
+                                                       s_col[(1 * CH + e) * NPIX + slot],
+                                                       s_col[(2 * CH + e) * NPIX + slot]);
+                        const float Tn = s_tn[e * NPIX + slot];
+                        pref[k].x = fmaf(w, col.x, pref[k].x);
+                        pref[k].y = fmaf(w, col.y, pref[k].y);
+                        pref[k].z = fmaf(w, col.z, pref[k].z);
+                        s_ah[e * NPIX + slot] = dL[k].x * (Tn * col.x - (Cf[k].x - pref[k].x)) +
+                                                dL[k].y * (Tn * col.y - (Cf[k].y - pref[k].y)) +
+                                                dL[k].z * (Tn * col.z - (Cf[k].z - pref[k].z)) - bgdot[k];
+                        s_gc[(0 * CH + e) * NPIX + slot] = dL[k].x * w;
+                        s_gc[(1 * CH + e) * NPIX + slot] = dL[k].y * w;
+                        s_gc[(2 * CH + e) * NPIX + slot] = dL[k].z * w;
+                    }
+                }
+            }
+            if (tid < cnt) s_nb[tid] = (s_na[tid] + 31) >> 5;
+            __syncthreads();
+            if (tid < 32) warp_prefix64(s_nb, cnt, s_pb);
+            __syncthreads();
+            // P6: per-pair gradients in warp batches of one entry each
+            {
+                const int nb = s_pb[cnt];
+                int e = 0;
+                for (int b = wid; b < nb; b += NT / 32) {
+                    while (b >= s_pb[e + 1]) ++e;
+                    const int kk = (b - s_pb[e]) * 32 + (int)lane;
+                    const bool valid = kk < s_na[e];
+                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
+                    const float4 dd = s_d[pix];
+                    const float *R = sm + e * es;
+                    const float3 g_c = make_float3(s_gc[(0 * CH + e) * NPIX + pix], s_gc[(1 * CH + e) * NPIX + pix],
+                                                   s_gc[(2 * CH + e) * NPIX + pix]);
+                    const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + pix], s_col[(1 * CH + e) * NPIX + pix],
+                                                   s_col[(2 * CH + e) * NPIX + pix]);
+                    pair_backward<NC, FORM>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0,
+                                            make_float3(dd.x, dd.y, dd.z), valid, s_ah[e * NPIX + pix], g_c, col,
+                                            acc + e * vg);
+                }
+            }
+            __syncthreads();
+            for (int e = 0; e < cnt; ++e) {
+                const int64_t gid = s_gid[e];
+                flush_entry<NC>(a, acc + e * vg, gid - vn, gid, vg, tid, NT);
             }
         }
         __syncthreads();
-        // P5: dL/dalpha_hat = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg and dL/dc_i = w_i dL
-        for (int e = 0; e < cnt; ++e) {
-            const float w = s_w[e * NT + tid];
-            if (w >= 0.0f) {
-                const float3 col = make_float3(s_col[(0 * CH + e) * NT + tid], s_col[(1 * CH + e) * NT + tid],
-                                               s_col[(2 * CH + e) * NT + tid]);
-                const float Tn = s_tn[e * NT + tid];
-                pref.x = fmaf(w, col.x, pref.x);
-                pref.y = fmaf(w, col.y, pref.y);
-                pref.z = fmaf(w, col.z, pref.z);
-                s_ah[e * NT + tid] = dL.x * (Tn * col.x - (Cf.x - pref.x)) + dL.y * (Tn * col.y - (Cf.y - pref.y)) +
-                                     dL.z * (Tn * col.z - (Cf.z - pref.z)) - bgdot;
-                s_gc[(0 * CH + e) * NT + tid] = dL.x * w;
-                s_gc[(1 * CH + e) * NT + tid] = dL.y * w;
-                s_gc[(2 * CH + e) * NT + tid] = dL.z * w;
-            }
-        }
-        if (tid < cnt) s_nb[tid] = (s_na[tid] + 31) >> 5;
-        __syncthreads();
-        if (tid < 32) warp_prefix64(s_nb, cnt, s_pb);
-        __syncthreads();
-        // P6: per-pair gradients in warp batches of one entry each
-        {
-            const int nb = s_pb[cnt];
-            int e = 0;
-            for (int b = wid; b < nb; b += NT / 32) {
-                while (b >= s_pb[e + 1]) ++e;
-                const int k = (b - s_pb[e]) * 32 + (int)lane;
-                const bool valid = k < s_na[e];
-                const int pix = valid ? s_al[e * NT + k] : 0;
-                const float4 dd = s_d[pix];
-                const float *R = sm + e * es;
-                const float3 g_c = make_float3(s_gc[(0 * CH + e) * NT + pix], s_gc[(1 * CH + e) * NT + pix],
-                                               s_gc[(2 * CH + e) * NT + pix]);
-                const float3 col = make_float3(s_col[(0 * CH + e) * NT + pix], s_col[(1 * CH + e) * NT + pix],
-                                               s_col[(2 * CH + e) * NT + pix]);
-                pair_backward<NC, FORM>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0,
-                                        make_float3(dd.x, dd.y, dd.z), valid, s_ah[e * NT + pix], g_c, col,
-                                        acc + e * vg);
-            }
-        }
-        __syncthreads();
-        for (int e = 0; e < cnt; ++e) {
-            const int64_t gid = s_gid[e];
-            flush_entry<NC>(a, acc + e * vg, gid - vn, gid, vg, tid, NT);
-        }
     }
-    (void)lane;
-}
-
-static size_t bwd_smem_bytes(int nc, int ns, int chunk)
-{
-    const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 +
-                             (size_t)kRasterThreads * (9 * 4 + 2 * 2);
-    return kRasterThreads * 16 + (size_t)chunk * per_entry;
-}
-
-int raster_bwd_default_chunk(int nc, int ns)
-{
-    int ch = 8;
-    while (ch > 1 && bwd_smem_bytes(nc, ns, ch) > 200 * 1024) --ch;
-    return ch;
-}
-
-template <int NC, int FORM, bool BF16>
-static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
-{
-    const size_t smem = bwd_smem_bytes(NC, a.n_sigma, a.chunk);
-    if (smem > 220 * 1024 || a.chunk > 64) return SNP_ERR_INVALID_ARG;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_raster_bwd<NC, FORM, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
-    }
-    if (a.n_tiles <= 0) return SNP_OK;
-    k_raster_bwd<NC, FORM, BF16><<<(unsigned)a.n_tiles, kRasterThreads, smem, st>>>(a);
-    note_launch();
-    return cudaGetLastError() == cudaSuccess ? SNP_OK : SNP_ERR_CUDA;
-}
-
-template <int NC>
-static snp_status dispatch_bwd(const RasterArgs &a, int form, int bf16, cudaStream_t st)
-{
-    if (form == SNP_FORM_STABLE)
-        return bf16 ? run_bwd<NC, 0, true>(a, st) : run_bwd<NC, 0, false>(a, st);
-    return bf16 ? run_bwd<NC, 1, true>(a, st) : run_bwd<NC, 1, false>(a, st);
-}
-
-snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
-                             cudaStream_t st)
-{
-    if (ts != 16) return SNP_ERR_UNSUPPORTED;
-    if (color_mode == SNP_COLOR_CONST) return dispatch_bwd<0>(a, form, bf16, st);
-    if (n_c == 32) return dispatch_bwd<32>(a, form, bf16, st);
-    if (n_c == 64) return dispatch_bwd<64>(a, form, bf16, st);
-    return SNP_ERR_UNSUPPORTED;
 }
 
 }  // namespace snp

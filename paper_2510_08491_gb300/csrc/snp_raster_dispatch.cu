@@ -1,0 +1,82 @@
+// snp_raster_dispatch.cu -- tile-size dispatch of the raster kernels, their
+// shared-memory sizing and default chunk, and the length-ordered tile queue.
+#include "snp_raster_bwd.cuh"
+#include "snp_raster_fwd.cuh"
+
+namespace snp {
+
+static int nc_of(int color_mode, int n_c) { return color_mode == SNP_COLOR_MLP ? n_c : 0; }
+
+size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
+{
+    const int nc = nc_of(color_mode, n_c);
+    if (ts == 8) return fwd_smem_bytes<8>(nc, n_sigma, chunk);
+    if (ts == 32) return fwd_smem_bytes<32>(nc, n_sigma, chunk);
+    return fwd_smem_bytes<16>(nc, n_sigma, chunk);
+}
+
+size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
+{
+    const int nc = nc_of(color_mode, n_c);
+    if (ts == 8) return bwd_smem_bytes<8>(nc, n_sigma, chunk);
+    if (ts == 32) return bwd_smem_bytes<32>(nc, n_sigma, chunk);
+    return bwd_smem_bytes<16>(nc, n_sigma, chunk);
+}
+
+// Largest chunk (<= 32 forward, <= 8 backward) within the shared-memory budget:
+// about half an SM for the forward (two CTAs per SM), most of one for the backward.
+int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts)
+{
+    const size_t fwd_budget = ts == 8 ? 52 * 1024 : 104 * 1024;
+    int ch = backward ? 8 : 32;
+    if (backward) {
+        while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts) > 200 * 1024) --ch;
+    } else {
+        while (ch > 1 && raster_fwd_smem(color_mode, n_c, n_sigma, ch, ts) > fwd_budget) --ch;
+    }
+    return ch;
+}
+
+snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
+                             cudaStream_t st)
+{
+    const int nc = nc_of(color_mode, n_c);
+    if (ts == 8) return launch_fwd_ts8(a, nc, form, bf16, st);
+    if (ts == 16) return launch_fwd_ts16(a, nc, form, bf16, st);
+    if (ts == 32) return launch_fwd_ts32(a, nc, form, bf16, st);
+    return SNP_ERR_UNSUPPORTED;
+}
+
+snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
+                             cudaStream_t st)
+{
+    const int nc = nc_of(color_mode, n_c);
+    if (ts == 8) return launch_bwd_ts8(a, nc, form, bf16, st);
+    if (ts == 16) return launch_bwd_ts16(a, nc, form, bf16, st);
+    if (ts == 32) return launch_bwd_ts32(a, nc, form, bf16, st);
+    return SNP_ERR_UNSUPPORTED;
+}
+
+// Queue keys: (0xffffffff - list length) so that an ascending sort puts the
+// longest tile lists first; value = tile id.
+__global__ void __launch_bounds__(256) k_tile_queue_keys(const uint2 *__restrict__ ranges, int64_t n_tiles,
+                                                         uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                         uint32_t *__restrict__ d_n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) *d_n = (uint32_t)n_tiles;
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    keys[t] = (uint64_t)(0xffffffffu - (r.y - r.x));
+    vals[t] = (uint32_t)t;
+}
+
+void launch_tile_queue(const uint2 *ranges, int64_t n_tiles, uint64_t *qkeys, uint32_t *qvals, uint32_t *d_n,
+                       cudaStream_t st)
+{
+    if (n_tiles <= 0) return;
+    k_tile_queue_keys<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(ranges, n_tiles, qkeys, qvals, d_n);
+    note_launch();
+}
+
+}  // namespace snp

@@ -1,0 +1,234 @@
+// snp_raster_fwd.cuh -- forward per-tile rasterizer ("render kernel", App. A).
+//
+// Persistent CTAs take screen tiles from a queue ordered by decreasing list
+// length.  A tile's depth-sorted list is walked in chunks staged in shared
+// memory; each chunk runs in phases so that the expensive per-pair work is done
+// by fully occupied warps:
+//   P1 (per pixel)  ray / ellipsoid test for every entry of the chunk; hits are
+//                   appended to per-entry pixel lists;
+//   P2 (per hit)    closed-form integral alpha_hat (Eq. 7/8);
+//   P3 (per pixel)  front-to-back weights w = T (1 - exp(-alpha_hat)),
+//                   T = exp(-sum alpha_hat) (Eq. 4, 9) and early termination --
+//                   transmittance does not depend on colour, so it is settled
+//                   before any colour is evaluated; composited pairs are listed;
+//   P4 (per pair)   colour MLP of every composited pair;
+//   P5 (per pixel)  C += w * colour in list order.
+// The result is the sequential front-to-back composite.  The per-pixel composited
+// colour, optical depth and number of list entries walked are saved for the
+// backward pass.
+#pragma once
+
+#include "snp_raster.cuh"
+
+namespace snp {
+
+template <int TS>
+__host__ __device__ inline size_t fwd_smem_bytes(int nc, int ns, int chunk)
+{
+    constexpr int NPIX = TileCfg<TS>::NPIX;
+    const size_t per_entry = (size_t)entry_stride(ns, nc) * 4 + NPIX * 4 /* alpha_hat */ + NPIX * 2 /* hit list */ +
+                             (nc > 0 ? NPIX * (4 + 12 + 2) /* weight, colour, list */ : 0);
+    return NPIX * 16 /* rays */ + (size_t)chunk * per_entry;
+}
+
+template <int TS, int NC, int FORM, bool BF16>
+__global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_raster_fwd(RasterArgs a)
+{
+    constexpr int NT = TileCfg<TS>::NT;
+    constexpr int NPIX = TileCfg<TS>::NPIX;
+    constexpr int PPT = TileCfg<TS>::PPT;
+    extern __shared__ float4 smem4[];
+    const int CH = a.chunk;
+    const int ns = a.n_sigma;
+    const int es = entry_stride(ns, NC);
+    float4 *s_d = smem4;                                        // [NPIX] pixel rays
+    float *sm = reinterpret_cast<float *>(smem4 + NPIX);        // [CH][es] staged entries
+    float *s_ah = sm + CH * es;                                 // [CH][NPIX] alpha_hat
+    float *s_w = s_ah + CH * NPIX;                              // [CH][NPIX] weights (MLP)
+    float *s_col = s_w + (NC > 0 ? CH * NPIX : 0);              // [3][CH][NPIX] colours (MLP)
+    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + (NC > 0 ? 3 * CH * NPIX : 0));  // [CH][NPIX]
+    uint16_t *s_al = s_hl + CH * NPIX;                          // [CH][NPIX] (MLP)
+    __shared__ uint32_t s_gid[kMaxChunk];
+    __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65];
+    __shared__ int s_view, s_item;
+
+    const int tid = threadIdx.x;
+    uint32_t n_cand = 0, n_hit = 0, n_comp = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.work_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.n_tiles) break;
+        const int tile = a.queue ? (int)a.queue[item] : item;
+        if (tid == 0) s_view = find_view(a.views, a.n_views, tile);
+        __syncthreads();
+        const int v = s_view;
+        const View &V = a.views[v];
+        const int lt = tile - V.tile_off;
+        const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+        int px[PPT], py[PPT];
+        bool inside[PPT], alive[PPT];
+        float3 d[PPT], C[PPT];
+        float tau[PPT], T[PPT];
+        uint32_t nwalk[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            int lx, ly;
+            tile_pixel<TS>(tid, k, lx, ly);
+            px[k] = tx * TS + lx;
+            py[k] = ty * TS + ly;
+            inside[k] = px[k] < V.width && py[k] < V.height;
+            d[k] = pixel_ray(V, px[k], py[k]);
+            s_d[k * NT + tid] = make_float4(d[k].x, d[k].y, d[k].z, 0.0f);
+            alive[k] = inside[k];
+            C[k] = make_float3(0.f, 0.f, 0.f);
+            tau[k] = 0.0f;
+            T[k] = 1.0f;
+            nwalk[k] = 0;
+        }
+        const uint2 rg = a.ranges[tile];
+        const int64_t vn = (int64_t)v * a.n;
+
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += CH) {
+            const int cnt = min((int)(rg.y - c0), CH);
+            __syncthreads();
+            if (tid < cnt) {
+                s_gid[tid] = a.vals[c0 + tid];
+                s_nh[tid] = 0;
+                s_na[tid] = 0;
+            }
+            __syncthreads();
+            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
+            __syncthreads();
+
+            // P1: which pixels' rays enter which ellipsoids
+            for (int e = 0; e < cnt; ++e) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    bool hit = false;
+                    if (alive[k]) {
+                        ++n_cand;
+                        hit = hit_test(sm + e * es, d[k]);
+                    }
+                    s_ah[e * NPIX + k * NT + tid] = 0.0f;
+                    list_append(hit, (uint16_t)(k * NT + tid), &s_nh[e], s_hl + e * NPIX);
+                }
+            }
+            __syncthreads();
+            if (tid < 32) warp_prefix64(s_nh, cnt, s_ph);
+            __syncthreads();
+
+            // P2: alpha_hat of every hit
+            {
+                const int nh = s_ph[cnt];
+                int e = 0;
+                for (int q = tid; q < nh; q += NT) {
+                    while (q >= s_ph[e + 1]) ++e;
+                    const int pix = s_hl[e * NPIX + (q - s_ph[e])];
+                    const float *R = sm + e * es;
+                    const float4 dd = s_d[pix];
+                    const float3 dv = make_float3(dd.x, dd.y, dd.z);
+                    Hit h;
+                    float ah = 0.0f;
+                    if (intersect(R, dv, h)) ah = integral<FORM>(R, R + kRecFloats, ns, dv, h);
+                    s_ah[e * NPIX + pix] = ah;
+                    ++n_hit;
+                }
+            }
+            __syncthreads();
+
+            // P3: compositing weights and termination, in list order
+            for (int e = 0; e < cnt; ++e) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const int slot = k * NT + tid;
+                    bool act = false;
+                    float w = 0.0f;
+                    if (alive[k]) {
+                        const float ah = s_ah[e * NPIX + slot];
+                        if (ah > 0.0f) {
+                            ++n_comp;
+                            w = T[k] * (1.0f - __expf(-ah));
+                            tau[k] += ah;
+                            T[k] = __expf(-tau[k]);
+                            nwalk[k] = c0 - rg.x + e + 1;
+                            act = true;
+                            if constexpr (NC == 0) {
+                                const float *R = sm + e * es;
+                                C[k].x = fmaf(w, R[kRecRgb + 0], C[k].x);
+                                C[k].y = fmaf(w, R[kRecRgb + 1], C[k].y);
+                                C[k].z = fmaf(w, R[kRecRgb + 2], C[k].z);
+                            }
+                            if (T[k] < a.t_min) alive[k] = false;
+                        }
+                    }
+                    if constexpr (NC > 0) {
+                        s_w[e * NPIX + slot] = act ? w : -1.0f;
+                        list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
+                    }
+                }
+            }
+
+            if constexpr (NC > 0) {
+                __syncthreads();
+                if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
+                __syncthreads();
+                // P4: colour of every composited pair
+                const int na = s_pa[cnt];
+                int e = 0;
+                for (int q = tid; q < na; q += NT) {
+                    while (q >= s_pa[e + 1]) ++e;
+                    const int pix = s_al[e * NPIX + (q - s_pa[e])];
+                    const float4 dd = s_d[pix];
+                    const float3 col =
+                        mlp_color<NC>(sm + e * es + kRecFloats + den_stride(ns), make_float3(dd.x, dd.y, dd.z));
+                    s_col[(0 * CH + e) * NPIX + pix] = col.x;
+                    s_col[(1 * CH + e) * NPIX + pix] = col.y;
+                    s_col[(2 * CH + e) * NPIX + pix] = col.z;
+                }
+                __syncthreads();
+                // P5: accumulate in list order
+                for (int e2 = 0; e2 < cnt; ++e2) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const int slot = k * NT + tid;
+                        const float w = s_w[e2 * NPIX + slot];
+                        if (w >= 0.0f) {
+                            C[k].x = fmaf(w, s_col[(0 * CH + e2) * NPIX + slot], C[k].x);
+                            C[k].y = fmaf(w, s_col[(1 * CH + e2) * NPIX + slot], C[k].y);
+                            C[k].z = fmaf(w, s_col[(2 * CH + e2) * NPIX + slot], C[k].z);
+                        }
+                    }
+                }
+            }
+            bool any_alive = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) any_alive |= alive[k];
+            if (__syncthreads_and(!any_alive)) break;
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (!inside[k]) continue;
+            const int64_t p = V.pix_off + (int64_t)py[k] * V.width + px[k];
+            a.image[3 * p + 0] = fmaf(T[k], a.bg[0], C[k].x);
+            a.image[3 * p + 1] = fmaf(T[k], a.bg[1], C[k].y);
+            a.image[3 * p + 2] = fmaf(T[k], a.bg[2], C[k].z);
+            if (a.px_state) {
+                a.px_state[p] = make_float4(C[k].x, C[k].y, C[k].z, tau[k]);
+                a.px_nwalk[p] = nwalk[k];
+            }
+        }
+        __syncthreads();
+    }
+    if (a.stats) {
+        const unsigned long long s0 = warp_sum_u64(n_cand), s1 = warp_sum_u64(n_hit), s2 = warp_sum_u64(n_comp);
+        if (lane_id() == 0) {
+            atomicAdd(a.stats + 0, s0);
+            atomicAdd(a.stats + 1, s1);
+            atomicAdd(a.stats + 2, s2);
+        }
+    }
+}
+
+}  // namespace snp

@@ -1,0 +1,105 @@
+// snp_raster_launch.cuh -- persistent launches of the raster kernels: the grid is
+// the number of CTAs that fit on the device at once, and every CTA pulls tiles
+// from the queue until it is exhausted.
+#pragma once
+
+#include "snp_raster_bwd.cuh"
+#include "snp_raster_fwd.cuh"
+
+namespace snp {
+
+constexpr size_t kSmemMax = 220 * 1024;
+
+// Raise the dynamic shared-memory limit of a kernel once per device (before any
+// stream capture: the first launch of each kernel on a device happens eagerly).
+template <typename K>
+static void allow_smem(K kern)
+{
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done & bit)) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        done |= bit;
+    }
+}
+
+template <typename K>
+static int persistent_grid(K kern, int threads, size_t smem, int64_t n_tiles)
+{
+    int dev = 0, sms = 1, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    int64_t g = (int64_t)(nb > 0 ? nb : 1) * sms;
+    if (g > n_tiles) g = n_tiles;
+    return (int)(g > 0 ? g : 1);
+}
+
+template <int TS, int NC, int FORM, bool BF16>
+static snp_status run_fwd(const RasterArgs &a, cudaStream_t st)
+{
+    const size_t smem = fwd_smem_bytes<TS>(NC, a.n_sigma, a.chunk);
+    if (smem > kSmemMax || a.chunk < 1 || a.chunk > 64) return SNP_ERR_INVALID_ARG;
+    if (a.n_tiles <= 0) return SNP_OK;
+    auto kern = k_raster_fwd<TS, NC, FORM, BF16>;
+    allow_smem(kern);
+    const int grid = persistent_grid(kern, TileCfg<TS>::NT, smem, a.n_tiles);
+    kern<<<grid, TileCfg<TS>::NT, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SNP_OK : SNP_ERR_CUDA;
+}
+
+template <int TS, int NC, int FORM, bool BF16>
+static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
+{
+    const size_t smem = bwd_smem_bytes<TS>(NC, a.n_sigma, a.chunk);
+    if (smem > kSmemMax || a.chunk < 1 || a.chunk > 64) return SNP_ERR_INVALID_ARG;
+    if (a.n_tiles <= 0) return SNP_OK;
+    auto kern = k_raster_bwd<TS, NC, FORM, BF16>;
+    allow_smem(kern);
+    const int grid = persistent_grid(kern, TileCfg<TS>::NT, smem, a.n_tiles);
+    kern<<<grid, TileCfg<TS>::NT, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SNP_OK : SNP_ERR_CUDA;
+}
+
+// Forms built for a tile size: the stable integral always, Eq. 8 literally when NAIVE.
+template <int TS, bool NAIVE>
+static snp_status dispatch_fwd(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st)
+{
+    if (form == SNP_FORM_NAIVE && !NAIVE) return SNP_ERR_UNSUPPORTED;
+#define SNP_FWD_CASE(NCV)                                                                          \
+    if (nc == NCV) {                                                                               \
+        if (form == SNP_FORM_STABLE)                                                               \
+            return bf16 ? run_fwd<TS, NCV, 0, true>(a, st) : run_fwd<TS, NCV, 0, false>(a, st);    \
+        if constexpr (NAIVE)                                                                       \
+            return bf16 ? run_fwd<TS, NCV, 1, true>(a, st) : run_fwd<TS, NCV, 1, false>(a, st);    \
+    }
+    SNP_FWD_CASE(0)
+    SNP_FWD_CASE(32)
+    SNP_FWD_CASE(64)
+#undef SNP_FWD_CASE
+    return SNP_ERR_UNSUPPORTED;
+}
+
+template <int TS, bool NAIVE>
+static snp_status dispatch_bwd(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st)
+{
+    if (form == SNP_FORM_NAIVE && !NAIVE) return SNP_ERR_UNSUPPORTED;
+#define SNP_BWD_CASE(NCV)                                                                          \
+    if (nc == NCV) {                                                                               \
+        if (form == SNP_FORM_STABLE)                                                               \
+            return bf16 ? run_bwd<TS, NCV, 0, true>(a, st) : run_bwd<TS, NCV, 0, false>(a, st);    \
+        if constexpr (NAIVE)                                                                       \
+            return bf16 ? run_bwd<TS, NCV, 1, true>(a, st) : run_bwd<TS, NCV, 1, false>(a, st);    \
+    }
+    SNP_BWD_CASE(0)
+    SNP_BWD_CASE(32)
+    SNP_BWD_CASE(64)
+#undef SNP_BWD_CASE
+    return SNP_ERR_UNSUPPORTED;
+}
+
+}  // namespace snp

@@ -149,6 +149,86 @@ class Renderer:
                                            int(max_keys)))
 
 
+    def autotune(self, ps: PackedScene, cams, cfg: Optional[L.Config] = None, backward: bool = True,
+                 cache_path: Optional[str] = None) -> L.Config:
+        """Pick tile size and staging chunk by timing them on this scene (snp_autotune).
+        With cache_path, results are memoised in a JSON file keyed by GPU and shapes."""
+        import json
+        import os
+        cfg = cfg or L.make_config()
+        key = "|".join(str(x) for x in (torch.cuda.get_device_name(self.device), ps.n, ps.desc.n_sigma,
+                                        ps.desc.color_mode, ps.desc.n_c, ps.desc.weight_dtype, cfg.integral_form,
+                                        int(backward), tuple((c.width, c.height) for c in cams)))
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            try:
+                cache = json.load(open(cache_path))
+            except Exception:
+                cache = {}
+        if key in cache:
+            best = L.make_config(tile_size=cache[key]["tile_size"], chunk=cache[key]["chunk"], form=cfg.integral_form,
+                                 t_min=cfg.t_min, bg=tuple(cfg.bg))
+            best.flags = cfg.flags
+            return best
+        best = L.Config()
+        ms = C.c_float()
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        sp = ps.ptrs()
+        carr = L.make_cameras(cams)
+        self.ctx.check(L.lib().snp_autotune(self.ctx.handle, C.byref(ps.desc), C.byref(sp), carr, len(cams),
+                                            C.byref(cfg), int(backward), C.byref(best), C.byref(ms), C.c_void_p(st)))
+        best.flags = cfg.flags
+        if cache_path:
+            cache[key] = {"tile_size": best.tile_size, "chunk": best.chunk, "ms": ms.value}
+            tmp = cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, cache_path)
+        self.last_autotune_ms = ms.value
+        return best
+
+
+class GraphStep:
+    """Forward + backward of a fixed scene layout and camera set captured into one CUDA graph.
+
+    The context reserves every workspace buffer first (no allocation and no host
+    synchronisation inside the graph); the number of tile keys is bounded by
+    max_keys and an overflow is reported by Renderer.stats().  Replay reads the
+    current contents of ps.geom / ps.net and dL and writes image / grads."""
+
+    def __init__(self, renderer: Renderer, ps: PackedScene, cams, cfg: L.Config, max_keys: int,
+                 dL: torch.Tensor, backward: bool = True):
+        self.r, self.ps, self.cams, self.cfg = renderer, ps, cams, cfg
+        renderer.reserve(ps, cams, cfg, max_keys)
+        P = renderer.image_size(cams)
+        self.image = torch.empty((P, 3), dtype=torch.float32, device=renderer.device)
+        self.dL = dL
+        self.g_geom = torch.zeros_like(ps.geom) if backward else None
+        self.g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device=ps.net.device) if backward else None
+        self.backward = backward
+        side = torch.cuda.Stream(renderer.device)
+        side.wait_stream(torch.cuda.current_stream(renderer.device))
+        with torch.cuda.stream(side):
+            self._body()  # warm-up outside the capture (sets kernel attributes)
+        torch.cuda.current_stream(renderer.device).wait_stream(side)
+        torch.cuda.synchronize(renderer.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body()
+        self.token = renderer.token
+
+    def _body(self):
+        if self.backward:
+            self.g_geom.zero_()
+            self.g_net.zero_()
+        self.r.forward(self.ps, self.cams, self.cfg, out=self.image)
+        if self.backward:
+            self.r.backward(self.ps, self.dL, self.g_geom, self.g_net)
+
+    def replay(self):
+        self.graph.replay()
+
+
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, geom, net, renderer, ps, cams, cfg):

@@ -34,10 +34,14 @@ def R():
 
 
 def _gpu_grads(R, scene, cams, dL, form=0, t_min=1e-4, bg=(0.0, 0.0, 0.0)):
+    return _gpu_grads_cfg(R, scene, cams, dL, form=form, t_min=t_min, bg=bg)
+
+
+def _gpu_grads_cfg(R, scene, cams, dL, **cfg_kw):
     from paper_2510_08491_gb300 import _lib as L
     from paper_2510_08491_gb300.render import pack_scene, unpack_geom_grad, unpack_net_grad
     ps = pack_scene(scene)
-    cfg = L.make_config(form=form, t_min=t_min, bg=bg)
+    cfg = L.make_config(**cfg_kw)
     R.forward(ps, cams, cfg)
     g_geom = torch.zeros_like(ps.geom)
     g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device=ps.net.device)

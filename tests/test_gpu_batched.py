@@ -1,0 +1,137 @@
+"""GPU checks of the batched form: tile sizes 8/16/32, the length-ordered
+persistent launches over many views of uneven size, CUDA-graph capture of the
+whole forward + backward with reserved capacity, the capacity overflow report,
+and the autotuner.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2510_08491_gb300 import synth
+from gpu_util import assert_image_close, grad_rel_errors, oracle_images
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2510_08491_gb300 import build
+    build.build()
+    from paper_2510_08491_gb300.render import Renderer
+    return Renderer(0)
+
+
+def _uneven_views(n, radius, seed=0):
+    g = np.random.default_rng(seed)
+    res = [synth.RESOLUTIONS[i] for i in g.integers(0, 4, size=n)]
+    res = [(w // 4, h // 4) for (w, h) in res]  # a quarter of the batched workload's sizes
+    return synth.fibonacci_cameras(n, radius, res)
+
+
+@pytest.mark.parametrize("color", ["const", "mlp"])
+def test_tile_sizes_give_identical_images(R, oracle_lib, color):
+    """The per-pixel work does not depend on the tiling: images are bit-identical
+    for 8, 16 and 32 pixel tiles, and keys match the oracle for each tile size."""
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene
+    O = oracle_lib
+    sc = synth.make_scene(2500, seed=31, center_half=2.0, n_sigma=16, color=color, n_c=32)
+    cams = _uneven_views(5, 7.0)
+    ps = pack_scene(sc)
+    imgs = {}
+    for ts in (8, 16, 32):
+        img = R.forward(ps, cams, L.make_config(tile_size=ts)).cpu().numpy()
+        keys, vals = R.debug_keys()
+        tl = O.tile_keys(sc, cams, ts)
+        assert np.array_equal(keys, tl.keys) and np.array_equal(vals, tl.vals), ts
+        imgs[ts] = img
+    assert np.array_equal(imgs[8], imgs[16]) and np.array_equal(imgs[32], imgs[16])
+    ref, flags, _, _ = oracle_images(O, sc, cams)
+    assert_image_close(imgs[16], ref, flags)
+
+
+@pytest.mark.parametrize("ts", [8, 32])
+def test_tile_size_backward(R, oracle_lib, ts):
+    from test_gpu_backward import _check, _dl, _gpu_grads_cfg, _oracle_grads
+    O = oracle_lib
+    sc = synth.make_scene(1200, seed=3, center_half=1.5, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
+    cams = [synth.look_at_camera((0.0, 0.5, 6.0), (0, 0, 0), 72, 56)]
+    dLv = _dl(O, sc, cams, 3)
+    g = _gpu_grads_cfg(R, sc, cams, np.concatenate(dLv), tile_size=ts)
+    gref = _oracle_grads(O, sc, cams, dLv)
+    _check(g, gref, sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
+
+
+def test_uneven_views_bf16_mlp64(R, oracle_lib):
+    """16 views of uneven size, N_sigma = 32, N_c = 64, BF16 weights (the batched
+    workload's shapes on a smaller scene): keys bit-exact, images within 1e-4."""
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene
+    O = oracle_lib
+    sc = synth.make_scene(6000, seed=41, center_half=3.0, n_sigma=32, color="mlp", n_c=64).to_bf16()
+    cams = _uneven_views(16, 10.0, seed=7)
+    ps = pack_scene(sc)
+    img = R.forward(ps, cams, L.make_config()).cpu().numpy()
+    keys, vals = R.debug_keys()
+    ref, flags, tl, _ = oracle_images(O, sc, cams)
+    assert np.array_equal(keys, tl.keys) and np.array_equal(vals, tl.vals)
+    assert_image_close(img, ref, flags)
+
+
+def test_graph_capture_matches_eager(R):
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import GraphStep, Renderer, pack_scene
+    sc = synth.make_scene(3000, seed=51, center_half=2.0, n_sigma=16, color="mlp", n_c=32)
+    cams = _uneven_views(4, 7.0, seed=3)
+    r = Renderer(0)
+    ps = pack_scene(sc)
+    cfg = L.make_config()
+    P = r.image_size(cams)
+    dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    img0 = r.forward(ps, cams, cfg).clone()
+    gg0 = torch.zeros_like(ps.geom)
+    gn0 = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
+    r.backward(ps, dL, gg0, gn0)
+    torch.cuda.synchronize()
+    K = r.stats().n_keys
+    step = GraphStep(r, ps, cams, cfg, max_keys=K + 1024, dL=dL)
+    for _ in range(2):
+        step.image.zero_()
+        step.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(step.image, img0)
+        for a, b in ((step.g_geom, gg0), (step.g_net, gn0)):
+            err = (a - b).abs().max().item()
+            assert err <= 1e-5 * (b.abs().max().item() + 1e-12), err
+    assert r.stats().n_keys == K
+
+
+def test_capacity_overflow_is_reported(R):
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import Renderer, pack_scene
+    sc = synth.make_scene(2000, seed=61, center_half=2.0, n_sigma=8)
+    cams = synth.ring_cameras(2, 6.0, 160, 120)
+    r = Renderer(0)
+    ps = pack_scene(sc)
+    cfg = L.make_config()
+    r.reserve(ps, cams, cfg, max_keys=100)
+    r.forward(ps, cams, cfg)  # reserved: no growth, keys beyond capacity are dropped and flagged
+    with pytest.raises(L.SnpError) as ei:
+        r.stats()
+    assert ei.value.status == L.SNP_ERR_CAPACITY
+
+
+def test_autotune_picks_a_working_configuration(R, tmp_path):
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene
+    sc = synth.make_scene(4000, seed=71, center_half=2.0, n_sigma=16, color="mlp", n_c=32)
+    cams = _uneven_views(3, 7.0, seed=9)
+    ps = pack_scene(sc)
+    cache = str(tmp_path / "tune.json")
+    best = R.autotune(ps, cams, L.make_config(), backward=True, cache_path=cache)
+    assert best.tile_size in (8, 16, 32) and best.chunk >= 1
+    again = R.autotune(ps, cams, L.make_config(), backward=True, cache_path=cache)
+    assert (again.tile_size, again.chunk) == (best.tile_size, best.chunk)
+    img = R.forward(ps, cams, best).cpu().numpy()
+    ref = R.forward(ps, cams, L.make_config()).cpu().numpy()
+    assert np.array_equal(img, ref)
