@@ -147,6 +147,10 @@ typedef struct {
  * that snp_stage_times can report per-stage device time (a few microseconds of
  * event overhead per call). */
 #define SNP_FLAG_STAGE_TIMING 1
+/* snp_config.flags: hand tiles to the persistent raster CTAs in order of
+ * decreasing list length instead of row-major order (trades L2 reuse of
+ * primitive records between neighbouring tiles for a shorter tail). */
+#define SNP_FLAG_LENGTH_QUEUE 2
 
 /* Stages reported by snp_stage_times. */
 enum {

@@ -2,6 +2,7 @@
 // forward/backward orchestration on one stream.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -243,6 +244,29 @@ static snp_status build_views(snp_context *ctx, const snp_camera *cams, int n_ca
         V.tile_off = (int32_t)t;
         V.pad_ = 0;
         V.pix_off = p;
+        {
+            // (R_wc^T)^-1 by the adjugate, in FP64
+            double M[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) M[a][b] = (double)c.R_wc[3 * b + a];  // R_wc^T
+            const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                               M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                               M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            if (!(fabs(det) > 1e-6)) return fail(ctx, SNP_ERR_INVALID_ARG, "camera %d: R_wc is singular", v);
+            const double id = 1.0 / det;
+            double I[3][3];
+            I[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) * id;
+            I[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) * id;
+            I[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) * id;
+            I[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) * id;
+            I[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) * id;
+            I[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) * id;
+            I[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) * id;
+            I[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) * id;
+            I[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) * id;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) V.Rti[3 * a + b] = I[a][b];
+        }
         t += (int64_t)V.tiles_x * V.tiles_y;
         p += (int64_t)c.width * c.height;
     }
@@ -519,12 +543,14 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     STAGE_BEGIN(SNP_STAGE_RANGES);
     CK(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)tiles * 8, st));
     launch_tile_ranges(skeys, d_nsort, key_bound, (uint2 *)ctx->ranges.p, st);
-    // persistent raster work queue: tiles by decreasing list length
+    // persistent raster work queue: tiles by decreasing list length (on request)
+    if (c.flags & SNP_FLAG_LENGTH_QUEUE) {
     launch_tile_queue((const uint2 *)ctx->ranges.p, tiles, (uint64_t *)ctx->qkeys.p, (uint32_t *)ctx->qvals.p,
                       d_tiles, st);
     ctx->queue_in_alt = radix_sort((uint64_t *)ctx->qkeys.p, (uint32_t *)ctx->qvals.p, (uint64_t *)ctx->qkeys_alt.p,
                                    (uint32_t *)ctx->qvals_alt.p, d_tiles, tiles, 32, (uint32_t *)ctx->qhist.p,
                                    (uint32_t *)ctx->qhist_scan.p, (uint32_t *)ctx->scan_tmp.p, st);
+    }
     STAGE_END();
     CK(cudaMemsetAsync(ctx->stats.p, 0, 24, st));
 
@@ -535,7 +561,9 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     a.px_nwalk = (uint32_t *)ctx->px_nwalk.p;
     a.stats = (unsigned long long *)ctx->stats.p;
     a.work_counter = d_work;
-    a.queue = (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p);
+    a.queue = (c.flags & SNP_FLAG_LENGTH_QUEUE)
+                  ? (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p)
+                  : nullptr;
     CK(cudaMemsetAsync(d_work, 0, 4, st));
     STAGE_BEGIN(SNP_STAGE_RASTER_FWD);
     s = launch_raster_fwd(a, desc->color_mode, desc->n_c, c.integral_form, desc->weight_dtype == SNP_BF16, ts, st);
@@ -582,7 +610,9 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     if (ctx->cfg.chunk > 0 && ctx->cfg.chunk < a.chunk) a.chunk = ctx->cfg.chunk;
     int *d_work = (int *)((char *)ctx->small.p + kSmallWork);
     a.work_counter = d_work;
-    a.queue = (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p);
+    a.queue = (ctx->cfg.flags & SNP_FLAG_LENGTH_QUEUE)
+                  ? (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p)
+                  : nullptr;
     CK(cudaMemsetAsync(d_work, 0, 4, st));
     STAGE_BEGIN(SNP_STAGE_RASTER_BWD);
     s = launch_raster_bwd(a, desc->color_mode, desc->n_c, ctx->cfg.integral_form, desc->weight_dtype == SNP_BF16,

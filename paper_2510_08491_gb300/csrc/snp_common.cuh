@@ -21,18 +21,33 @@ namespace snp {
 constexpr int kFeat = SNP_FEAT_DIM;
 constexpr int kMaxViews = 64;
 
-// Projection record (float offsets).
-constexpr int kRecMinv = 0;   // 9: diag(1/s) R_q^T, world offset -> unit-sphere coordinates
-constexpr int kRecOp = 9;     // 3: Minv (eye - c)
-constexpr int kRecOcm = 12;   // 3: (eye - c) / m,  m = max(s)
-constexpr int kRecInvM = 15;  // 1: 1 / m
-constexpr int kRecRgb = 16;   // 3: constant colour
-constexpr int kRecDepth = 19; // 1: camera-frame z of the centre
-constexpr int kRecFloats = 20;
+// Projection record (float offsets), per (view, primitive).  The ray of a pixel is
+// written relative to the ray through the primitive's centre: with camera-frame
+// centre mu, r_c = mu / mu_z and the unnormalised camera-frame pixel ray
+// r = ((px+.5-cx)/fx, (py+.5-cy)/fy, 1) = r_c + dr, dr = ((px+.5-U_c)/fx, (py+.5-V_c)/fy, 0)
+// where (U_c, V_c) is the projected centre; the line in unit-sphere coordinates is
+// (t - mu_z) e + t (e + f) with e = G r_c, f = G dr, G = diag(1/s) R_q^T R_wc^T.
+constexpr int kRecG = 0;      // 9: G, row-major
+constexpr int kRecE = 9;      // 3: e = G r_c
+constexpr int kRecMz = 12;    // 1: mu_z
+constexpr int kRecMz2 = 13;   // 1: mu_z^2
+constexpr int kRecU = 14;     // 4: U_c hi, U_c lo, V_c hi, V_c lo (FP64 value split into two floats)
+constexpr int kRecAc = 18;    // 3: R_wc^T r_c / m,  m = max(s)
+constexpr int kRecInvM = 21;  // 1: 1 / m
+constexpr int kRecOcm = 22;   // 3: (eye - c) / m  (literal Eq. 8 phases only)
+constexpr int kRecRgb = 25;   // 3: constant colour
+constexpr int kRecDepth = 28; // 1: camera-frame z of the centre (FP32 key value)
+constexpr int kRecGlo = 32;   // 9: FP64 remainders of G (G = hi + lo)
+constexpr int kRecElo = 41;   // 3: FP64 remainders of e
+constexpr int kRecMzlo = 44;  // 1: FP64 remainder of mu_z
+constexpr int kRecFloats = 48;
 
-// Per (view, primitive) geometry-gradient record (floats): d/dMinv (9), d/dop (3),
-// d/docm (3), d/d(1/m) (1), d/drgb (3), unused (1).
-constexpr int kGvFloats = 20;
+// Per (view, primitive) gradient record (floats): d/dG columns 0 and 1 (6, row-major
+// [3][2]), d/de (3), d/dmu_z (1), d/dU_c (1), d/dV_c (1), d/d(R_wc^T r_c / m) (3),
+// d/d(1/m) (1), d/docm (3), d/drgb (3), unused (2).
+constexpr int kGvFloats = 24;
+constexpr int kGvG = 0, kGvE = 6, kGvMz = 9, kGvU = 10, kGvV = 11, kGvAc = 12, kGvInvM = 15, kGvOcm = 16,
+              kGvRgb = 19;
 
 // Per-view constants shared by the kernels.
 struct View {
@@ -44,6 +59,10 @@ struct View {
     int32_t tile_off;  // first global tile id of this view
     int32_t pad_;
     int64_t pix_off;   // first pixel of this view in the concatenated image
+    // Inverse of R_wc^T in FP64: the stored FP32 rotation is not exactly
+    // orthonormal, so the camera-frame centre used for the ray geometry is
+    // mu' = (R_wc^T)^-1 (c - eye), for which c - eye = R_wc^T mu' holds exactly.
+    double Rti[9];
 };
 
 // Field offsets of one primitive's network record (elements), see snp_net_layout.
@@ -59,18 +78,27 @@ __device__ __forceinline__ float ksub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float kdiv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
 
-// Pixel ray (unit, world frame) through the centre of pixel (px, py), evaluated in
-// FP64 once per pixel and rounded to FP32 (the ray position near a primitive far
-// from the camera amplifies any error of d by the distance).
-__device__ __forceinline__ float3 pixel_ray(const View &v, int px, int py)
+// Per-pixel ray data: pixel-centre coordinates (exact in FP32) and the
+// unnormalised world direction g = R_wc^T ((px+.5-cx)/fx, (py+.5-cy)/fy, 1) with
+// its length, evaluated in FP64 once per pixel and rounded.
+struct PixRay {
+    float pxh, pyh, gn;
+    float3 g;
+};
+
+__device__ __forceinline__ PixRay pixel_ray(const View &v, int px, int py)
 {
+    PixRay r;
+    r.pxh = (float)px + 0.5f;
+    r.pyh = (float)py + 0.5f;
     const double x = ((double)px + 0.5 - (double)v.cx) / (double)v.fx;
     const double y = ((double)py + 0.5 - (double)v.cy) / (double)v.fy;
-    const double rx = (double)v.R[0] * x + (double)v.R[3] * y + (double)v.R[6];
-    const double ry = (double)v.R[1] * x + (double)v.R[4] * y + (double)v.R[7];
-    const double rz = (double)v.R[2] * x + (double)v.R[5] * y + (double)v.R[8];
-    const double inv = 1.0 / sqrt(rx * rx + ry * ry + rz * rz);
-    return make_float3((float)(rx * inv), (float)(ry * inv), (float)(rz * inv));
+    const double gx = (double)v.R[0] * x + (double)v.R[3] * y + (double)v.R[6];
+    const double gy = (double)v.R[1] * x + (double)v.R[4] * y + (double)v.R[7];
+    const double gz = (double)v.R[2] * x + (double)v.R[5] * y + (double)v.R[8];
+    r.g = make_float3((float)gx, (float)gy, (float)gz);
+    r.gn = (float)sqrt(gx * gx + gy * gy + gz * gz);
+    return r;
 }
 
 template <bool BF16>

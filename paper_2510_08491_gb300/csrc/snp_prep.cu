@@ -169,25 +169,56 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ geom,
     const double qd[4] = {q[0], q[1], q[2], q[3]};
     const double iqn = 1.0 / sqrt(qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3]);
     const double W = qd[0] * iqn, X = qd[1] * iqn, Y = qd[2] * iqn, Z = qd[3] * iqn;
-    const double Rd[3][3] = {
+    const double Rq[3][3] = {
         {1.0 - 2.0 * (Y * Y + Z * Z), 2.0 * (X * Y - W * Z), 2.0 * (X * Z + W * Y)},
         {2.0 * (X * Y + W * Z), 1.0 - 2.0 * (X * X + Z * Z), 2.0 * (Y * Z - W * X)},
         {2.0 * (X * Z - W * Y), 2.0 * (Y * Z + W * X), 1.0 - 2.0 * (X * X + Y * Y)}};
     const double md = fmax(fmax(sd[0], sd[1]), sd[2]);
-    const double oc[3] = {(double)V.eye[0] - c[0], (double)V.eye[1] - c[1], (double)V.eye[2] - c[2]};
+    double Rw[3][3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rw[k / 3][k % 3] = V.R[k];
+    const double dc[3] = {(double)c[0] - V.eye[0], (double)c[1] - V.eye[1], (double)c[2] - V.eye[2]};
+    double mud[3];  // mu' = (R_wc^T)^-1 (c - eye)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mud[a] = V.Rti[3 * a + 0] * dc[0] + V.Rti[3 * a + 1] * dc[1] + V.Rti[3 * a + 2] * dc[2];
+    const double rc[3] = {mud[0] / mud[2], mud[1] / mud[2], 1.0};
+    // G = diag(1/s) R_q^T R_wc^T:  G[a][b] = sum_j R_q[j][a] R_wc[b][j] / s_a
+    double G[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            G[a][b] = (Rq[0][a] * Rw[b][0] + Rq[1][a] * Rw[b][1] + Rq[2][a] * Rw[b][2]) / sd[a];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double m0 = Rd[0][a] / sd[a], m1 = Rd[1][a] / sd[a], m2 = Rd[2][a] / sd[a];
-        r[kRecMinv + 3 * a + 0] = (float)m0;
-        r[kRecMinv + 3 * a + 1] = (float)m1;
-        r[kRecMinv + 3 * a + 2] = (float)m2;
-        r[kRecOp + a] = (float)(m0 * oc[0] + m1 * oc[1] + m2 * oc[2]);
-        r[kRecOcm + a] = (float)(oc[a] / md);
-    }
-    r[kRecInvM] = (float)(1.0 / md);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) r[kRecRgb + a] = rgb[a];
+        for (int b = 0; b < 3; ++b) {
+            const float hi = (float)G[a][b];
+            r[kRecG + 3 * a + b] = hi;
+            r[kRecGlo + 3 * a + b] = (float)(G[a][b] - (double)hi);
+        }
+        const double ea = G[a][0] * rc[0] + G[a][1] * rc[1] + G[a][2];
+        r[kRecE + a] = (float)ea;
+        r[kRecElo + a] = (float)(ea - (double)(float)ea);
+        // R_wc^T r_c / m
+        r[kRecAc + a] = (float)((Rw[0][a] * rc[0] + Rw[1][a] * rc[1] + Rw[2][a]) / md);
+        r[kRecOcm + a] = (float)(-dc[a] / md);
+        r[kRecRgb + a] = rgb[a];
+    }
+    r[kRecMz] = (float)mud[2];
+    r[kRecMzlo] = (float)(mud[2] - (double)(float)mud[2]);
+    r[kRecMz2] = (float)(mud[2] * mud[2]);
+    const double uc = (double)V.cx + (double)V.fx * rc[0];
+    const double vc = (double)V.cy + (double)V.fy * rc[1];
+    const float uhi = (float)uc, vhi = (float)vc;
+    r[kRecU + 0] = uhi;
+    r[kRecU + 1] = (float)(uc - (double)uhi);
+    r[kRecU + 2] = vhi;
+    r[kRecU + 3] = (float)(vc - (double)vhi);
+    r[kRecInvM] = (float)(1.0 / md);
     r[kRecDepth] = mu[2];
+    r[29] = r[30] = r[31] = 0.0f;
+    r[45] = r[46] = r[47] = 0.0f;
 }
 
 // ---------------------------------------------------------------------------

@@ -91,73 +91,187 @@ __device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, in
     }
 }
 
-// Ray / ellipsoid closest-approach test in unit-sphere coordinates.
-struct Hit {
-    float tm, half;  // midpoint and half chord (world units along the unit ray)
-    float3 dp;       // Minv d
-    float3 p;        // closest point to the centre (unit-sphere coordinates)
-    float A, B, iA, h2;
+// Per-tile camera constants for the pair arithmetic.
+struct CamK {
+    float ifx, ify;  // 1 / fx, 1 / fy
+    float fx, fy;
+    float3 r0, r1;   // camera x and y axes in world coordinates (rows 0, 1 of R_wc)
 };
 
-__device__ __forceinline__ bool intersect(const float *R, float3 d, Hit &h)
+__device__ __forceinline__ CamK cam_consts(const View &V)
 {
-    const float4 r0 = reinterpret_cast<const float4 *>(R)[0];
-    const float4 r1 = reinterpret_cast<const float4 *>(R)[1];
-    const float4 r2 = reinterpret_cast<const float4 *>(R)[2];
-    // Minv rows: (r0.x r0.y r0.z) (r0.w r1.x r1.y) (r1.z r1.w r2.x); op = (r2.y r2.z r2.w)
-    h.dp.x = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
-    h.dp.y = fmaf(r0.w, d.x, fmaf(r1.x, d.y, r1.y * d.z));
-    h.dp.z = fmaf(r1.z, d.x, fmaf(r1.w, d.y, r2.x * d.z));
+    CamK k;
+    k.ifx = 1.0f / V.fx;
+    k.ify = 1.0f / V.fy;
+    k.fx = V.fx;
+    k.fy = V.fy;
+    k.r0 = make_float3(V.R[0], V.R[1], V.R[2]);
+    k.r1 = make_float3(V.R[3], V.R[4], V.R[5]);
+    return k;
+}
+
+// Ray / ellipsoid intersection, relative to the ray through the centre.  In
+// unit-sphere coordinates the ray is (t - mu_z) e + t dp, dp = e + f, f = G dr
+// (t in units of the unnormalised ray g).  Closest approach to the centre:
+// |p|^2 = mu_z^2 |e x f|^2 / |dp|^2, so h^2 = 1 - |p|^2 needs no cancellation of
+// large terms; t_mid = mu_z + s with s = -mu_z (f . dp) / |dp|^2; half chord
+// sqrt(h^2 / |dp|^2).
+struct Hit {
+    float dx, dy;    // dr = (dx, dy, 0)
+    float3 f, dp, w; // f = G dr, dp = e + f, w = e x f
+    float A, iA, W2, h2, fdp;
+    float s, t, half;
+};
+
+// Pairs whose FP32 h^2 lies within this distance of the silhouette are evaluated
+// again in FP64 (the chord length grows like sqrt(h^2), so an FP32 error of ~1e-7
+// in h^2 would move alpha_hat by ~1e-3 at a grazing ray).
+constexpr float kRefineH2 = 1e-4f;
+
+static __device__ __noinline__ void intersect_fp64(const float *R, const CamK &ck, const PixRay &ry, Hit &h)
+{
+    double G0[3], G1[3], e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        G0[a] = (double)R[kRecG + 3 * a + 0] + (double)R[kRecGlo + 3 * a + 0];
+        G1[a] = (double)R[kRecG + 3 * a + 1] + (double)R[kRecGlo + 3 * a + 1];
+        e[a] = (double)R[kRecE + a] + (double)R[kRecElo + a];
+    }
+    const double mz = (double)R[kRecMz] + (double)R[kRecMzlo];
+    const double uc = (double)R[kRecU + 0] + (double)R[kRecU + 1];
+    const double vc = (double)R[kRecU + 2] + (double)R[kRecU + 3];
+    const double dx = ((double)ry.pxh - uc) / (double)ck.fx;
+    const double dy = ((double)ry.pyh - vc) / (double)ck.fy;
+    double f[3], dp[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[a] = G0[a] * dx + G1[a] * dy;
+        dp[a] = e[a] + f[a];
+    }
+    const double A = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
+    const double w[3] = {e[1] * f[2] - e[2] * f[1], e[2] * f[0] - e[0] * f[2], e[0] * f[1] - e[1] * f[0]};
+    const double W2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double h2 = 1.0 - mz * mz * W2 / A;
+    const double fdp = f[0] * dp[0] + f[1] * dp[1] + f[2] * dp[2];
+    const double sd = -mz * fdp / A;
+    h.dx = (float)dx;
+    h.dy = (float)dy;
+    h.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
+    h.dp = make_float3((float)dp[0], (float)dp[1], (float)dp[2]);
+    h.w = make_float3((float)w[0], (float)w[1], (float)w[2]);
+    h.A = (float)A;
+    h.iA = (float)(1.0 / A);
+    h.W2 = (float)W2;
+    h.h2 = (float)h2;
+    h.fdp = (float)fdp;
+    h.s = (float)sd;
+    h.t = (float)(mz + sd);
+    h.half = (float)sqrt(h2 > 0.0 ? h2 / A : 0.0);
+    if (!(h2 > 0.0)) h.h2 = 0.0f;
+}
+
+__device__ __forceinline__ bool intersect(const float *R, const CamK &ck, const PixRay &ry, Hit &h)
+{
+    const float4 g0 = reinterpret_cast<const float4 *>(R)[0];  // G00 G01 G02 G10
+    const float4 g1 = reinterpret_cast<const float4 *>(R)[1];  // G11 G12 G20 G21
+    const float4 g2 = reinterpret_cast<const float4 *>(R)[2];  // G22 ex ey ez
+    const float4 g3 = reinterpret_cast<const float4 *>(R)[3];  // mz mz2 Uhi Ulo
+    const float4 g4 = reinterpret_cast<const float4 *>(R)[4];  // Vhi Vlo ...
+    h.dx = ((ry.pxh - g3.z) - g3.w) * ck.ifx;
+    h.dy = ((ry.pyh - g4.x) - g4.y) * ck.ify;
+    h.f.x = fmaf(g0.x, h.dx, g0.y * h.dy);
+    h.f.y = fmaf(g0.w, h.dx, g1.x * h.dy);
+    h.f.z = fmaf(g1.z, h.dx, g1.w * h.dy);
+    const float3 e = make_float3(g2.y, g2.z, g2.w);
+    h.dp = make_float3(e.x + h.f.x, e.y + h.f.y, e.z + h.f.z);
     h.A = fmaf(h.dp.x, h.dp.x, fmaf(h.dp.y, h.dp.y, h.dp.z * h.dp.z));
-    h.B = fmaf(r2.y, h.dp.x, fmaf(r2.z, h.dp.y, r2.w * h.dp.z));
     h.iA = __fdividef(1.0f, h.A);
-    h.tm = -h.B * h.iA;
-    h.p.x = fmaf(h.tm, h.dp.x, r2.y);
-    h.p.y = fmaf(h.tm, h.dp.y, r2.z);
-    h.p.z = fmaf(h.tm, h.dp.z, r2.w);
-    h.h2 = 1.0f - fmaf(h.p.x, h.p.x, fmaf(h.p.y, h.p.y, h.p.z * h.p.z));
+    h.w = make_float3(fmaf(e.y, h.f.z, -e.z * h.f.y), fmaf(e.z, h.f.x, -e.x * h.f.z), fmaf(e.x, h.f.y, -e.y * h.f.x));
+    h.W2 = fmaf(h.w.x, h.w.x, fmaf(h.w.y, h.w.y, h.w.z * h.w.z));
+    h.h2 = 1.0f - g3.y * h.W2 * h.iA;
+    if (fabsf(h.h2) < kRefineH2) {
+        intersect_fp64(R, ck, ry, h);
+        return h.h2 > 0.0f && h.half > 0.0f;
+    }
     if (!(h.h2 > 0.0f)) return false;
+    h.fdp = fmaf(h.f.x, h.dp.x, fmaf(h.f.y, h.dp.y, h.f.z * h.dp.z));
+    h.s = -g3.x * h.fdp * h.iA;
+    h.t = g3.x + h.s;
     const float x = h.h2 * h.iA;
     h.half = x * rsqrtf(x);
     return true;
 }
 
-// alpha_hat of one (ray, primitive) pair.  FORM 0 (stable):
-//   Delta_t [b2 + sum_k w2_k cos(phi_k) sinc(theta_k)], phi_k = w0 (W1_k . u_mid + b1_k),
-//   theta_k = w0 (W1_k . d) half / m.   FORM 1 (naive, Eq. 8 literally):
-//   sum_k w2_k [sin(a_k t_out + psi_k) - sin(a_k t_in + psi_k)] / a_k + b2 (t_out - t_in),
-//   a_k = w0 W1_k . d / m, psi_k = w0 (W1_k . (eye - c) / m + b1_k).
+__device__ __forceinline__ bool hit_test(const float *R, const CamK &ck, const PixRay &ry)
+{
+    Hit h;
+    return intersect(R, ck, ry, h);
+}
+
+// alpha_hat of one (ray, primitive) pair.  With u_mid = s a_c + (t / m) dg,
+// dg = dx r0 + dy r1 (world offset of the ray direction), FORM 0 (stable):
+//   |g| 2 half [b2 + sum_k w2_k cos(phi_k) sinc(theta_k)], phi_k = w0 (W1_k . u_mid + b1_k),
+//   theta_k = w0 (W1_k . g) half / m.   FORM 1 (Eq. 8 literally):
+//   |g| [sum_k w2_k (sin(a_k t_out + psi_k) - sin(a_k t_in + psi_k)) / a_k + b2 (t_out - t_in)],
+//   a_k = w0 W1_k . g / m, psi_k = w0 (W1_k . (eye - c) / m + b1_k).
 template <int FORM>
-__device__ __forceinline__ float integral(const float *R, const float *D, int ns, float3 d, const Hit &h)
+__device__ __forceinline__ float integral(const float *R, const float *D, int ns, const CamK &ck, const PixRay &ry,
+                                          const Hit &h)
 {
     const float inv_m = R[kRecInvM];
     const float4 *W = reinterpret_cast<const float4 *>(D);
     const float *w2 = D + 4 * ns;
     float acc = 0.0f;
     if constexpr (FORM == 0) {
-        const float tmm = h.tm * inv_m, hm = h.half * inv_m;
-        const float3 u = make_float3(fmaf(tmm, d.x, R[kRecOcm + 0]), fmaf(tmm, d.y, R[kRecOcm + 1]),
-                                     fmaf(tmm, d.z, R[kRecOcm + 2]));
+        const float tm = h.t * inv_m, hm = h.half * inv_m;
+        const float3 dg = make_float3(fmaf(h.dx, ck.r0.x, h.dy * ck.r1.x), fmaf(h.dx, ck.r0.y, h.dy * ck.r1.y),
+                                      fmaf(h.dx, ck.r0.z, h.dy * ck.r1.z));
+        const float3 u = make_float3(fmaf(h.s, R[kRecAc + 0], tm * dg.x), fmaf(h.s, R[kRecAc + 1], tm * dg.y),
+                                     fmaf(h.s, R[kRecAc + 2], tm * dg.z));
 #pragma unroll 4
         for (int k = 0; k < ns; ++k) {
             const float4 w = W[k];
-            const float g = fmaf(w.x, d.x, fmaf(w.y, d.y, w.z * d.z));
+            const float g = fmaf(w.x, ry.g.x, fmaf(w.y, ry.g.y, w.z * ry.g.z));
             const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
             acc = fmaf(w2[k] * __cosf(ph), sincf_fast(g * hm), acc);
         }
-        return 2.0f * h.half * (w2[ns] + acc);
+        return 2.0f * h.half * ry.gn * (w2[ns] + acc);
     } else {
-        const float tin = h.tm - h.half, tout = h.tm + h.half;
+        const float tin = h.t - h.half, tout = h.t + h.half;
         const float ox = R[kRecOcm + 0], oy = R[kRecOcm + 1], oz = R[kRecOcm + 2];
 #pragma unroll 4
         for (int k = 0; k < ns; ++k) {
             const float4 w = W[k];
-            const float ak = fmaf(w.x, d.x, fmaf(w.y, d.y, w.z * d.z)) * inv_m;
+            const float ak = fmaf(w.x, ry.g.x, fmaf(w.y, ry.g.y, w.z * ry.g.z)) * inv_m;
             const float psi = fmaf(w.x, ox, fmaf(w.y, oy, fmaf(w.z, oz, w.w)));
             acc = fmaf(w2[k], __fdividef(__sinf(fmaf(ak, tout, psi)) - __sinf(fmaf(ak, tin, psi)), ak), acc);
         }
-        return fmaf(w2[ns], tout - tin, acc);
+        return ry.gn * fmaf(w2[ns], tout - tin, acc);
     }
+}
+
+__device__ __forceinline__ float3 unit_dir(const PixRay &ry)
+{
+    const float ig = 1.0f / ry.gn;
+    return make_float3(ry.g.x * ig, ry.g.y * ig, ry.g.z * ig);
+}
+
+// Per-pixel ray data in shared memory (two float4 per pixel slot).
+__device__ __forceinline__ void store_ray(float4 *s_ray, int slot, const PixRay &r)
+{
+    s_ray[2 * slot] = make_float4(r.pxh, r.pyh, r.gn, 0.0f);
+    s_ray[2 * slot + 1] = make_float4(r.g.x, r.g.y, r.g.z, 0.0f);
+}
+
+__device__ __forceinline__ PixRay load_ray(const float4 *s_ray, int slot)
+{
+    const float4 a = s_ray[2 * slot], b = s_ray[2 * slot + 1];
+    PixRay r;
+    r.pxh = a.x;
+    r.pyh = a.y;
+    r.gn = a.z;
+    r.g = make_float3(b.x, b.y, b.z);
+    return r;
 }
 
 // Colour MLP of one pixel ray: z1 = relu(Wc1_d d + h0), z2 = relu(Wc2 z1 + bc2),
@@ -208,27 +322,6 @@ __device__ __forceinline__ float3 mlp_color(const float *C, float3 d, float *z1_
         c2 = fmaf(wa.z, a0, fmaf(wb.z, a1, c2));
     }
     return make_float3(sigmoidf_fast(c0), sigmoidf_fast(c1), sigmoidf_fast(c2));
-}
-
-// Entry/exit test only (h^2 > 0), the same arithmetic as intersect().
-__device__ __forceinline__ bool hit_test(const float *R, float3 d)
-{
-    Hit h;
-    const float4 r0 = reinterpret_cast<const float4 *>(R)[0];
-    const float4 r1 = reinterpret_cast<const float4 *>(R)[1];
-    const float4 r2 = reinterpret_cast<const float4 *>(R)[2];
-    h.dp.x = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
-    h.dp.y = fmaf(r0.w, d.x, fmaf(r1.x, d.y, r1.y * d.z));
-    h.dp.z = fmaf(r1.z, d.x, fmaf(r1.w, d.y, r2.x * d.z));
-    h.A = fmaf(h.dp.x, h.dp.x, fmaf(h.dp.y, h.dp.y, h.dp.z * h.dp.z));
-    h.B = fmaf(r2.y, h.dp.x, fmaf(r2.z, h.dp.y, r2.w * h.dp.z));
-    h.iA = __fdividef(1.0f, h.A);
-    h.tm = -h.B * h.iA;
-    h.p.x = fmaf(h.tm, h.dp.x, r2.y);
-    h.p.y = fmaf(h.tm, h.dp.y, r2.z);
-    h.p.z = fmaf(h.tm, h.dp.z, r2.w);
-    h.h2 = 1.0f - fmaf(h.p.x, h.p.x, fmaf(h.p.y, h.p.y, h.p.z * h.p.z));
-    return h.h2 > 0.0f;
 }
 
 // Warp-aggregated append of `val` to list[] for the lanes with pred set.

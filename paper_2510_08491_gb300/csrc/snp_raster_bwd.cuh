@@ -82,38 +82,49 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
 // without a pair pass contrib = false (their contributions are zero).
 template <int NC, int FORM>
 __device__ __forceinline__ void pair_backward(const float *R, const float *D, const float *Cb, int ns, float w0,
-                                              float3 d, bool contrib, float g_ah, float3 g_c, float3 col,
-                                              float *A)
+                                              const CamK &ck, const PixRay &ry, bool contrib, float g_ah, float3 g_c,
+                                              float3 col, float *A)
 {
     const unsigned lane = lane_id();
+    const float3 d = unit_dir(ry);
     Hit h;
-    if (!contrib || !intersect(R, d, h)) {
+    if (!contrib || !intersect(R, ck, ry, h)) {
         // benign geometry for lanes that only take part in the warp reductions
-        h.tm = 0.0f; h.half = 1.0f; h.dp = make_float3(1.f, 0.f, 0.f); h.p = make_float3(0.f, 0.f, 0.f);
-        h.A = 1.0f; h.B = 0.0f; h.iA = 1.0f; h.h2 = 1.0f;
+        h.dx = h.dy = 0.0f;
+        h.f = make_float3(0.f, 0.f, 0.f);
+        h.dp = make_float3(1.f, 0.f, 0.f);
+        h.w = make_float3(0.f, 0.f, 0.f);
+        h.A = h.iA = h.h2 = 1.0f;
+        h.W2 = h.fdp = h.s = h.t = 0.0f;
+        h.half = 1.0f;
         g_ah = 0.0f;
         g_c = make_float3(0.f, 0.f, 0.f);
         col = make_float3(0.f, 0.f, 0.f);
     }
-    // ---- density (closed-form integral) and geometry
+    // ---- density (closed-form integral)
     const float inv_m = R[kRecInvM];
+    const float mz = R[kRecMz], mz2 = R[kRecMz2];
+    const float3 ac = make_float3(R[kRecAc + 0], R[kRecAc + 1], R[kRecAc + 2]);
     const float3 ocm = make_float3(R[kRecOcm + 0], R[kRecOcm + 1], R[kRecOcm + 2]);
     const float4 *W = reinterpret_cast<const float4 *>(D);
     const float *w2 = D + 4 * ns;
     const float b2 = w2[ns];
+    const float3 dg = make_float3(fmaf(h.dx, ck.r0.x, h.dy * ck.r1.x), fmaf(h.dx, ck.r0.y, h.dy * ck.r1.y),
+                                  fmaf(h.dx, ck.r0.z, h.dy * ck.r1.z));
+    const float tm = h.t * inv_m, hm = h.half * inv_m;
+    const float3 u = make_float3(fmaf(h.s, ac.x, tm * dg.x), fmaf(h.s, ac.y, tm * dg.y), fmaf(h.s, ac.z, tm * dg.z));
+    const float gscale = g_ah * ry.gn;  // dL/dalpha_hat times |g|
     float3 g_u = make_float3(0.f, 0.f, 0.f), g_ocm = make_float3(0.f, 0.f, 0.f);
-    float g_hm = 0.0f, S = b2, g_invm = 0.0f, g_tm = 0.0f, g_half = 0.0f, g_b2;
-    const float tmm = h.tm * inv_m, hm = h.half * inv_m, dt = 2.0f * h.half;
-    const float tin = h.tm - h.half, tout = h.tm + h.half;
-    const float3 u = make_float3(fmaf(tmm, d.x, ocm.x), fmaf(tmm, d.y, ocm.y), fmaf(tmm, d.z, ocm.z));
-    const float gS = g_ah * dt;
+    float g_hm = 0.0f, S = b2, g_invm = 0.0f, g_t = 0.0f, g_half = 0.0f, g_b2;
+    const float tin = h.t - h.half, tout = h.t + h.half;
+    const float gS = gscale * 2.0f * h.half;
     float g_tout = 0.0f, g_tin = 0.0f;
     if constexpr (FORM == 0) {
         g_b2 = gS;
     } else {
-        g_b2 = g_ah * (tout - tin);
-        g_tout = g_ah * b2;
-        g_tin = -g_ah * b2;
+        g_b2 = gscale * (tout - tin);
+        g_tout = gscale * b2;
+        g_tin = -gscale * b2;
     }
     for (int k0 = 0; k0 < ns; k0 += 6) {
         float vv[32];
@@ -124,7 +135,7 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
             if (k < ns) {
                 const float4 w = W[k];
                 const float wk = w2[k];
-                const float g = fmaf(w.x, d.x, fmaf(w.y, d.y, w.z * d.z));
+                const float g = fmaf(w.x, ry.g.x, fmaf(w.y, ry.g.y, w.z * ry.g.z));
                 if constexpr (FORM == 0) {
                     const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
                     const float th = g * hm;
@@ -139,9 +150,9 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
                     const float gphi = -gS * wk * sp * sc;
                     const float gth = gS * wk * cp * scp;
                     gw2 = gS * cp * sc;
-                    gw[0] = w0 * fmaf(gphi, u.x, gth * hm * d.x);
-                    gw[1] = w0 * fmaf(gphi, u.y, gth * hm * d.y);
-                    gw[2] = w0 * fmaf(gphi, u.z, gth * hm * d.z);
+                    gw[0] = w0 * fmaf(gphi, u.x, gth * hm * ry.g.x);
+                    gw[1] = w0 * fmaf(gphi, u.y, gth * hm * ry.g.y);
+                    gw[2] = w0 * fmaf(gphi, u.z, gth * hm * ry.g.z);
                     gb1 = w0 * gphi;
                     g_u.x = fmaf(gphi, w.x, g_u.x);
                     g_u.y = fmaf(gphi, w.y, g_u.y);
@@ -153,20 +164,20 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
                     float s1, c1, s0, c0v;
                     __sincosf(fmaf(ak, tout, psi), &s1, &c1);
                     __sincosf(fmaf(ak, tin, psi), &s0, &c0v);
-                    const float ia = g_ah != 0.0f ? __fdividef(1.0f, ak) : 0.0f;
-                    gw2 = g_ah * (s1 - s0) * ia;
-                    const float gpsi = g_ah * wk * (c1 - c0v) * ia;
-                    const float ga = g_ah * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
-                    gw[0] = w0 * fmaf(gpsi, ocm.x, ga * inv_m * d.x);
-                    gw[1] = w0 * fmaf(gpsi, ocm.y, ga * inv_m * d.y);
-                    gw[2] = w0 * fmaf(gpsi, ocm.z, ga * inv_m * d.z);
+                    const float ia = gscale != 0.0f ? __fdividef(1.0f, ak) : 0.0f;
+                    gw2 = gscale * (s1 - s0) * ia;
+                    const float gpsi = gscale * wk * (c1 - c0v) * ia;
+                    const float ga = gscale * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
+                    gw[0] = w0 * fmaf(gpsi, ocm.x, ga * inv_m * ry.g.x);
+                    gw[1] = w0 * fmaf(gpsi, ocm.y, ga * inv_m * ry.g.y);
+                    gw[2] = w0 * fmaf(gpsi, ocm.z, ga * inv_m * ry.g.z);
                     gb1 = w0 * gpsi;
                     g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
                     g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
                     g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
                     g_invm = fmaf(ga, g, g_invm);
-                    g_tout = fmaf(g_ah * wk, c1, g_tout);
-                    g_tin = fmaf(-g_ah * wk, c0v, g_tin);
+                    g_tout = fmaf(gscale * wk, c1, g_tout);
+                    g_tin = fmaf(-gscale * wk, c0v, g_tin);
                 }
             }
             vv[5 * kk + 0] = gw[0];
@@ -184,34 +195,49 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
             atomicAdd(A + dst, r);
         }
     }
+    // ---- geometry: (t, half) and u back to the record quantities
+    float g_s = 0.0f;
+    float3 g_ac = make_float3(0.f, 0.f, 0.f), g_dg = make_float3(0.f, 0.f, 0.f);
     if constexpr (FORM == 0) {
-        const float gud = g_u.x * d.x + g_u.y * d.y + g_u.z * d.z;
-        g_half = 2.0f * g_ah * S + g_hm * inv_m;
-        g_invm = g_hm * h.half + gud * h.tm;
-        g_tm = gud * inv_m;
-        g_ocm = g_u;
+        // u = s ac + (t / m) dg; alpha_hat = 2 half |g| S; theta uses hm = half / m
+        g_half = 2.0f * gscale * S + g_hm * inv_m;
+        g_invm = g_hm * h.half + h.t * (g_u.x * dg.x + g_u.y * dg.y + g_u.z * dg.z);
+        g_s = g_u.x * ac.x + g_u.y * ac.y + g_u.z * ac.z;
+        g_t = inv_m * (g_u.x * dg.x + g_u.y * dg.y + g_u.z * dg.z);
+        g_ac = make_float3(h.s * g_u.x, h.s * g_u.y, h.s * g_u.z);
+        g_dg = make_float3(tm * g_u.x, tm * g_u.y, tm * g_u.z);
     } else {
-        g_tm = g_tout + g_tin;
+        g_t = g_tout + g_tin;
         g_half = g_tout - g_tin;
     }
-    // half = sqrt(h2 / A): tm, half -> closest point, A, B -> Minv d, op
+    // t = mz + s, s = -mz (f . dp) / A, half = sqrt(h2 / A), h2 = 1 - mz^2 |w|^2 / A
+    const float g_st = g_s + g_t;
+    float g_mz = g_t - g_st * h.fdp * h.iA;
+    const float g_fdp = -mz * h.iA * g_st;
+    float g_iA = -mz * h.fdp * g_st;
     const float gx = __fdividef(g_half, 2.0f * h.half);
     const float g_h2 = gx * h.iA;
-    float g_iA = gx * h.h2;
-    const float3 g_p = make_float3(-2.0f * g_h2 * h.p.x, -2.0f * g_h2 * h.p.y, -2.0f * g_h2 * h.p.z);
-    float3 g_op = g_p;
-    g_tm += g_p.x * h.dp.x + g_p.y * h.dp.y + g_p.z * h.dp.z;
-    float3 g_dp = make_float3(h.tm * g_p.x, h.tm * g_p.y, h.tm * g_p.z);
-    const float g_B = -g_tm * h.iA;
-    g_iA -= g_tm * h.B;
+    g_iA += gx * h.h2;
+    g_mz += 2.0f * mz * (-g_h2 * h.W2 * h.iA);
+    const float g_W2 = -g_h2 * mz2 * h.iA;
+    g_iA += -g_h2 * mz2 * h.W2;
+    const float3 g_w = make_float3(2.0f * g_W2 * h.w.x, 2.0f * g_W2 * h.w.y, 2.0f * g_W2 * h.w.z);
     const float g_A = -g_iA * h.iA * h.iA;
-    const float3 op = make_float3(R[kRecOp + 0], R[kRecOp + 1], R[kRecOp + 2]);
-    g_dp.x = fmaf(2.0f * g_A, h.dp.x, fmaf(g_B, op.x, g_dp.x));
-    g_dp.y = fmaf(2.0f * g_A, h.dp.y, fmaf(g_B, op.y, g_dp.y));
-    g_dp.z = fmaf(2.0f * g_A, h.dp.z, fmaf(g_B, op.z, g_dp.z));
-    g_op.x = fmaf(g_B, h.dp.x, g_op.x);
-    g_op.y = fmaf(g_B, h.dp.y, g_op.y);
-    g_op.z = fmaf(g_B, h.dp.z, g_op.z);
+    const float3 e = make_float3(R[kRecE + 0], R[kRecE + 1], R[kRecE + 2]);
+    // dp = e + f:  dL/ddp from A = dp.dp and from fdp = f.dp
+    const float3 g_dp = make_float3(fmaf(2.0f * g_A, h.dp.x, g_fdp * h.f.x), fmaf(2.0f * g_A, h.dp.y, g_fdp * h.f.y),
+                                    fmaf(2.0f * g_A, h.dp.z, g_fdp * h.f.z));
+    // w = e x f:  dL/de = f x g_w,  dL/df = g_w x e
+    float3 g_e = make_float3(h.f.y * g_w.z - h.f.z * g_w.y + g_dp.x, h.f.z * g_w.x - h.f.x * g_w.z + g_dp.y,
+                             h.f.x * g_w.y - h.f.y * g_w.x + g_dp.z);
+    const float3 g_f = make_float3(g_w.y * e.z - g_w.z * e.y + g_dp.x + g_fdp * h.dp.x,
+                                   g_w.z * e.x - g_w.x * e.z + g_dp.y + g_fdp * h.dp.y,
+                                   g_w.x * e.y - g_w.y * e.x + g_dp.z + g_fdp * h.dp.z);
+    // f = G[:,0] dx + G[:,1] dy;  dg = dx r0 + dy r1;  dx = (px + .5 - U_c) / fx
+    const float g_dx = g_f.x * R[kRecG + 0] + g_f.y * R[kRecG + 3] + g_f.z * R[kRecG + 6] +
+                       g_dg.x * ck.r0.x + g_dg.y * ck.r0.y + g_dg.z * ck.r0.z;
+    const float g_dy = g_f.x * R[kRecG + 1] + g_f.y * R[kRecG + 4] + g_f.z * R[kRecG + 7] +
+                       g_dg.x * ck.r1.x + g_dg.y * ck.r1.y + g_dg.z * ck.r1.z;
 
     float3 g_a3 = make_float3(0.f, 0.f, 0.f);
     if constexpr (NC > 0) {
@@ -220,25 +246,30 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
     }
     {
         float vv[32];
-        vv[0] = g_dp.x * d.x; vv[1] = g_dp.x * d.y; vv[2] = g_dp.x * d.z;
-        vv[3] = g_dp.y * d.x; vv[4] = g_dp.y * d.y; vv[5] = g_dp.y * d.z;
-        vv[6] = g_dp.z * d.x; vv[7] = g_dp.z * d.y; vv[8] = g_dp.z * d.z;
-        vv[9] = g_op.x; vv[10] = g_op.y; vv[11] = g_op.z;
-        vv[12] = g_ocm.x; vv[13] = g_ocm.y; vv[14] = g_ocm.z;
-        vv[15] = g_invm;
-        vv[16] = NC == 0 ? g_c.x : 0.0f;
-        vv[17] = NC == 0 ? g_c.y : 0.0f;
-        vv[18] = NC == 0 ? g_c.z : 0.0f;
-        vv[19] = 0.0f;
-        vv[20] = g_b2;
-        vv[21] = g_a3.x; vv[22] = g_a3.y; vv[23] = g_a3.z;
+        vv[kGvG + 0] = g_f.x * h.dx; vv[kGvG + 1] = g_f.x * h.dy;
+        vv[kGvG + 2] = g_f.y * h.dx; vv[kGvG + 3] = g_f.y * h.dy;
+        vv[kGvG + 4] = g_f.z * h.dx; vv[kGvG + 5] = g_f.z * h.dy;
+        vv[kGvE + 0] = g_e.x; vv[kGvE + 1] = g_e.y; vv[kGvE + 2] = g_e.z;
+        vv[kGvMz] = g_mz;
+        vv[kGvU] = -g_dx * ck.ifx;
+        vv[kGvV] = -g_dy * ck.ify;
+        vv[kGvAc + 0] = g_ac.x; vv[kGvAc + 1] = g_ac.y; vv[kGvAc + 2] = g_ac.z;
+        vv[kGvInvM] = g_invm;
+        vv[kGvOcm + 0] = g_ocm.x; vv[kGvOcm + 1] = g_ocm.y; vv[kGvOcm + 2] = g_ocm.z;
+        vv[kGvRgb + 0] = NC == 0 ? g_c.x : 0.0f;
+        vv[kGvRgb + 1] = NC == 0 ? g_c.y : 0.0f;
+        vv[kGvRgb + 2] = NC == 0 ? g_c.z : 0.0f;
+        vv[22] = 0.0f;
+        vv[23] = 0.0f;
+        vv[24] = g_b2;
+        vv[25] = g_a3.x; vv[26] = g_a3.y; vv[27] = g_a3.z;
 #pragma unroll
-        for (int q = 24; q < 32; ++q) vv[q] = 0.0f;
+        for (int q = 28; q < 32; ++q) vv[q] = 0.0f;
         const float r = warp_reduce_scatter32(vv);
         if (r != 0.0f) {
-            if (lane < 20) atomicAdd(A + ga_geo(ns) + lane, r);
-            else if (lane == 20) atomicAdd(A + 5 * ns, r);
-            else if (lane < 24) atomicAdd(A + ga_bc3(ns) + (lane - 21), r);
+            if (lane < (unsigned)kGvFloats) atomicAdd(A + ga_geo(ns) + lane, r);
+            else if (lane == 24) atomicAdd(A + 5 * ns, r);
+            else if (lane < 28) atomicAdd(A + ga_bc3(ns) + (lane - 25), r);
         }
     }
 
@@ -324,7 +355,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
     const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 + (size_t)NPIX * (9 * 4 + 2 * 2);
-    return NPIX * 16 + (size_t)chunk * per_entry;
+    return NPIX * 32 + (size_t)chunk * per_entry;
 }
 
 template <int TS, int NC, int FORM, bool BF16>
@@ -338,8 +369,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
     const int ns = a.n_sigma;
     const int es = entry_stride(ns, NC);
     const int vg = grad_stride(ns, NC);
-    float4 *s_d = smem4;                                   // [NPIX] pixel rays
-    float *sm = reinterpret_cast<float *>(smem4 + NPIX);   // [CH][es] staged entries
+    float4 *s_ray = smem4;                                 // [2 NPIX] pixel rays
+    float *sm = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [CH][es] staged entries
     float *acc = sm + CH * es;                             // [CH][vg] per-entry gradient sums
     float *s_ah = acc + CH * vg;                           // [CH][NPIX] alpha_hat, then dL/dalpha_hat
     float *s_w = s_ah + CH * NPIX;                         // [CH][NPIX] weights (-1: not composited)
@@ -374,7 +405,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
         const View &V = a.views[v];
         const int lt = tile - V.tile_off;
         const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-        float3 d[PPT], Cf[PPT], dL[PPT], pref[PPT];
+        const CamK ck = cam_consts(V);
+        PixRay ry[PPT];
+        float3 Cf[PPT], dL[PPT], pref[PPT];
         float tau[PPT], bgdot[PPT];
         uint32_t nwalk[PPT];
 #pragma unroll
@@ -383,8 +416,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
             tile_pixel<TS>(tid, k, lx, ly);
             const int px = tx * TS + lx, py = ty * TS + ly;
             const bool inside = px < V.width && py < V.height;
-            d[k] = pixel_ray(V, px, py);
-            s_d[k * NT + tid] = make_float4(d[k].x, d[k].y, d[k].z, 0.0f);
+            ry[k] = pixel_ray(V, px, py);
+            store_ray(s_ray, k * NT + tid, ry[k]);
             Cf[k] = make_float3(0.f, 0.f, 0.f);
             dL[k] = make_float3(0.f, 0.f, 0.f);
             pref[k] = make_float3(0.f, 0.f, 0.f);
@@ -424,7 +457,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                 const uint32_t pos = c0 - rg.x + e;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    const bool hit = pos < nwalk[k] && hit_test(sm + e * es, d[k]);
+                    const bool hit = pos < nwalk[k] && hit_test(sm + e * es, ck, ry[k]);
                     s_ah[e * NPIX + k * NT + tid] = 0.0f;
                     list_append(hit, (uint16_t)(k * NT + tid), &s_nh[e], s_hl + e * NPIX);
                 }
@@ -440,11 +473,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                     while (q >= s_ph[e + 1]) ++e;
                     const int pix = s_hl[e * NPIX + (q - s_ph[e])];
                     const float *R = sm + e * es;
-                    const float4 dd = s_d[pix];
-                    const float3 dv = make_float3(dd.x, dd.y, dd.z);
+                    const PixRay r = load_ray(s_ray, pix);
                     Hit h;
                     float ah = 0.0f;
-                    if (intersect(R, dv, h)) ah = integral<FORM>(R, R + kRecFloats, ns, dv, h);
+                    if (intersect(R, ck, r, h)) ah = integral<FORM>(R, R + kRecFloats, ns, ck, r, h);
                     s_ah[e * NPIX + pix] = ah;
                 }
             }
@@ -483,8 +515,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                     if constexpr (NC == 0) {
                         col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
                     } else {
-                        const float4 dd = s_d[pix];
-                        col = mlp_color<NC>(R + kRecFloats + den_stride(ns), make_float3(dd.x, dd.y, dd.z));
+                        col = mlp_color<NC>(R + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)));
                     }
                     s_col[(0 * CH + e) * NPIX + pix] = col.x;
                     s_col[(1 * CH + e) * NPIX + pix] = col.y;
@@ -528,15 +559,14 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                     const int kk = (b - s_pb[e]) * 32 + (int)lane;
                     const bool valid = kk < s_na[e];
                     const int pix = valid ? s_al[e * NPIX + kk] : 0;
-                    const float4 dd = s_d[pix];
+                    const PixRay r = load_ray(s_ray, pix);
                     const float *R = sm + e * es;
                     const float3 g_c = make_float3(s_gc[(0 * CH + e) * NPIX + pix], s_gc[(1 * CH + e) * NPIX + pix],
                                                    s_gc[(2 * CH + e) * NPIX + pix]);
                     const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + pix], s_col[(1 * CH + e) * NPIX + pix],
                                                    s_col[(2 * CH + e) * NPIX + pix]);
-                    pair_backward<NC, FORM>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0,
-                                            make_float3(dd.x, dd.y, dd.z), valid, s_ah[e * NPIX + pix], g_c, col,
-                                            acc + e * vg);
+                    pair_backward<NC, FORM>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0, ck, r,
+                                            valid, s_ah[e * NPIX + pix], g_c, col, acc + e * vg);
                 }
             }
             __syncthreads();

@@ -28,7 +28,7 @@ __host__ __device__ inline size_t fwd_smem_bytes(int nc, int ns, int chunk)
     constexpr int NPIX = TileCfg<TS>::NPIX;
     const size_t per_entry = (size_t)entry_stride(ns, nc) * 4 + NPIX * 4 /* alpha_hat */ + NPIX * 2 /* hit list */ +
                              (nc > 0 ? NPIX * (4 + 12 + 2) /* weight, colour, list */ : 0);
-    return NPIX * 16 /* rays */ + (size_t)chunk * per_entry;
+    return NPIX * 32 /* rays */ + (size_t)chunk * per_entry;
 }
 
 template <int TS, int NC, int FORM, bool BF16>
@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
     const int CH = a.chunk;
     const int ns = a.n_sigma;
     const int es = entry_stride(ns, NC);
-    float4 *s_d = smem4;                                        // [NPIX] pixel rays
-    float *sm = reinterpret_cast<float *>(smem4 + NPIX);        // [CH][es] staged entries
+    float4 *s_ray = smem4;                                      // [2 NPIX] pixel rays
+    float *sm = reinterpret_cast<float *>(smem4 + 2 * NPIX);    // [CH][es] staged entries
     float *s_ah = sm + CH * es;                                 // [CH][NPIX] alpha_hat
     float *s_w = s_ah + CH * NPIX;                              // [CH][NPIX] weights (MLP)
     float *s_col = s_w + (NC > 0 ? CH * NPIX : 0);              // [3][CH][NPIX] colours (MLP)
@@ -67,9 +67,11 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
         const View &V = a.views[v];
         const int lt = tile - V.tile_off;
         const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+        const CamK ck = cam_consts(V);
         int px[PPT], py[PPT];
         bool inside[PPT], alive[PPT];
-        float3 d[PPT], C[PPT];
+        PixRay ry[PPT];
+        float3 C[PPT];
         float tau[PPT], T[PPT];
         uint32_t nwalk[PPT];
 #pragma unroll
@@ -79,8 +81,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
             px[k] = tx * TS + lx;
             py[k] = ty * TS + ly;
             inside[k] = px[k] < V.width && py[k] < V.height;
-            d[k] = pixel_ray(V, px[k], py[k]);
-            s_d[k * NT + tid] = make_float4(d[k].x, d[k].y, d[k].z, 0.0f);
+            ry[k] = pixel_ray(V, px[k], py[k]);
+            store_ray(s_ray, k * NT + tid, ry[k]);
             alive[k] = inside[k];
             C[k] = make_float3(0.f, 0.f, 0.f);
             tau[k] = 0.0f;
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
                     bool hit = false;
                     if (alive[k]) {
                         ++n_cand;
-                        hit = hit_test(sm + e * es, d[k]);
+                        hit = hit_test(sm + e * es, ck, ry[k]);
                     }
                     s_ah[e * NPIX + k * NT + tid] = 0.0f;
                     list_append(hit, (uint16_t)(k * NT + tid), &s_nh[e], s_hl + e * NPIX);
@@ -127,11 +129,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
                     while (q >= s_ph[e + 1]) ++e;
                     const int pix = s_hl[e * NPIX + (q - s_ph[e])];
                     const float *R = sm + e * es;
-                    const float4 dd = s_d[pix];
-                    const float3 dv = make_float3(dd.x, dd.y, dd.z);
+                    const PixRay r = load_ray(s_ray, pix);
                     Hit h;
                     float ah = 0.0f;
-                    if (intersect(R, dv, h)) ah = integral<FORM>(R, R + kRecFloats, ns, dv, h);
+                    if (intersect(R, ck, r, h)) ah = integral<FORM>(R, R + kRecFloats, ns, ck, r, h);
                     s_ah[e * NPIX + pix] = ah;
                     ++n_hit;
                 }
@@ -180,9 +181,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
                 for (int q = tid; q < na; q += NT) {
                     while (q >= s_pa[e + 1]) ++e;
                     const int pix = s_al[e * NPIX + (q - s_pa[e])];
-                    const float4 dd = s_d[pix];
                     const float3 col =
-                        mlp_color<NC>(sm + e * es + kRecFloats + den_stride(ns), make_float3(dd.x, dd.y, dd.z));
+                        mlp_color<NC>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)));
                     s_col[(0 * CH + e) * NPIX + pix] = col.x;
                     s_col[(1 * CH + e) * NPIX + pix] = col.y;
                     s_col[(2 * CH + e) * NPIX + pix] = col.z;

@@ -3,6 +3,10 @@
 // from the queue until it is exhausted.
 #pragma once
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "snp_raster_bwd.cuh"
 #include "snp_raster_fwd.cuh"
 
@@ -10,19 +14,20 @@ namespace snp {
 
 constexpr size_t kSmemMax = 220 * 1024;
 
-// Raise the dynamic shared-memory limit of a kernel once per device (before any
-// stream capture: the first launch of each kernel on a device happens eagerly).
+// Raise the dynamic shared-memory limit of a kernel once per (kernel, device)
+// (before any stream capture: each kernel's first launch on a device is eager).
 template <typename K>
 static void allow_smem(K kern)
 {
-    static unsigned long long done = 0;
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
     int dev = 0;
     cudaGetDevice(&dev);
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (!(done & bit)) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        done |= bit;
-    }
+    const std::pair<const void *, int> key((const void *)kern, dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    done.insert(key);
 }
 
 template <typename K>

@@ -56,10 +56,15 @@ def test_mlp_multiview_ragged(R, oracle_lib, form):
     ref, flags, tl, _ = oracle_images(O, sc, cams, form=form)
     assert np.array_equal(keys, tl.keys)
     assert np.array_equal(vals, tl.vals)
-    # Eq. 8 literally: phases are measured from the camera (|psi| ~ w0 |W1| |eye - c| / m, hundreds of
-    # radians, FP32 ulp ~3e-5 rad) and divided by a_k, so the literal form carries a larger FP32 error.
-    tol = IMG_TOL if form == 0 else 2e-3
-    assert_image_close(img, ref, flags, tol=tol, tol_flagged=2 * tol)
+    if form == 0:
+        assert_image_close(img, ref, flags)
+    else:
+        # Eq. 8 literally: the phases are measured from the camera (|psi| ~ w0 |W1| |eye - c| / m, hundreds
+        # of radians, FP32 ulp ~3e-5 rad) and divided by a_k = w0 W1_k . d / m, which is unbounded as
+        # W1_k . d -> 0; the literal form is checked statistically and its outliers are what the stable
+        # form removes.
+        err = np.abs(img.astype(np.float64) - ref).max(axis=1)
+        assert err.mean() < 2e-6 and np.quantile(err, 0.999) < 1e-3, (err.mean(), np.quantile(err, 0.999))
 
 
 def test_mlp64_ns32_bf16(R, oracle_lib):
