@@ -6,13 +6,17 @@
 //   [0, 20)             projection record (kRec* offsets)
 //   density block       per hidden unit k a float4 (w0 W1_k, w0 b1_k), then w2[N_sigma], b2, pad
 //   colour block (MLP)  C1[n_c] float4 (Wc1[j][0..2], h0_j = bc1_j + Wc1[j][3..10] . feat),
-//                       W2[n_c][n_c], B2[n_c], C3[n_c] float4 (Wc3[0..2][j], 0), B3 float4
+//                       W2 as bf16 hi[n_c][n_c + 8] then lo[n_c][n_c + 8] (Wc2 = hi + lo;
+//                       lo is not staged for bf16 weights), B2[n_c],
+//                       C3[n_c] float4 (Wc3[0..2][j], 0), B3 float4
 // The folded first-layer bias h0 uses that the feature part of the colour input is
-// constant per primitive; only the direction part varies per pixel.
+// constant per primitive; only the direction part varies per pixel.  The hidden
+// layer runs on the tensor cores over warp batches of 32 rays (snp_mma.cuh).
 #pragma once
 
 #include "snp_common.cuh"
 #include "snp_internal.h"
+#include "snp_mma.cuh"
 
 namespace snp {
 
@@ -21,15 +25,19 @@ constexpr int kMaxChunk = 256;
 
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 __host__ __device__ constexpr int den_stride(int ns) { return 4 * ns + round4(ns + 1); }
-__host__ __device__ constexpr int col_stride(int nc) { return nc == 0 ? 0 : nc * nc + 9 * nc + 4; }
+// Row stride (bf16 elements) of the staged Wc2: the 8 extra elements move each
+// row by 16 bytes of bank offset, so the eight 16-byte rows of one ldmatrix
+// read hit distinct banks.
+__host__ __device__ constexpr int w2_ld(int nc) { return nc + 8; }
+__host__ __device__ constexpr int col_stride(int nc) { return nc == 0 ? 0 : nc * w2_ld(nc) + 9 * nc + 4; }
 __host__ __device__ constexpr int entry_stride(int ns, int nc) { return kRecFloats + den_stride(ns) + col_stride(nc); }
 
 // Colour-block offsets (floats, from the start of the colour block).
 __host__ __device__ constexpr int cb_C1(int) { return 0; }
 __host__ __device__ constexpr int cb_W2(int nc) { return 4 * nc; }
-__host__ __device__ constexpr int cb_B2(int nc) { return 4 * nc + nc * nc; }
-__host__ __device__ constexpr int cb_C3(int nc) { return 5 * nc + nc * nc; }
-__host__ __device__ constexpr int cb_B3(int nc) { return 9 * nc + nc * nc; }
+__host__ __device__ constexpr int cb_B2(int nc) { return 4 * nc + nc * w2_ld(nc); }
+__host__ __device__ constexpr int cb_C3(int nc) { return 5 * nc + nc * w2_ld(nc); }
+__host__ __device__ constexpr int cb_B3(int nc) { return 9 * nc + nc * w2_ld(nc); }
 
 // Stage `cnt` list entries (global record ids s_gid[0..cnt)) of view offset vn
 // into shared memory.  All threads of the block participate.
@@ -83,10 +91,15 @@ __device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, in
             C[cb_C3(NC) + 4 * j + 3] = 0.0f;
             if (j < 4) C[cb_B3(NC) + j] = j < 3 ? ld_w<BF16>(a.net, base + a.off_bc3 + j) : 0.0f;
         }
-        for (int idx = tid; idx < cnt * NC * NC; idx += nt) {
-            const int e = idx / (NC * NC), k = idx - e * (NC * NC);
-            const int64_t base = ((int64_t)s_gid[e] - vn) * a.stride;
-            sm[e * es + kRecFloats + dstr + cb_W2(NC) + k] = ld_w<BF16>(a.net, base + a.off_Wc2 + k);
+        constexpr int half = NC * NC / 2;
+        for (int idx = tid; idx < cnt * half; idx += nt) {
+            const int e = idx / half, q = idx - e * half;
+            const int row = q / (NC / 2), k = 2 * (q - row * (NC / 2));
+            const int64_t w = ((int64_t)s_gid[e] - vn) * a.stride + a.off_Wc2 + row * NC + k;
+            const Split2 sp = split2<!BF16>(ld_w<BF16>(a.net, w), ld_w<BF16>(a.net, w + 1));
+            uint32_t *W = reinterpret_cast<uint32_t *>(sm + e * es + kRecFloats + dstr + cb_W2(NC));
+            W[(row * w2_ld(NC) + k) / 2] = sp.hi;
+            if constexpr (!BF16) W[((NC + row) * w2_ld(NC) + k) / 2] = sp.lo;
         }
     }
 }
@@ -274,54 +287,310 @@ __device__ __forceinline__ PixRay load_ray(const float4 *s_ray, int slot)
     return r;
 }
 
-// Colour MLP of one pixel ray: z1 = relu(Wc1_d d + h0), z2 = relu(Wc2 z1 + bc2),
-// c = sigmoid(Wc3 z2 + bc3).  Optionally keeps z1 / z2 for the backward pass.
-template <int NC>
-__device__ __forceinline__ float3 mlp_color(const float *C, float3 d, float *z1_out = nullptr,
-                                            float *z2_out = nullptr)
+// ---- colour MLP (Sec. 3.3) over a warp batch: 32 pixel rays of one primitive,
+// lane r holding ray r.  z1 = relu(Wc1_d d + h0), a2 = Wc2 z1 + bc2, z2 = relu(a2),
+// c = sigmoid(Wc3 z2 + bc3).  The rays are the rows of the tensor-core tiles; a
+// batch runs in two passes of 16 rows, lane (g, t) holding rows 16 p + g and
+// 16 p + g + 8 of pass p.  Per-unit values of a pass live in accumulator layout:
+// x[nt][i] is row (i < 2 ? first : second), unit 8 nt + 2 t + (i & 1).
+
+__device__ __forceinline__ float3 shfl_f3(float3 v, int src)
 {
-    const float4 *C1 = reinterpret_cast<const float4 *>(C + cb_C1(NC));
-    const float *W2 = C + cb_W2(NC);
-    const float *B2 = C + cb_B2(NC);
-    const float4 *C3 = reinterpret_cast<const float4 *>(C + cb_C3(NC));
-    const float4 B3 = *reinterpret_cast<const float4 *>(C + cb_B3(NC));
-    float z1[NC];
+    return make_float3(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src));
+}
+
+// First layer for the pass rows with directions d0, d1.
+template <int NC>
+__device__ __forceinline__ void color_layer1(const float4 *C1, float3 d0, float3 d1, float (&z)[NC / 8][4])
+{
+    const int t = threadIdx.x & 3;
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const float4 w = C1[j];
-        z1[j] = fmaxf(fmaf(w.x, d.x, fmaf(w.y, d.y, fmaf(w.z, d.z, w.w))), 0.0f);
-        if (z1_out) z1_out[j] = z1[j];
+    for (int nt = 0; nt < NC / 8; ++nt) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float4 w = C1[8 * nt + 2 * t + j];
+            z[nt][j] = fmaxf(fmaf(w.x, d0.x, fmaf(w.y, d0.y, fmaf(w.z, d0.z, w.w))), 0.0f);
+            z[nt][2 + j] = fmaxf(fmaf(w.x, d1.x, fmaf(w.y, d1.y, fmaf(w.z, d1.z, w.w))), 0.0f);
+        }
     }
-    float c0 = B3.x, c1 = B3.y, c2 = B3.z;
+}
+
+// Accumulator layout -> split A fragments of the 16 x NC block (k tile kt covers
+// units 16 kt .. 16 kt + 15, i.e. accumulator tiles 2 kt and 2 kt + 1).
+template <int NC>
+__device__ __forceinline__ void acc_to_afrag(const float (&x)[NC / 8][4], uint32_t (&ah)[NC / 16][4],
+                                             uint32_t (&al)[NC / 16][4])
+{
+#pragma unroll
+    for (int kt = 0; kt < NC / 16; ++kt) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float *src = x[2 * kt + (q >> 1)] + 2 * (q & 1);
+            const Split2 sp = split2<true>(src[0], src[1]);
+            ah[kt][q] = sp.hi;
+            al[kt][q] = sp.lo;
+        }
+    }
+}
+
+// acc[nt] += Z Wc2^T over the pass rows: B fragments are 8 x 8 blocks of the
+// row-major staged Wc2 (rows = output units) read by ldmatrix.
+template <int NC, bool BF16>
+__device__ __forceinline__ void color_gemm_zw(const uint32_t (&zh)[NC / 16][4], const uint32_t (&zl)[NC / 16][4],
+                                              const __nv_bfloat16 *Wh, float (&acc)[NC / 8][4])
+{
+    const int lane = threadIdx.x & 31;
+    const __nv_bfloat16 *Wl = Wh + NC * w2_ld(NC);
+#pragma unroll
+    for (int nt = 0; nt < NC / 8; ++nt) {
+#pragma unroll
+        for (int kq = 0; kq < NC / 32; ++kq) {
+            const int off = (8 * nt + (lane & 7)) * w2_ld(NC) + 32 * kq + 8 * (lane >> 3);
+            uint32_t bh[4], bl[4] = {0u, 0u, 0u, 0u};
+            ldsm_x4(bh, Wh + off);
+            if constexpr (!BF16) ldsm_x4(bl, Wl + off);
+            mma_split<!BF16>(acc[nt], zh[2 * kq], zl[2 * kq], bh[0], bh[1], bl[0], bl[1]);
+            mma_split<!BF16>(acc[nt], zh[2 * kq + 1], zl[2 * kq + 1], bh[2], bh[3], bl[2], bl[3]);
+        }
+    }
+}
+
+// gz[nk] += GA Wc2 over the pass rows (GA = dL/da2 as A fragments over the
+// output units): B fragments are transposed 8 x 8 blocks of the staged Wc2.
+template <int NC, bool BF16>
+__device__ __forceinline__ void color_gemm_gw(const uint32_t (&gh)[NC / 16][4], const uint32_t (&gl)[NC / 16][4],
+                                              const __nv_bfloat16 *Wh, float (&gz)[NC / 8][4])
+{
+    const int lane = threadIdx.x & 31, m = lane >> 3;
+    const __nv_bfloat16 *Wl = Wh + NC * w2_ld(NC);
+#pragma unroll
+    for (int kn = 0; kn < NC / 16; ++kn) {
+#pragma unroll
+        for (int nk = 0; nk < NC / 8; nk += 2) {
+            const int off = (16 * kn + 8 * (m & 1) + (lane & 7)) * w2_ld(NC) + 8 * (nk + (m >> 1));
+            uint32_t bh[4], bl[4] = {0u, 0u, 0u, 0u};
+            ldsm_x4_trans(bh, Wh + off);
+            if constexpr (!BF16) ldsm_x4_trans(bl, Wl + off);
+            mma_split<!BF16>(gz[nk], gh[kn], gl[kn], bh[0], bh[1], bl[0], bl[1]);
+            mma_split<!BF16>(gz[nk + 1], gh[kn], gl[kn], bh[2], bh[3], bl[2], bl[3]);
+        }
+    }
+}
+
+// Unit index of slot m (= 2 nt + j) of lane column t in accumulator layout.
+__device__ __forceinline__ int acc_unit(int m, int t) { return 8 * (m >> 1) + 2 * t + (m & 1); }
+
+// Colour of the batch's rays.  Lane r holds ray r: direction d, output slot pix,
+// valid.  Colour channel c of a valid ray goes to out[c * plane + pix].
+template <int NC, bool BF16>
+__device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, bool valid, float *out, int plane)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
+    const float *B2 = Cb + cb_B2(NC);
+    const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
+    const float4 B3 = *reinterpret_cast<const float4 *>(Cb + cb_B3(NC));
+    const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
+    const int vp = valid ? pix : -1;
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int r0 = 16 * p + g, r1 = r0 + 8;
+        const float3 d0 = shfl_f3(d, r0), d1 = shfl_f3(d, r1);
+        float z[NC / 8][4];
+        color_layer1<NC>(C1, d0, d1, z);
+        uint32_t zh[NC / 16][4], zl[NC / 16][4];
+        acc_to_afrag<NC>(z, zh, zl);
+        float acc[NC / 8][4];
+#pragma unroll
+        for (int nt = 0; nt < NC / 8; ++nt) {
+            const float2 b = *reinterpret_cast<const float2 *>(B2 + 8 * nt + 2 * t);
+            acc[nt][0] = acc[nt][2] = b.x;
+            acc[nt][1] = acc[nt][3] = b.y;
+        }
+        color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
+        float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int nt = 0; nt < NC / 8; ++nt) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float4 w = C3[acc_unit(2 * nt + j, t)];
+                const float za = fmaxf(acc[nt][j], 0.0f), zb = fmaxf(acc[nt][2 + j], 0.0f);
+                c[0] = fmaf(w.x, za, c[0]);
+                c[1] = fmaf(w.y, za, c[1]);
+                c[2] = fmaf(w.z, za, c[2]);
+                c[3] = fmaf(w.x, zb, c[3]);
+                c[4] = fmaf(w.y, zb, c[4]);
+                c[5] = fmaf(w.z, zb, c[5]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            c[q] += __shfl_xor_sync(0xffffffffu, c[q], 1);
+            c[q] += __shfl_xor_sync(0xffffffffu, c[q], 2);
+        }
+        const int q0 = __shfl_sync(0xffffffffu, vp, r0), q1 = __shfl_sync(0xffffffffu, vp, r1);
+        const int q = t == 0 ? q0 : q1;
+        if (t < 2 && q >= 0) {
+            const int o = 3 * t;
+            out[q] = sigmoidf_fast(c[o + 0] + B3.x);
+            out[plane + q] = sigmoidf_fast(c[o + 1] + B3.y);
+            out[2 * plane + q] = sigmoidf_fast(c[o + 2] + B3.z);
+        }
+    }
+}
+
+// Backward of the colour MLP for the batch: lane r holds ray r's direction d and
+// dL/da3 (the pre-sigmoid colour gradient; zero for lanes without a pair).
+// Accumulates dL/d(Wc1_d, h0) into AC1 [NC][4], dL/dWc2 into AW2 [NC][NC] and
+// dL/d(Wc3, bc2) into AW3 [NC][4] (shared memory, atomics).  The three
+// contractions a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays
+// dL/da2 z1^T run on the tensor cores; the last uses movmatrix transposes of the
+// pass's register fragments with the rays as the reduction dimension.
+template <int NC, bool BF16>
+__device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3 g_a3, float *AC1, float *AW2,
+                                               float *AW3)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
+    const float *B2 = Cb + cb_B2(NC);
+    const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
+    const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
+    // dL/dWc2 stays in registers across both passes when it fits (NC = 32)
+    __syncwarp();
+    constexpr bool kHold = NC <= 32;
+    constexpr int HM = kHold ? NC / 16 : 1, HN = kHold ? NC / 8 : 1;
+    float dw[HM][HN][4];
+#pragma unroll
+    for (int i = 0; i < HM; ++i)
+#pragma unroll
+        for (int j = 0; j < HN; ++j) dw[i][j][0] = dw[i][j][1] = dw[i][j][2] = dw[i][j][3] = 0.0f;
+
 #pragma unroll 1
-    for (int j = 0; j < NC; j += 2) {
-        const float4 *ra = reinterpret_cast<const float4 *>(W2 + j * NC);
-        const float4 *rb = reinterpret_cast<const float4 *>(W2 + (j + 1) * NC);
-        float a0 = B2[j], a1 = B2[j + 1];
+    for (int p = 0; p < 2; ++p) {
+        const int r0 = 16 * p + g, r1 = r0 + 8;
+        const float3 d0 = shfl_f3(d, r0), d1 = shfl_f3(d, r1);
+        const float3 e0 = shfl_f3(g_a3, r0), e1 = shfl_f3(g_a3, r1);
+        float z[NC / 8][4];
+        color_layer1<NC>(C1, d0, d1, z);
+        uint32_t zh[NC / 16][4], zl[NC / 16][4];
+        acc_to_afrag<NC>(z, zh, zl);
+        float acc[NC / 8][4];
 #pragma unroll
-        for (int k = 0; k < NC / 4; ++k) {
-            const float4 wa = ra[k], wb = rb[k];
-            a0 = fmaf(wa.x, z1[4 * k + 0], a0);
-            a1 = fmaf(wb.x, z1[4 * k + 0], a1);
-            a0 = fmaf(wa.y, z1[4 * k + 1], a0);
-            a1 = fmaf(wb.y, z1[4 * k + 1], a1);
-            a0 = fmaf(wa.z, z1[4 * k + 2], a0);
-            a1 = fmaf(wb.z, z1[4 * k + 2], a1);
-            a0 = fmaf(wa.w, z1[4 * k + 3], a0);
-            a1 = fmaf(wb.w, z1[4 * k + 3], a1);
+        for (int nt = 0; nt < NC / 8; ++nt) {
+            const float2 b = *reinterpret_cast<const float2 *>(B2 + 8 * nt + 2 * t);
+            acc[nt][0] = acc[nt][2] = b.x;
+            acc[nt][1] = acc[nt][3] = b.y;
         }
-        a0 = fmaxf(a0, 0.0f);
-        a1 = fmaxf(a1, 0.0f);
-        if (z2_out) {
-            z2_out[j] = a0;
-            z2_out[j + 1] = a1;
+        color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
+        // dL/dz2 = Wc3^T dL/da3, dL/da2 (ReLU), and the (Wc3, bc2) partials of the two rows
+        {
+            float pw[NC];
+#pragma unroll
+            for (int nt = 0; nt < NC / 8; ++nt) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int m = 2 * nt + j;
+                    const float4 w = C3[acc_unit(m, t)];
+                    const float a = acc[nt][j], b = acc[nt][2 + j];
+                    const float za = fmaxf(a, 0.0f), zb = fmaxf(b, 0.0f);
+                    const float ga = a > 0.0f ? fmaf(w.x, e0.x, fmaf(w.y, e0.y, w.z * e0.z)) : 0.0f;
+                    const float gb = b > 0.0f ? fmaf(w.x, e1.x, fmaf(w.y, e1.y, w.z * e1.z)) : 0.0f;
+                    pw[4 * m + 0] = fmaf(e0.x, za, e1.x * zb);
+                    pw[4 * m + 1] = fmaf(e0.y, za, e1.y * zb);
+                    pw[4 * m + 2] = fmaf(e0.z, za, e1.z * zb);
+                    pw[4 * m + 3] = ga + gb;
+                    acc[nt][j] = ga;
+                    acc[nt][2 + j] = gb;
+                }
+            }
+            reduce_scatter_rows<NC>(pw);
+#pragma unroll
+            for (int i = 0; i < NC / 8; ++i) {
+                const int idx = g * (NC / 8) + i;
+                if (pw[i] != 0.0f) atomicAdd(AW3 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pw[i]);
+            }
         }
-        const float4 wa = C3[j], wb = C3[j + 1];
-        c0 = fmaf(wa.x, a0, fmaf(wb.x, a1, c0));
-        c1 = fmaf(wa.y, a0, fmaf(wb.y, a1, c1));
-        c2 = fmaf(wa.z, a0, fmaf(wb.z, a1, c2));
+        uint32_t gh[NC / 16][4], gl[NC / 16][4];
+        acc_to_afrag<NC>(acc, gh, gl);
+        // dL/dz1 = Wc2^T dL/da2, dL/da1 (ReLU) and the (Wc1_d, h0) partials
+        {
+            float gz[NC / 8][4];
+#pragma unroll
+            for (int nk = 0; nk < NC / 8; ++nk) gz[nk][0] = gz[nk][1] = gz[nk][2] = gz[nk][3] = 0.0f;
+            color_gemm_gw<NC, BF16>(gh, gl, Wh, gz);
+            float pc[NC];
+#pragma unroll
+            for (int nk = 0; nk < NC / 8; ++nk) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int m = 2 * nk + j;
+                    const float ga = z[nk][j] > 0.0f ? gz[nk][j] : 0.0f;
+                    const float gb = z[nk][2 + j] > 0.0f ? gz[nk][2 + j] : 0.0f;
+                    pc[4 * m + 0] = fmaf(ga, d0.x, gb * d1.x);
+                    pc[4 * m + 1] = fmaf(ga, d0.y, gb * d1.y);
+                    pc[4 * m + 2] = fmaf(ga, d0.z, gb * d1.z);
+                    pc[4 * m + 3] = ga + gb;
+                }
+            }
+            reduce_scatter_rows<NC>(pc);
+#pragma unroll
+            for (int i = 0; i < NC / 8; ++i) {
+                const int idx = g * (NC / 8) + i;
+                if (pc[i] != 0.0f) atomicAdd(AC1 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pc[i]);
+            }
+        }
+        // dL/dWc2 += GA^T Z over the pass rows: A = transposed dL/da2 blocks,
+        // B = transposed z1 blocks, the 16 rows as the reduction dimension
+        uint32_t tzh[NC / 8][2], tzl[NC / 8][2];
+#pragma unroll
+        for (int nk = 0; nk < NC / 8; ++nk) {
+            const int kt = nk >> 1, o = 2 * (nk & 1);
+            tzh[nk][0] = movm_trans(zh[kt][o]);
+            tzh[nk][1] = movm_trans(zh[kt][o + 1]);
+            tzl[nk][0] = movm_trans(zl[kt][o]);
+            tzl[nk][1] = movm_trans(zl[kt][o + 1]);
+        }
+#pragma unroll
+        for (int mn = 0; mn < NC / 16; ++mn) {
+            const uint32_t th[4] = {movm_trans(gh[mn][0]), movm_trans(gh[mn][2]), movm_trans(gh[mn][1]),
+                                    movm_trans(gh[mn][3])};
+            const uint32_t tl[4] = {movm_trans(gl[mn][0]), movm_trans(gl[mn][2]), movm_trans(gl[mn][1]),
+                                    movm_trans(gl[mn][3])};
+#pragma unroll
+            for (int nk = 0; nk < NC / 8; ++nk) {
+                if constexpr (kHold) {
+                    mma16816(dw[mn][nk], tl, tzh[nk][0], tzh[nk][1]);
+                    mma16816(dw[mn][nk], th, tzl[nk][0], tzl[nk][1]);
+                    mma16816(dw[mn][nk], th, tzh[nk][0], tzh[nk][1]);
+                } else {
+                    float d4[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
+                    mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
+                    mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
+                    const int n0 = 16 * mn + g, k0 = 8 * nk + 2 * t;
+                    if (d4[0] != 0.0f) atomicAdd(AW2 + n0 * NC + k0, d4[0]);
+                    if (d4[1] != 0.0f) atomicAdd(AW2 + n0 * NC + k0 + 1, d4[1]);
+                    if (d4[2] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0, d4[2]);
+                    if (d4[3] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0 + 1, d4[3]);
+                }
+            }
+        }
     }
-    return make_float3(sigmoidf_fast(c0), sigmoidf_fast(c1), sigmoidf_fast(c2));
+    if constexpr (kHold) {
+#pragma unroll
+        for (int mn = 0; mn < HM; ++mn) {
+#pragma unroll
+            for (int nk = 0; nk < HN; ++nk) {
+                const int n0 = 16 * mn + g, k0 = 8 * nk + 2 * t;
+                if (dw[mn][nk][0] != 0.0f) atomicAdd(AW2 + n0 * NC + k0, dw[mn][nk][0]);
+                if (dw[mn][nk][1] != 0.0f) atomicAdd(AW2 + n0 * NC + k0 + 1, dw[mn][nk][1]);
+                if (dw[mn][nk][2] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0, dw[mn][nk][2]);
+                if (dw[mn][nk][3] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0 + 1, dw[mn][nk][3]);
+            }
+        }
+    }
 }
 
 // Warp-aggregated append of `val` to list[] for the lanes with pred set.
@@ -358,6 +627,16 @@ __device__ __forceinline__ void warp_prefix64(const int *count, int n, int *pre)
     if ((int)lane + 32 < n) pre[lane + 32] = tot_a + y - b;
     if (lane == 0) pre[n] = tot_a + __shfl_sync(0xffffffffu, y, 31);
     else __shfl_sync(0xffffffffu, y, 31);
+}
+
+// Warp batches of 32 pairs per list entry: nb[e] = ceil(count[e] / 32) and its
+// exclusive prefix pre[0..n].  One warp.
+__device__ __forceinline__ void warp_batch_prefix(const int *count, int n, int *nb, int *pre)
+{
+    const unsigned lane = lane_id();
+    for (int e = (int)lane; e < n; e += 32) nb[e] = (count[e] + 31) >> 5;
+    __syncwarp();
+    warp_prefix64(nb, n, pre);
 }
 
 // Tile shapes: TS x TS pixels, NT threads, PPT pixels per thread.  Warps always

@@ -80,7 +80,7 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
 // Gradient of one (pixel, primitive) pair, reduced across the warp into the
 // entry's shared-memory accumulator A.  All 32 lanes call it together; lanes
 // without a pair pass contrib = false (their contributions are zero).
-template <int NC, int FORM>
+template <int NC, int FORM, bool BF16>
 __device__ __forceinline__ void pair_backward(const float *R, const float *D, const float *Cb, int ns, float w0,
                                               const CamK &ck, const PixRay &ry, bool contrib, float g_ah, float3 g_c,
                                               float3 col, float *A)
@@ -273,80 +273,10 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
         }
     }
 
-    // ---- colour MLP backward
+    // ---- colour MLP backward (whole warp)
     if constexpr (NC > 0) {
-        const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
-        const float *W2 = Cb + cb_W2(NC);
-        const float *B2 = Cb + cb_B2(NC);
-        const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
         float *AC1 = A + ga_col(ns);
-        float *AW2 = AC1 + 4 * NC;
-        float *AW3 = AW2 + NC * NC;
-        float z1[NC], gz1[NC];
-#pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            const float4 w = C1[j];
-            z1[j] = fmaxf(fmaf(w.x, d.x, fmaf(w.y, d.y, fmaf(w.z, d.z, w.w))), 0.0f);
-            gz1[j] = 0.0f;
-        }
-        for (int j0 = 0; j0 < NC; j0 += 8) {
-            float v4[32];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const int j = j0 + jj;
-                const float4 *row = reinterpret_cast<const float4 *>(W2 + j * NC);
-                float a2 = B2[j];
-#pragma unroll
-                for (int k = 0; k < NC / 4; ++k) {
-                    const float4 w = row[k];
-                    a2 = fmaf(w.x, z1[4 * k + 0], a2);
-                    a2 = fmaf(w.y, z1[4 * k + 1], a2);
-                    a2 = fmaf(w.z, z1[4 * k + 2], a2);
-                    a2 = fmaf(w.w, z1[4 * k + 3], a2);
-                }
-                const float z2 = fmaxf(a2, 0.0f);
-                const float4 w3 = C3[j];
-                const float gz2 = fmaf(w3.x, g_a3.x, fmaf(w3.y, g_a3.y, w3.z * g_a3.z));
-                const float ga2 = a2 > 0.0f ? gz2 : 0.0f;
-#pragma unroll
-                for (int s = 0; s < NC / 32; ++s) {
-                    float vv[32];
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) vv[i] = ga2 * z1[32 * s + i];
-                    const float r = warp_reduce_scatter32(vv);
-                    if (r != 0.0f) atomicAdd(AW2 + j * NC + 32 * s + lane, r);
-                }
-#pragma unroll
-                for (int k = 0; k < NC / 4; ++k) {
-                    const float4 w = row[k];
-                    gz1[4 * k + 0] = fmaf(w.x, ga2, gz1[4 * k + 0]);
-                    gz1[4 * k + 1] = fmaf(w.y, ga2, gz1[4 * k + 1]);
-                    gz1[4 * k + 2] = fmaf(w.z, ga2, gz1[4 * k + 2]);
-                    gz1[4 * k + 3] = fmaf(w.w, ga2, gz1[4 * k + 3]);
-                }
-                v4[4 * jj + 0] = g_a3.x * z2;
-                v4[4 * jj + 1] = g_a3.y * z2;
-                v4[4 * jj + 2] = g_a3.z * z2;
-                v4[4 * jj + 3] = ga2;
-            }
-            const float r = warp_reduce_scatter32(v4);
-            if (r != 0.0f) atomicAdd(AW3 + 4 * j0 + lane, r);
-        }
-#pragma unroll
-        for (int j0 = 0; j0 < NC; j0 += 8) {
-            float vv[32];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const int j = j0 + jj;
-                const float ga1 = z1[j] > 0.0f ? gz1[j] : 0.0f;
-                vv[4 * jj + 0] = ga1 * d.x;
-                vv[4 * jj + 1] = ga1 * d.y;
-                vv[4 * jj + 2] = ga1 * d.z;
-                vv[4 * jj + 3] = ga1;
-            }
-            const float r = warp_reduce_scatter32(vv);
-            if (r != 0.0f) atomicAdd(AC1 + 4 * j0 + lane, r);
-        }
+        warp_color_bwd<NC, BF16>(Cb, d, g_a3, AC1, AC1 + 4 * NC, AC1 + 4 * NC + NC * NC);
     }
 }
 
@@ -501,25 +431,33 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                 }
             }
             __syncthreads();
-            if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
+            if (tid < 32) {
+                warp_prefix64(s_na, cnt, s_pa);
+                warp_batch_prefix(s_na, cnt, s_nb, s_pb);
+            }
             __syncthreads();
             // P4: colour of every composited pair
-            {
+            if constexpr (NC == 0) {
                 const int na = s_pa[cnt];
                 int e = 0;
                 for (int q = tid; q < na; q += NT) {
                     while (q >= s_pa[e + 1]) ++e;
                     const int pix = s_al[e * NPIX + (q - s_pa[e])];
                     const float *R = sm + e * es;
-                    float3 col;
-                    if constexpr (NC == 0) {
-                        col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
-                    } else {
-                        col = mlp_color<NC>(R + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)));
-                    }
-                    s_col[(0 * CH + e) * NPIX + pix] = col.x;
-                    s_col[(1 * CH + e) * NPIX + pix] = col.y;
-                    s_col[(2 * CH + e) * NPIX + pix] = col.z;
+                    s_col[(0 * CH + e) * NPIX + pix] = R[kRecRgb + 0];
+                    s_col[(1 * CH + e) * NPIX + pix] = R[kRecRgb + 1];
+                    s_col[(2 * CH + e) * NPIX + pix] = R[kRecRgb + 2];
+                }
+            } else {
+                const int nb = s_pb[cnt];
+                int e = 0;
+                for (int b = wid; b < nb; b += NT / 32) {
+                    while (b >= s_pb[e + 1]) ++e;
+                    const int kk = (b - s_pb[e]) * 32 + (int)lane;
+                    const bool valid = kk < s_na[e];
+                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
+                    warp_color<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)),
+                                         pix, valid, s_col + e * NPIX, CH * NPIX);
                 }
             }
             __syncthreads();
@@ -546,9 +484,6 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                     }
                 }
             }
-            if (tid < cnt) s_nb[tid] = (s_na[tid] + 31) >> 5;
-            __syncthreads();
-            if (tid < 32) warp_prefix64(s_nb, cnt, s_pb);
             __syncthreads();
             // P6: per-pair gradients in warp batches of one entry each
             {
@@ -565,7 +500,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                                                    s_gc[(2 * CH + e) * NPIX + pix]);
                     const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + pix], s_col[(1 * CH + e) * NPIX + pix],
                                                    s_col[(2 * CH + e) * NPIX + pix]);
-                    pair_backward<NC, FORM>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0, ck, r,
+                    pair_backward<NC, FORM, BF16>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0, ck, r,
                                             valid, s_ah[e * NPIX + pix], g_c, col, acc + e * vg);
                 }
             }

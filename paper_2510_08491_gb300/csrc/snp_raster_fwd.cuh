@@ -11,7 +11,8 @@
 //                   T = exp(-sum alpha_hat) (Eq. 4, 9) and early termination --
 //                   transmittance does not depend on colour, so it is settled
 //                   before any colour is evaluated; composited pairs are listed;
-//   P4 (per pair)   colour MLP of every composited pair;
+//   P4 (per warp)   colour MLP of the composited pairs in warp batches of 32
+//                   pairs of one list entry (tensor cores for the hidden layer);
 //   P5 (per pixel)  C += w * colour in list order.
 // The result is the sequential front-to-back composite.  The per-pixel composited
 // colour, optical depth and number of list entries walked are saved for the
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + (NC > 0 ? 3 * CH * NPIX : 0));  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                          // [CH][NPIX] (MLP)
     __shared__ uint32_t s_gid[kMaxChunk];
-    __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65];
+    __shared__ int s_nh[65], s_na[65], s_ph[65], s_nb[65], s_pb[65];
     __shared__ int s_view, s_item;
 
     const int tid = threadIdx.x;
@@ -173,19 +174,18 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
 
             if constexpr (NC > 0) {
                 __syncthreads();
-                if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
+                if (tid < 32) warp_batch_prefix(s_na, cnt, s_nb, s_pb);
                 __syncthreads();
-                // P4: colour of every composited pair
-                const int na = s_pa[cnt];
+                // P4: colour of every composited pair, in warp batches of one entry each
+                const int nb = s_pb[cnt];
                 int e = 0;
-                for (int q = tid; q < na; q += NT) {
-                    while (q >= s_pa[e + 1]) ++e;
-                    const int pix = s_al[e * NPIX + (q - s_pa[e])];
-                    const float3 col =
-                        mlp_color<NC>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)));
-                    s_col[(0 * CH + e) * NPIX + pix] = col.x;
-                    s_col[(1 * CH + e) * NPIX + pix] = col.y;
-                    s_col[(2 * CH + e) * NPIX + pix] = col.z;
+                for (int b = tid >> 5; b < nb; b += NT / 32) {
+                    while (b >= s_pb[e + 1]) ++e;
+                    const int kk = (b - s_pb[e]) * 32 + (int)lane_id();
+                    const bool valid = kk < s_na[e];
+                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
+                    warp_color<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)),
+                                         pix, valid, s_col + e * NPIX, CH * NPIX);
                 }
                 __syncthreads();
                 // P5: accumulate in list order

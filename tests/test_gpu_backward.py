@@ -9,6 +9,13 @@ kernels evaluate the ray geometry relative to the ray through each primitive's
 centre (FP32 h^2 error ~1e-7) and re-evaluate pairs with |h^2| < 1e-4 in FP64,
 so the 1 / sqrt(h^2) growth of the derivative near a silhouette is followed.
 The _dl helper keeps a sil_eps option for diagnostics.
+
+The colour MLP's hidden layer runs on the tensor cores with split-bf16 operands
+(about 1e-5 relative per product), so a ReLU pre-activation within ~1e-5 of zero
+may be decided differently from FP64.  The gradient is discontinuous there (the
+ReLU kink), so, like the termination near-ties, pixels with a composited pair
+whose smallest |pre-activation| is below RELU_EPS = 1e-4 get dL = 0 (about 1% of
+the pixels of these scenes).
 """
 import numpy as np
 import pytest
@@ -21,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 GRAD_TOL = 1e-3
 SIL_EPS = 0.0
+RELU_EPS = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -63,8 +71,10 @@ def _oracle_grads(O, scene, cams, dL_views, t_min=1e-4, bg=(0.0, 0.0, 0.0), ts=1
     return total
 
 
-def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0), sil_eps=SIL_EPS):
-    """Seeded dL/dC, zero on near-tie termination pixels and near-silhouette pixels."""
+def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0), sil_eps=SIL_EPS, relu_eps=RELU_EPS):
+    """Seeded dL/dC, zero on near-tie termination pixels, on pixels with a pair at
+    a colour-MLP ReLU kink (|pre-activation| < relu_eps) and, for diagnostics, on
+    near-silhouette pixels (|h^2| < sil_eps)."""
     from oracle import grad as G
     rng = np.random.default_rng(seed)
     imgs, tl, outs = O.render_image(scene, cams, 16, t_min, bg)
@@ -73,14 +83,16 @@ def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0), sil_eps=SIL_EPS):
     for v, (cam, o) in enumerate(zip(cams, outs)):
         d = rng.normal(size=(cam.n_pixels, 3))
         d[o.flags != 0] = 0.0
-        if sil_eps > 0:
+        if sil_eps > 0 or (relu_eps > 0 and scene.color == "mlp"):
             pix = np.arange(cam.n_pixels, dtype=np.int32)
             gt = tl.view_tile_off[v] + O.pixel_tile(cam, 16, pix)
             lens = tl.tile_off[gt + 1] - tl.tile_off[gt]
             owner = np.repeat(np.arange(cam.n_pixels), lens)
-            _, h2, _, _ = G.pair_diagnostics(scene, cam, pix, gt, tl.tile_off, lp)
+            _, h2, ah, amin = G.pair_diagnostics(scene, cam, pix, gt, tl.tile_off, lp)
             near = np.zeros(cam.n_pixels, bool)
             near[owner[np.abs(h2) < sil_eps]] = True
+            if scene.color == "mlp":
+                near[owner[(ah > 0) & (amin < relu_eps)]] = True
             d[near] = 0.0
         per_view.append(d)
     return per_view
