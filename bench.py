@@ -8,6 +8,13 @@ rasterizer -> backward rasterizer -> per-primitive gradient post-passes, on the
 N_c = 32, FP32).  Prints one JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--graph] [--autotune]
+
+Other workloads (paper_2510_08491_gb300.synth.workload): diff300k_720p adds the
+squared-error loss against a render of the perturbed scene to the step;
+batch500k_16view (16 views of uneven size, BF16 weights, N_sigma = 32, N_c = 64)
+is timed as replays of one captured CUDA graph with the tile size and chunk
+picked by the autotuner.
 """
 from __future__ import annotations
 
@@ -25,6 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpixel/s fwd and fwd+bwd at 1080p, 100k–500k primitives vs plain FP32 fwd; % roofline"
 WORKLOAD = "fwd100k_1080p_4view"
+# workloads timed as graph replays with an autotuned tile size and chunk
+BATCHED = ("batch500k_16view",)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -157,9 +166,22 @@ def run_ours(args, rank, world):
     r = Renderer(dev)
     ps = pack_scene(sc)
     P = sum(c.n_pixels for c in cams)
-    cfg = L.make_config(t_min=wl.t_min, timing=True)
+    batched = args.workload in BATCHED
+    use_graph = args.graph or batched
+    cfg = L.make_config(t_min=wl.t_min, timing=not use_graph)
+    if args.autotune or batched:
+        cfg = r.autotune(ps, cams, cfg, backward=True)
+        cfg.flags = L.FLAG_STAGE_TIMING if not use_graph else 0
     img = torch.empty((P, 3), device="cuda", dtype=torch.float32)
-    dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 1e-3
+    target = None
+    if wl.target_scene is not None:
+        # the differentiation workload: squared error against a render of the perturbed scene
+        target = r.forward(pack_scene(wl.target_scene), cams, L.make_config(t_min=wl.t_min)).clone()
+        dL = torch.empty((P, 3), device="cuda", dtype=torch.float32)
+        loss = torch.zeros(1, device="cuda", dtype=torch.float32)
+    else:
+        dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 1e-3
+        loss = None
     g_geom = torch.zeros_like(ps.geom)
     g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -168,6 +190,8 @@ def run_ours(args, rank, world):
         g_geom.zero_()
         g_net.zero_()
         r.forward(ps, cams, cfg, out=img)
+        if target is not None:
+            r.mse_loss(img, target, dL, loss)
         r.backward(ps, dL, g_geom, g_net)
 
     def fwd_only():
@@ -178,6 +202,20 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     stats = r.stats()
     counts = {"cand": stats.n_candidates, "hit": stats.n_hits, "comp": stats.n_composited}
+    graph = None
+    if use_graph:
+        from paper_2510_08491_gb300.render import GraphStep
+        graph = GraphStep(r, ps, cams, cfg, max_keys=int(stats.n_keys * 1.05) + 4096,
+                          dL=None if target is not None else dL, target=target)
+        img, g_geom, g_net = graph.image, graph.g_geom, graph.g_net
+        if target is not None:
+            dL, loss = graph.dL, graph.loss
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        timed_step = graph.replay
+    else:
+        timed_step = step
     dist = world > 1
     if dist:
         import torch.distributed as D
@@ -190,14 +228,28 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            step()
+            timed_step()
         e1.record(stream)
         torch.cuda.synchronize()
         if dist:
             D.barrier()
-    launches = (L.kernel_launches() - l0) // max(args.steps, 1)
     ms = e0.elapsed_time(e1) / args.steps
-    st = r.ctx.stage_times(reset=True)
+    if graph is not None:
+        # graph replays launch no kernel through the library's counter; count one eager step
+        l0 = L.kernel_launches()
+        step()
+        torch.cuda.synchronize()
+        launches = L.kernel_launches() - l0
+        # per-kernel device times from eager steps with stage timing (same kernels, same config)
+        cfg.flags = L.FLAG_STAGE_TIMING
+        r.ctx.stage_times(reset=True)
+        for _ in range(max(min(args.steps, 5), 2)):
+            step()
+        torch.cuda.synchronize()
+        st = r.ctx.stage_times(reset=True)
+    else:
+        launches = (L.kernel_launches() - l0) // max(args.steps, 1)
+        st = r.ctx.stage_times(reset=True)
     if dist:
         t = torch.tensor([ms], device="cuda")
         D.all_reduce(t, op=D.ReduceOp.MAX)
@@ -218,22 +270,28 @@ def run_ours(args, rank, world):
     ms_fwd = f0.elapsed_time(f1) / nf
     r.ctx.stage_times(reset=True)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: parameters and the
+    # step's image input (dL/dimage, or the target image of the loss) in, image,
+    # gradients (and loss) out
     h_geom = ps.geom.cpu().pin_memory()
     h_net = ps.net.cpu().pin_memory()
-    h_dL = dL.cpu().pin_memory()
+    d_in = target if target is not None else dL
+    h_in = d_in.cpu().pin_memory()
     h_img = torch.empty((P, 3), dtype=torch.float32).pin_memory()
     h_gg = torch.empty_like(g_geom, device="cpu").pin_memory()
     h_gn = torch.empty_like(g_net, device="cpu").pin_memory()
+    h_loss = torch.empty(1, dtype=torch.float32).pin_memory()
 
     def e2e_step():
         ps.geom.copy_(h_geom, non_blocking=True)
         ps.net.copy_(h_net, non_blocking=True)
-        dL.copy_(h_dL, non_blocking=True)
-        step()
+        d_in.copy_(h_in, non_blocking=True)
+        timed_step()
         h_img.copy_(img, non_blocking=True)
         h_gg.copy_(g_geom, non_blocking=True)
         h_gn.copy_(g_net, non_blocking=True)
+        if loss is not None:
+            h_loss.copy_(loss, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -246,8 +304,8 @@ def run_ours(args, rank, world):
     x1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = x0.elapsed_time(x1) / ne
-    h2d = h_geom.numel() * h_geom.element_size() + h_net.numel() * h_net.element_size() + h_dL.numel() * 4
-    d2h = h_img.numel() * 4 + h_gg.numel() * 4 + h_gn.numel() * 4
+    h2d = h_geom.numel() * h_geom.element_size() + h_net.numel() * h_net.element_size() + h_in.numel() * 4
+    d2h = h_img.numel() * 4 + h_gg.numel() * 4 + h_gn.numel() * 4 + (4 if loss is not None else 0)
 
     # roofline of the dominant kernel (FP32 ALU bound)
     fwd_u, bwd_u = fma_per_unit(sc.n_sigma, sc.n_c if sc.color == "mlp" else 0)
@@ -279,9 +337,13 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "primitives": sc.n, "views": len(cams),
                    "resolution": f"{cams[0].width}x{cams[0].height}", "n_sigma": sc.n_sigma,
-                   "n_c": sc.n_c if sc.color == "mlp" else 0, "tile": 16, "step": "forward+backward",
+                   "n_c": sc.n_c if sc.color == "mlp" else 0, "weights": sc.weight_dtype,
+                   "tile": int(cfg.tile_size), "chunk": int(cfg.chunk),
+                   "step": "forward+loss+backward" if target is not None else "forward+backward",
+                   "graph": graph is not None, "autotuned": bool(args.autotune or batched),
                    "parallelism": "replicas" if world > 1 else "single-gpu",
-                   "l2": "inputs larger than L2 (network weights %.2f GB)" % (h_net.numel() * 4 / 1e9)},
+                   "l2": "inputs larger than L2 (network weights %.2f GB)" % (h_net.numel() * h_net.element_size()
+                                                                              / 1e9)},
         "fwd_mpix_s": round(world * P / (ms_fwd * 1e-3) / 1e6, 3),
         "fwd_ms": round(ms_fwd, 4),
         "roofline": {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3),
@@ -296,7 +358,9 @@ def run_ours(args, rank, world):
         "work": {"keys": stats.n_keys, "candidates": counts["cand"], "hits": counts["hit"],
                  "composited": counts["comp"], "pixels": P},
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if loss is not None:
+        res["loss"] = float(h_loss.item())
+    if rank == 0 and not args.no_cpu_baseline and (args.workload == WORKLOAD or args.cpu_baseline):
         npx, secs, cores = oracle_sample(wl, args.cpu_tiles)
         res["cpu_baseline"] = {"value": round(npx / secs / 1e6, 6), "unit": "Mpixel/s", "cores": cores,
                                "kind": "oracle",
@@ -337,6 +401,10 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=16)
     ap.add_argument("--ref-tiles", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline", action="store_true",
+                    help="also time the oracle sample on a workload other than the default one")
+    ap.add_argument("--graph", action="store_true", help="time replays of a captured CUDA graph of the step")
+    ap.add_argument("--autotune", action="store_true", help="pick tile size and chunk with snp_autotune first")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -251,6 +251,24 @@ snp_status snp_stage_times(snp_context *ctx, double *ms, int64_t *calls, int32_t
  * contexts), for accounting of work per step. */
 int64_t snp_kernel_launches(void);
 
+/* Photometric loss of the differentiation workload: the mean squared error
+ *   L = (1 / n) sum_i (image_i - target_i)^2
+ * over n = 3 * pixels values, and its gradient dL/dimage_i = 2 (image_i - target_i) / n,
+ * which is the dL_dimages input of snp_render_backward.  (The paper trains with
+ * the photometric loss of 3D Gaussian splatting (Sec. 3.3, Training); the squared
+ * error is the loss of the 300k-primitive, 1280 x 720 differentiation workload.)
+ *   image, target  device, n floats each (HWC, views concatenated), caller-owned
+ *   dL_dimage      device, n floats, caller-owned, overwritten
+ *   loss           device, one float, caller-owned, overwritten
+ *   stream         cudaStream_t; asynchronous, no allocation and no host
+ *                  synchronisation (capturable in a CUDA graph)
+ * The sum runs in FP64 in a fixed order (deterministic).  Calls on one context
+ * share its reduction slots: do not run two at once on different streams.
+ * n = 0 writes loss = 0.  Errors: SNP_ERR_INVALID_ARG for a null pointer or
+ * n < 0, SNP_ERR_CUDA if the launch fails. */
+snp_status snp_mse_loss(snp_context *ctx, const float *image, const float *target, int64_t n, float *dL_dimage,
+                        float *loss, void *stream);
+
 /* Allocation-free sort (the paper has no counterpart: this is a library
  * service).  Sorts n (key, value) pairs in place by the low key_bits bits of the
  * key, stably (equal keys keep their input order) -- the same LSD radix sort

@@ -81,6 +81,7 @@ _SIGS = {
     "snp_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32],
     "snp_autotune": [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(ScenePtrs), C.POINTER(Camera), C.c_int32,
                      C.POINTER(Config), C.c_int32, C.POINTER(Config), C.POINTER(C.c_float), C.c_void_p],
+    "snp_mse_loss": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
 }
 FLAG_STAGE_TIMING = 1
 FLAG_LENGTH_QUEUE = 2

@@ -128,6 +128,8 @@ struct snp_context {
     // device workspace
     Buf views, rec, trect, counts, offsets, scan_tmp, keys, vals, keys_alt, vals_alt, hist, hist_scan, ranges,
         px_state, px_nwalk, stats, small, g_view, g_h0, qkeys, qvals, qkeys_alt, qvals_alt, qhist, qhist_scan;
+    // loss reduction: kLossSlots FP64 block sums, then the completion counter
+    Buf loss_part;
     // pinned host staging
     View *h_views = nullptr;
     uint32_t *h_small = nullptr;
@@ -322,10 +324,13 @@ snp_status snp_create(int32_t device, snp_context **out)
     ctx->device = device;
     if (cudaMallocHost((void **)&ctx->h_views, sizeof(View) * kMaxViews) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->h_small, 64) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_views, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_views, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&ctx->loss_part.p, kLossSlots * 8 + 16) != cudaSuccess ||
+        cudaMemset(ctx->loss_part.p, 0, kLossSlots * 8 + 16) != cudaSuccess) {
         snp_destroy(ctx);
         return SNP_ERR_CUDA;
     }
+    ctx->loss_part.bytes = kLossSlots * 8 + 16;
     *out = ctx;
     return SNP_OK;
 }
@@ -338,7 +343,8 @@ void snp_destroy(snp_context *ctx)
     Buf *bufs[] = {&ctx->views, &ctx->rec, &ctx->trect, &ctx->counts, &ctx->offsets, &ctx->scan_tmp, &ctx->keys,
                    &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
                    &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0,
-                   &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan};
+                   &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan,
+                   &ctx->loss_part};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_views) cudaFreeHost(ctx->h_views);
@@ -737,6 +743,26 @@ snp_status snp_stage_times(snp_context *ctx, double *ms, int64_t *calls, int32_t
 }
 
 int64_t snp_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+snp_status snp_mse_loss(snp_context *ctx, const float *image, const float *target, int64_t n, float *dL_dimage,
+                        float *loss, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n < 0) return fail(ctx, SNP_ERR_INVALID_ARG, "negative value count %lld", (long long)n);
+    if (!loss || (n > 0 && (!image || !target || !dL_dimage))) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    CK(cudaSetDevice(ctx->device));
+    if (n == 0) {
+        CK(cudaMemsetAsync(loss, 0, sizeof(float), st));
+        return SNP_OK;
+    }
+    double *part = (double *)ctx->loss_part.p;
+    unsigned *counter = (unsigned *)(part + kLossSlots);
+    const snp_status s = launch_mse_loss(image, target, n, dL_dimage, loss, part, counter, kLossSlots, st);
+    if (s != SNP_OK) return fail(ctx, s, "loss launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return SNP_OK;
+}
 
 snp_status snp_get_stats(snp_context *ctx, int64_t token, snp_stats *out, void *stream)
 {

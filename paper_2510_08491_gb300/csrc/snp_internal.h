@@ -68,6 +68,10 @@ struct RasterArgs {
 // snp_raster_*.cu
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
+// snp_loss.cu
+constexpr int kLossSlots = 1024;
+snp_status launch_mse_loss(const float *img, const float *tgt, int64_t n, float *dL, float *loss, double *part,
+                           unsigned *counter, int max_blocks, cudaStream_t st);
 snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
 size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);

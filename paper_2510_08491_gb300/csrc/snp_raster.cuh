@@ -287,7 +287,7 @@ __device__ __forceinline__ PixRay load_ray(const float4 *s_ray, int slot)
     return r;
 }
 
-// ---- colour MLP (Sec. 3.3) over a warp batch: 32 pixel rays of one primitive,
+// ---- colour MLP (Sec. 3.1) over a warp batch: 32 pixel rays of one primitive,
 // lane r holding ray r.  z1 = relu(Wc1_d d + h0), a2 = Wc2 z1 + bc2, z2 = relu(a2),
 // c = sigmoid(Wc3 z2 + bc3).  The rays are the rows of the tensor-core tiles; a
 // batch runs in two passes of 16 rows, lane (g, t) holding rows 16 p + g and

@@ -123,6 +123,22 @@ class Renderer:
                                                    C.byref(sp), C.c_void_p(dL.contiguous().data_ptr()),
                                                    C.byref(gp), C.c_void_p(st)))
 
+    def mse_loss(self, image: torch.Tensor, target: torch.Tensor, dL: Optional[torch.Tensor] = None,
+                 loss: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
+        """Mean squared error of image vs target and its gradient (snp_mse_loss), on the
+        device and without synchronising: returns (loss [1] tensor, dL/dimage)."""
+        if image.shape != target.shape or image.dtype != torch.float32 or target.dtype != torch.float32:
+            raise ValueError("image and target must be float32 tensors of one shape")
+        image, target = image.contiguous(), target.contiguous()
+        dL = torch.empty_like(image) if dL is None else dL
+        loss = torch.empty(1, dtype=torch.float32, device=image.device) if loss is None else loss
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        self.ctx.check(L.lib().snp_mse_loss(self.ctx.handle, C.c_void_p(image.data_ptr()),
+                                            C.c_void_p(target.data_ptr()), image.numel(),
+                                            C.c_void_p(dL.data_ptr()), C.c_void_p(loss.data_ptr()),
+                                            C.c_void_p(st)))
+        return loss, dL
+
     def stats(self, token: Optional[int] = None) -> L.Stats:
         s = L.Stats()
         st = torch.cuda.current_stream(self.device).cuda_stream
@@ -197,11 +213,20 @@ class GraphStep:
     current contents of ps.geom / ps.net and dL and writes image / grads."""
 
     def __init__(self, renderer: Renderer, ps: PackedScene, cams, cfg: L.Config, max_keys: int,
-                 dL: torch.Tensor, backward: bool = True):
+                 dL: Optional[torch.Tensor] = None, backward: bool = True, target: Optional[torch.Tensor] = None):
+        """dL: fixed image gradient for the backward; or target: the step computes the
+        squared-error loss against it (snp_mse_loss) and back-propagates its gradient
+        (self.loss holds the loss after each replay)."""
         self.r, self.ps, self.cams, self.cfg = renderer, ps, cams, cfg
         renderer.reserve(ps, cams, cfg, max_keys)
         P = renderer.image_size(cams)
         self.image = torch.empty((P, 3), dtype=torch.float32, device=renderer.device)
+        self.target = target
+        self.loss = torch.zeros(1, dtype=torch.float32, device=renderer.device) if target is not None else None
+        if target is not None:
+            dL = torch.empty((P, 3), dtype=torch.float32, device=renderer.device)
+        elif backward and dL is None:
+            raise ValueError("GraphStep needs dL or target for the backward")
         self.dL = dL
         self.g_geom = torch.zeros_like(ps.geom) if backward else None
         self.g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device=ps.net.device) if backward else None
@@ -222,6 +247,8 @@ class GraphStep:
             self.g_geom.zero_()
             self.g_net.zero_()
         self.r.forward(self.ps, self.cams, self.cfg, out=self.image)
+        if self.target is not None:
+            self.r.mse_loss(self.image, self.target, self.dL, self.loss)
         if self.backward:
             self.r.backward(self.ps, self.dL, self.g_geom, self.g_net)
 

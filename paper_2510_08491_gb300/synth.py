@@ -115,11 +115,14 @@ class Scene:
 def bf16_round(x: np.ndarray) -> np.ndarray:
     """Round float32 values to the nearest bfloat16 (ties to even); return float32."""
     x = np.ascontiguousarray(x, dtype=np.float32)
-    u = x.view(np.uint32).astype(np.uint64)
-    lsb = (u >> 16) & 1
-    r = ((u + 0x7FFF + lsb) >> 16) << 16
-    out = (r & 0xFFFFFFFF).astype(np.uint32).view(np.float32)
-    return out.reshape(x.shape).copy()
+    out = np.empty_like(x)
+    src, dst = x.reshape(-1).view(np.uint32), out.reshape(-1).view(np.uint32)
+    step = 1 << 24  # bounded temporaries for the 500k-primitive scenes
+    for a in range(0, src.size, step):
+        u = src[a:a + step].astype(np.uint64)
+        r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+        dst[a:a + step] = (r & 0xFFFFFFFF).astype(np.uint32)
+    return out
 
 
 # ----------------------------------------------------------------------------- cameras
@@ -272,6 +275,8 @@ class Workload:
     tile_size: int = 16
     t_min: float = 1e-4
     note: str = ""
+    # differentiation workload: the loss is the squared error against a render of this scene
+    target_scene: Optional[Scene] = None
 
     @property
     def n_pixels(self) -> int:
@@ -293,7 +298,7 @@ def workload(name: str, seed: int = 0) -> Workload:
         return Workload(name, wl.scene, wl.cameras[:1], 16)
     if name == "diff300k_720p":
         sc = make_scene(300_000, seed, center_half=3.0, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
-        return Workload(name, sc, ring_cameras(1, 8.0, 1280, 720), 16)
+        return Workload(name, sc, ring_cameras(1, 8.0, 1280, 720), 16, target_scene=perturb(sc, seed + 11, 0.01))
     if name == "thin50k_1080p":
         sc = make_scene(50_000, seed, center_half=3.0, n_sigma=16, omega0=30.0, color="mlp",
                         n_c=32, thin_ratio_max=50.0)
