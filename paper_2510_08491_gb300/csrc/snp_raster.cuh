@@ -382,9 +382,12 @@ __device__ __forceinline__ void color_gemm_gw(const uint32_t (&gh)[NC / 16][4], 
 __device__ __forceinline__ int acc_unit(int m, int t) { return 8 * (m >> 1) + 2 * t + (m & 1); }
 
 // Colour of the batch's rays.  Lane r holds ray r: direction d, output slot pix,
-// valid.  Colour channel c of a valid ray goes to out[c * plane + pix].
+// valid; the valid rays are lanes 0 .. nrows-1 (nrows is warp-uniform, so a batch
+// of at most 16 rays runs one pass).  Colour channel c of a valid ray goes to
+// out[c * plane + pix].
 template <int NC, bool BF16>
-__device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, bool valid, float *out, int plane)
+__device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, bool valid, int nrows, float *out,
+                                           int plane)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
@@ -393,9 +396,10 @@ __device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, b
     const float4 B3 = *reinterpret_cast<const float4 *>(Cb + cb_B3(NC));
     const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
     const int vp = valid ? pix : -1;
+    const int passes = nrows > 16 ? 2 : 1;
     __syncwarp();
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
+#pragma unroll 1
+    for (int p = 0; p < passes; ++p) {
         const int r0 = 16 * p + g, r1 = r0 + 8;
         const float3 d0 = shfl_f3(d, r0), d1 = shfl_f3(d, r1);
         float z[NC / 8][4];
@@ -442,33 +446,26 @@ __device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, b
 }
 
 // Backward of the colour MLP for the batch: lane r holds ray r's direction d and
-// dL/da3 (the pre-sigmoid colour gradient; zero for lanes without a pair).
+// dL/da3 (the pre-sigmoid colour gradient; zero for lanes without a pair); rows
+// at or beyond nrows (warp-uniform) carry no pair, so nrows <= 16 runs one pass.
 // Accumulates dL/d(Wc1_d, h0) into AC1 [NC][4], dL/dWc2 into AW2 [NC][NC] and
 // dL/d(Wc3, bc2) into AW3 [NC][4] (shared memory, atomics).  The three
 // contractions a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays
 // dL/da2 z1^T run on the tensor cores; the last uses movmatrix transposes of the
 // pass's register fragments with the rays as the reduction dimension.
 template <int NC, bool BF16>
-__device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3 g_a3, float *AC1, float *AW2,
-                                               float *AW3)
+__device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3 g_a3, int nrows, float *AC1,
+                                               float *AW2, float *AW3)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
     const float *B2 = Cb + cb_B2(NC);
     const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
     const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
-    // dL/dWc2 stays in registers across both passes when it fits (NC = 32)
     __syncwarp();
-    constexpr bool kHold = NC <= 32;
-    constexpr int HM = kHold ? NC / 16 : 1, HN = kHold ? NC / 8 : 1;
-    float dw[HM][HN][4];
-#pragma unroll
-    for (int i = 0; i < HM; ++i)
-#pragma unroll
-        for (int j = 0; j < HN; ++j) dw[i][j][0] = dw[i][j][1] = dw[i][j][2] = dw[i][j][3] = 0.0f;
-
+    const int passes = nrows > 16 ? 2 : 1;
 #pragma unroll 1
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < passes; ++p) {
         const int r0 = 16 * p + g, r1 = r0 + 8;
         const float3 d0 = shfl_f3(d, r0), d1 = shfl_f3(d, r1);
         const float3 e0 = shfl_f3(g_a3, r0), e1 = shfl_f3(g_a3, r1);
@@ -560,34 +557,15 @@ __device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3
                                     movm_trans(gl[mn][3])};
 #pragma unroll
             for (int nk = 0; nk < NC / 8; ++nk) {
-                if constexpr (kHold) {
-                    mma16816(dw[mn][nk], tl, tzh[nk][0], tzh[nk][1]);
-                    mma16816(dw[mn][nk], th, tzl[nk][0], tzl[nk][1]);
-                    mma16816(dw[mn][nk], th, tzh[nk][0], tzh[nk][1]);
-                } else {
-                    float d4[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
-                    mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
-                    mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
-                    const int n0 = 16 * mn + g, k0 = 8 * nk + 2 * t;
-                    if (d4[0] != 0.0f) atomicAdd(AW2 + n0 * NC + k0, d4[0]);
-                    if (d4[1] != 0.0f) atomicAdd(AW2 + n0 * NC + k0 + 1, d4[1]);
-                    if (d4[2] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0, d4[2]);
-                    if (d4[3] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0 + 1, d4[3]);
-                }
-            }
-        }
-    }
-    if constexpr (kHold) {
-#pragma unroll
-        for (int mn = 0; mn < HM; ++mn) {
-#pragma unroll
-            for (int nk = 0; nk < HN; ++nk) {
+                float d4[4] = {0.f, 0.f, 0.f, 0.f};
+                mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
+                mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
+                mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
                 const int n0 = 16 * mn + g, k0 = 8 * nk + 2 * t;
-                if (dw[mn][nk][0] != 0.0f) atomicAdd(AW2 + n0 * NC + k0, dw[mn][nk][0]);
-                if (dw[mn][nk][1] != 0.0f) atomicAdd(AW2 + n0 * NC + k0 + 1, dw[mn][nk][1]);
-                if (dw[mn][nk][2] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0, dw[mn][nk][2]);
-                if (dw[mn][nk][3] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0 + 1, dw[mn][nk][3]);
+                if (d4[0] != 0.0f) atomicAdd(AW2 + n0 * NC + k0, d4[0]);
+                if (d4[1] != 0.0f) atomicAdd(AW2 + n0 * NC + k0 + 1, d4[1]);
+                if (d4[2] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0, d4[2]);
+                if (d4[3] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0 + 1, d4[3]);
             }
         }
     }
@@ -648,6 +626,11 @@ struct TileCfg {
     static constexpr int PPT = NPIX / NT;
     static constexpr int MIN_BLOCKS = TS == 8 ? 4 : 2;
 };
+
+// CTAs per SM the backward kernel is built for: two (128 registers, a staging
+// chunk that fits two CTAs' shared memory) where the colour network is at most
+// 32 wide and a thread holds one pixel, else one.
+__host__ __device__ constexpr int bwd_min_blocks(int ts, int nc) { return (ts == 16 && nc <= 32) ? 2 : 1; }
 
 template <int TS>
 __device__ __forceinline__ void tile_pixel(int tid, int k, int &lx, int &ly)

@@ -79,11 +79,12 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
 
 // Gradient of one (pixel, primitive) pair, reduced across the warp into the
 // entry's shared-memory accumulator A.  All 32 lanes call it together; lanes
-// without a pair pass contrib = false (their contributions are zero).
+// without a pair pass contrib = false (their contributions are zero) and the
+// pairs occupy lanes 0 .. nrows-1.
 template <int NC, int FORM, bool BF16>
 __device__ __forceinline__ void pair_backward(const float *R, const float *D, const float *Cb, int ns, float w0,
-                                              const CamK &ck, const PixRay &ry, bool contrib, float g_ah, float3 g_c,
-                                              float3 col, float *A)
+                                              const CamK &ck, const PixRay &ry, bool contrib, int nrows, float g_ah,
+                                              float3 g_c, float3 col, float *A)
 {
     const unsigned lane = lane_id();
     const float3 d = unit_dir(ry);
@@ -276,7 +277,7 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
     // ---- colour MLP backward (whole warp)
     if constexpr (NC > 0) {
         float *AC1 = A + ga_col(ns);
-        warp_color_bwd<NC, BF16>(Cb, d, g_a3, AC1, AC1 + 4 * NC, AC1 + 4 * NC + NC * NC);
+        warp_color_bwd<NC, BF16>(Cb, d, g_a3, nrows, AC1, AC1 + 4 * NC, AC1 + 4 * NC + NC * NC);
     }
 }
 
@@ -289,7 +290,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk)
 }
 
 template <int TS, int NC, int FORM, bool BF16>
-__global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
+__global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_raster_bwd(RasterArgs a)
 {
     constexpr int NT = TileCfg<TS>::NT;
     constexpr int NPIX = TileCfg<TS>::NPIX;
@@ -453,11 +454,11 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                 int e = 0;
                 for (int b = wid; b < nb; b += NT / 32) {
                     while (b >= s_pb[e + 1]) ++e;
-                    const int kk = (b - s_pb[e]) * 32 + (int)lane;
+                    const int k0 = (b - s_pb[e]) * 32, kk = k0 + (int)lane;
                     const bool valid = kk < s_na[e];
                     const int pix = valid ? s_al[e * NPIX + kk] : 0;
                     warp_color<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)),
-                                         pix, valid, s_col + e * NPIX, CH * NPIX);
+                                         pix, valid, s_na[e] - k0, s_col + e * NPIX, CH * NPIX);
                 }
             }
             __syncthreads();
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                 int e = 0;
                 for (int b = wid; b < nb; b += NT / 32) {
                     while (b >= s_pb[e + 1]) ++e;
-                    const int kk = (b - s_pb[e]) * 32 + (int)lane;
+                    const int k0 = (b - s_pb[e]) * 32, kk = k0 + (int)lane;
                     const bool valid = kk < s_na[e];
                     const int pix = valid ? s_al[e * NPIX + kk] : 0;
                     const PixRay r = load_ray(s_ray, pix);
@@ -501,7 +502,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, 1) k_raster_bwd(RasterArgs a)
                     const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + pix], s_col[(1 * CH + e) * NPIX + pix],
                                                    s_col[(2 * CH + e) * NPIX + pix]);
                     pair_backward<NC, FORM, BF16>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0, ck, r,
-                                            valid, s_ah[e * NPIX + pix], g_c, col, acc + e * vg);
+                                                  valid, s_na[e] - k0, s_ah[e * NPIX + pix], g_c, col,
+                                                  acc + e * vg);
                 }
             }
             __syncthreads();

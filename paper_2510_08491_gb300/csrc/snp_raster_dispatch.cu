@@ -24,13 +24,15 @@ size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
 }
 
 // Largest chunk (<= 32 forward, <= 8 backward) within the shared-memory budget:
-// about half an SM for the forward (two CTAs per SM), most of one for the backward.
+// about half an SM for the forward (two CTAs per SM); for the backward half an SM
+// where it is built for two CTAs per SM, else most of one.
 int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts)
 {
     const size_t fwd_budget = ts == 8 ? 52 * 1024 : 104 * 1024;
+    const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2 ? 110 * 1024 : 200 * 1024;
     int ch = backward ? 8 : 32;
     if (backward) {
-        while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts) > 200 * 1024) --ch;
+        while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts) > bwd_budget) --ch;
     } else {
         while (ch > 1 && raster_fwd_smem(color_mode, n_c, n_sigma, ch, ts) > fwd_budget) --ch;
     }

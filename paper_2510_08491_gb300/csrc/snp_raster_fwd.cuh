@@ -181,11 +181,11 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
                 int e = 0;
                 for (int b = tid >> 5; b < nb; b += NT / 32) {
                     while (b >= s_pb[e + 1]) ++e;
-                    const int kk = (b - s_pb[e]) * 32 + (int)lane_id();
+                    const int k0 = (b - s_pb[e]) * 32, kk = k0 + (int)lane_id();
                     const bool valid = kk < s_na[e];
                     const int pix = valid ? s_al[e * NPIX + kk] : 0;
                     warp_color<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)),
-                                         pix, valid, s_col + e * NPIX, CH * NPIX);
+                                         pix, valid, s_na[e] - k0, s_col + e * NPIX, CH * NPIX);
                 }
                 __syncthreads();
                 // P5: accumulate in list order
