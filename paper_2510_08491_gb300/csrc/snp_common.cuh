@@ -3,7 +3,7 @@
 // Layouts (all device memory):
 //   geom   float [n][16]   centre(3) log-scale(3) quaternion wxyz(4) rgb(3) unused(3)
 //   net    [n][stride]     weight dtype, field offsets from snp_get_net_layout
-//   rec    float [V*n][20] per (view, primitive) projection record (kRec* below)
+//   rec    float [V*n][48] per (view, primitive) projection record (kRec* below)
 //   trect  int4  [V*n]     inclusive tile rectangle tx0, ty0, tx1, ty1
 //   keys   u64   [K]       (global tile << 32) | float bits of the camera-frame depth
 //   vals   u32   [K]       view * n + primitive

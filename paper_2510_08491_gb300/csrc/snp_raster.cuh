@@ -3,7 +3,7 @@
 // ray/ellipsoid test, the closed-form integral (Sec. 3.2, Eq. 8) and the colour MLP.
 //
 // Shared-memory entry (floats) for one primitive of the chunk:
-//   [0, 20)             projection record (kRec* offsets)
+//   [0, kRecFloats)     projection record (kRec* offsets)
 //   density block       per hidden unit k a float4 (w0 W1_k, w0 b1_k), then w2[N_sigma], b2, pad
 //   colour block (MLP)  C1[n_c] float4 (Wc1[j][0..2], h0_j = bc1_j + Wc1[j][3..10] . feat),
 //                       W2 as bf16 hi[n_c][n_c + 8] then lo[n_c][n_c + 8] (Wc2 = hi + lo;
@@ -448,7 +448,10 @@ __device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, b
 // Backward of the colour MLP for the batch: lane r holds ray r's direction d and
 // dL/da3 (the pre-sigmoid colour gradient; zero for lanes without a pair); rows
 // at or beyond nrows (warp-uniform) carry no pair, so nrows <= 16 runs one pass.
-// Accumulates dL/d(Wc1_d, h0) into AC1 [NC][4], dL/dWc2 into AW2 [NC][NC] and
+// Accumulates dL/d(Wc1_d, h0) into AC1 [NC][4], dL/dWc2 into AW2 [NC * NC] (in
+// mma fragment order: element i of lane l of output tile (mn, nk), i.e. of row
+// 16 mn + l/4 + 8 (i >> 1), column 8 nk + 2 (l % 4) + (i & 1), at
+// ((mn NC/8 + nk) 4 + i) 32 + l) and
 // dL/d(Wc3, bc2) into AW3 [NC][4] (shared memory, atomics).  The three
 // contractions a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays
 // dL/da2 z1^T run on the tensor cores; the last uses movmatrix transposes of the
@@ -561,11 +564,12 @@ __device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3
                 mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
                 mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
                 mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
-                const int n0 = 16 * mn + g, k0 = 8 * nk + 2 * t;
-                if (d4[0] != 0.0f) atomicAdd(AW2 + n0 * NC + k0, d4[0]);
-                if (d4[1] != 0.0f) atomicAdd(AW2 + n0 * NC + k0 + 1, d4[1]);
-                if (d4[2] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0, d4[2]);
-                if (d4[3] != 0.0f) atomicAdd(AW2 + (n0 + 8) * NC + k0 + 1, d4[3]);
+                // fragment order: element i of lane l of tile (mn, nk) at ((mn NC/8 + nk) 4 + i) 32 + l,
+                // so each atomic of the warp hits 32 consecutive words (no bank conflicts)
+                float *dst = AW2 + (mn * (NC / 8) + nk) * 128 + lane;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (d4[i] != 0.0f) atomicAdd(dst + 32 * i, d4[i]);
             }
         }
     }

@@ -24,7 +24,8 @@ namespace snp {
 __host__ __device__ constexpr int ga_geo(int ns) { return round4(5 * ns + 1); }
 __host__ __device__ constexpr int ga_bc3(int ns) { return ga_geo(ns) + kGvFloats; }
 __host__ __device__ constexpr int ga_col(int ns) { return ga_bc3(ns) + 4; }
-// colour: C1G [nc][4] (Wc1[j][0..2], h0_j), W2G [nc][nc], W3G [nc][4] (Wc3[0..2][j], bc2_j)
+// colour: C1G [nc][4] (Wc1[j][0..2], h0_j), W2G [nc * nc] in mma fragment order (see
+// warp_color_bwd), W3G [nc][4] (Wc3[0..2][j], bc2_j)
 __host__ __device__ constexpr int grad_stride(int ns, int nc)
 {
     return nc == 0 ? ga_col(ns) : ga_col(ns) + 4 * nc + nc * nc + 4 * nc;
@@ -64,7 +65,11 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
                     atomicAdd(a.g_h0 + prim * NC + j, val);
                 }
             } else if ((t -= 4 * NC) < NC * NC) {
-                if (a.g_net) atomicAdd(a.g_net + nb + a.off_Wc2 + t, val);
+                // fragment order (see warp_color_bwd): ((mn * NC/8 + nk) * 4 + i) * 32 + lane
+                const int ln = t & 31, i = (t >> 5) & 3, tile = t >> 7;
+                const int n = 16 * (tile / (NC / 8)) + (ln >> 2) + 8 * (i >> 1);
+                const int k = 8 * (tile % (NC / 8)) + 2 * (ln & 3) + (i & 1);
+                if (a.g_net) atomicAdd(a.g_net + nb + a.off_Wc2 + n * NC + k, val);
             } else {
                 t -= NC * NC;
                 const int j = t >> 2, r = t & 3;
@@ -285,8 +290,8 @@ template <int TS>
 __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
-    const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 + (size_t)NPIX * (9 * 4 + 2 * 2);
-    return NPIX * 32 + (size_t)chunk * per_entry;
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2 * 2);
+    return NPIX * (32 + 12) + (size_t)chunk * per_entry;
 }
 
 template <int TS, int NC, int FORM, bool BF16>
@@ -301,14 +306,13 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const int es = entry_stride(ns, NC);
     const int vg = grad_stride(ns, NC);
     float4 *s_ray = smem4;                                 // [2 NPIX] pixel rays
-    float *sm = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [CH][es] staged entries
+    float *s_dl = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [3][NPIX] dL/dC of the tile's pixels
+    float *sm = s_dl + 3 * NPIX;                           // [CH][es] staged entries
     float *acc = sm + CH * es;                             // [CH][vg] per-entry gradient sums
     float *s_ah = acc + CH * vg;                           // [CH][NPIX] alpha_hat, then dL/dalpha_hat
     float *s_w = s_ah + CH * NPIX;                         // [CH][NPIX] weights (-1: not composited)
-    float *s_tn = s_w + CH * NPIX;                         // [CH][NPIX] transmittance after the entry
-    float *s_col = s_tn + CH * NPIX;                       // [3][CH][NPIX] colours
-    float *s_gc = s_col + 3 * CH * NPIX;                   // [3][CH][NPIX] dL/dcolour
-    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_gc + 3 * CH * NPIX);  // [CH][NPIX]
+    float *s_col = s_w + CH * NPIX;                        // [3][CH][NPIX] colours
+    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + 3 * CH * NPIX);  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
     __shared__ uint32_t s_gid[kMaxChunk];
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65];
@@ -365,6 +369,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             }
             bgdot[k] = __expf(-tau_f) * (dL[k].x * a.bg[0] + dL[k].y * a.bg[1] + dL[k].z * a.bg[2]);
             tau[k] = 0.0f;
+            s_dl[k * NT + tid] = dL[k].x;
+            s_dl[NPIX + k * NT + tid] = dL[k].y;
+            s_dl[2 * NPIX + k * NT + tid] = dL[k].z;
         }
         const uint2 rg = a.ranges[tile];
         const int64_t vn = (int64_t)v * a.n;
@@ -413,6 +420,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             }
             __syncthreads();
             // P3: replay of the compositing weights
+            float tau_c[PPT];  // optical depth at the chunk start, for P5
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) tau_c[k] = tau[k];
             for (int e = 0; e < cnt; ++e) {
                 const uint32_t pos = c0 - rg.x + e;
 #pragma unroll
@@ -424,7 +434,6 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         const float Ti = __expf(-tau[k]);
                         s_w[e * NPIX + slot] = Ti * (1.0f - __expf(-ah));
                         tau[k] += ah;
-                        s_tn[e * NPIX + slot] = __expf(-tau[k]);
                     } else {
                         s_w[e * NPIX + slot] = -1.0f;
                     }
@@ -462,7 +471,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            // P5: dL/dalpha_hat = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg and dL/dc_i = w_i dL
+            // P5: dL/dalpha_hat = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg
             for (int e = 0; e < cnt; ++e) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
@@ -472,16 +481,14 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + slot],
                                                        s_col[(1 * CH + e) * NPIX + slot],
                                                        s_col[(2 * CH + e) * NPIX + slot]);
-                        const float Tn = s_tn[e * NPIX + slot];
+                        tau_c[k] += s_ah[e * NPIX + slot];
+                        const float Tn = __expf(-tau_c[k]);
                         pref[k].x = fmaf(w, col.x, pref[k].x);
                         pref[k].y = fmaf(w, col.y, pref[k].y);
                         pref[k].z = fmaf(w, col.z, pref[k].z);
                         s_ah[e * NPIX + slot] = dL[k].x * (Tn * col.x - (Cf[k].x - pref[k].x)) +
                                                 dL[k].y * (Tn * col.y - (Cf[k].y - pref[k].y)) +
                                                 dL[k].z * (Tn * col.z - (Cf[k].z - pref[k].z)) - bgdot[k];
-                        s_gc[(0 * CH + e) * NPIX + slot] = dL[k].x * w;
-                        s_gc[(1 * CH + e) * NPIX + slot] = dL[k].y * w;
-                        s_gc[(2 * CH + e) * NPIX + slot] = dL[k].z * w;
                     }
                 }
             }
@@ -497,8 +504,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     const int pix = valid ? s_al[e * NPIX + kk] : 0;
                     const PixRay r = load_ray(s_ray, pix);
                     const float *R = sm + e * es;
-                    const float3 g_c = make_float3(s_gc[(0 * CH + e) * NPIX + pix], s_gc[(1 * CH + e) * NPIX + pix],
-                                                   s_gc[(2 * CH + e) * NPIX + pix]);
+                    // dL/dc_i = w_i dL
+                    const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
+                    const float3 g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
                     const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + pix], s_col[(1 * CH + e) * NPIX + pix],
                                                    s_col[(2 * CH + e) * NPIX + pix]);
                     pair_backward<NC, FORM, BF16>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0, ck, r,
