@@ -184,6 +184,21 @@ def pair_diagnostics(scene, cam, pix, pix_list, list_off, list_prim):
     return pair_prim, h2.numpy(), ah.numpy(), amin.numpy()
 
 
+def min_direction_dot(scene, cam, pix, pix_list, list_off, list_prim):
+    """Per candidate pair (same order as pair_diagnostics): min_k |W1_k . d| over the
+    density network's hidden units, d the unit pixel ray.  This is the directional
+    frequency that Eq. 8 divides by (a_k = w0 W1_k . d / m); the precision-stress
+    workload is built so that a share of the hit pairs has it below 1e-4."""
+    lens = (list_off[pix_list + 1] - list_off[pix_list]).astype(np.int64)
+    starts = list_off[pix_list]
+    pair_pix = np.repeat(np.arange(len(pix)), lens)
+    pair_pos = np.arange(lens.sum()) - np.repeat(np.cumsum(lens) - lens, lens)
+    pair_prim = list_prim[np.repeat(starts, lens) + pair_pos].astype(np.int64)
+    d = pixel_rays(cam, pix).numpy()[pair_pix]
+    W1 = np.asarray(scene.W1, np.float64)[pair_prim]
+    return np.abs(np.einsum("qkj,qj->qk", W1, d)).min(axis=1)
+
+
 def grads(scene, cam, pix, pix_list, list_off, list_prim, dL_dC: np.ndarray, t_min: float = 1e-4,
           bg=(0.0, 0.0, 0.0)):
     """Vector-Jacobian product: d(sum dL_dC * C)/d(every parameter array), float64 numpy."""

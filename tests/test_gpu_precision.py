@@ -1,0 +1,122 @@
+"""Precision stress on the thin-primitive workload (50k primitives with axis
+ratios up to 1:50, omega0 = 30, a share of W1 rows nearly orthogonal to the rays
+through their primitive; 1920 x 1080): FP32 vs BF16 weights x stable vs literal
+(Eq. 8) integral, image and gradient error against the FP64 oracle on 48
+seeded tiles.
+
+BF16 runs are compared with the oracle on the BF16-rounded weights (compute
+error) and on the original FP32 weights (total error).  The stable form must
+meet the parity bars (images 1e-4, flagged termination near-ties 2e-4;
+gradients 1e-3 in norm per group); the literal form is reported, and must be
+worse than the stable one on the image, since its division by
+a_k = w0 W1_k . d / m is what the stress targets.  Run with -s for the table.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2510_08491_gb300 import synth
+from gpu_util import grad_rel_errors
+
+pytestmark = pytest.mark.gpu
+
+TILES = 48
+RELU_EPS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2510_08491_gb300 import build
+    build.build()
+    from oracle import grad as G
+    from oracle import oracle as O
+    from paper_2510_08491_gb300.render import Renderer
+    O.build()
+    wl = synth.workload("thin50k_1080p")
+    sc, cam = wl.scene, wl.cameras[0]
+    rng = np.random.default_rng(5)
+    tx_n, ty_n = O.tiles_xy(cam, 16)
+    pix = []
+    for t in rng.choice(tx_n * ty_n, size=TILES, replace=False):
+        ty, tx = divmod(int(t), tx_n)
+        ys, xs = np.mgrid[ty * 16:min(ty * 16 + 16, cam.height), tx * 16:min(tx * 16 + 16, cam.width)]
+        pix.append((ys * cam.width + xs).ravel())
+    pix = np.sort(np.concatenate(pix)).astype(np.int32)
+    return dict(O=O, G=G, R=Renderer(0), sc=sc, sc_bf=sc.to_bf16(), cam=cam, pix=pix, rng=rng)
+
+
+def _oracle(S, scene):
+    O, G, cam, pix = S["O"], S["G"], S["cam"], S["pix"]
+    tl = O.tile_keys(scene, [cam], 16)
+    out = O.render_view_tiled(scene, [cam], 0, tl, 16, pix)
+    lp = (tl.vals.astype(np.int64) % scene.n).astype(np.int32)
+    gt = tl.view_tile_off[0] + O.pixel_tile(cam, 16, pix)
+    return out, tl, lp, gt
+
+
+def _mask(S, scene, out, tl, lp, gt):
+    """Sampled pixels whose dL is kept: no termination near-tie, no ReLU kink."""
+    G = S["G"]
+    keep = out.flags == 0
+    _, h2, ah, amin = G.pair_diagnostics(scene, S["cam"], S["pix"], gt, tl.tile_off, lp)
+    lens = tl.tile_off[gt + 1] - tl.tile_off[gt]
+    owner = np.repeat(np.arange(len(S["pix"])), lens)
+    bad = np.zeros(len(S["pix"]), bool)
+    bad[owner[(ah > 0) & (amin < RELU_EPS)]] = True
+    return keep & ~bad
+
+
+def _gpu(S, scene, form, dL_pix):
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene, unpack_geom_grad, unpack_net_grad
+    R, cam, pix = S["R"], S["cam"], S["pix"]
+    ps = pack_scene(scene)
+    img = R.forward(ps, [cam], L.make_config(form=form))
+    dL = torch.zeros((cam.n_pixels, 3), dtype=torch.float32, device="cuda")
+    dL[torch.from_numpy(pix.astype(np.int64)).cuda()] = torch.from_numpy(dL_pix.astype(np.float32)).cuda()
+    gg = torch.zeros_like(ps.geom)
+    gn = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
+    R.backward(ps, dL, gg, gn)
+    torch.cuda.synchronize()
+    g = unpack_geom_grad(gg)
+    g.update(unpack_net_grad(ps, gn, scene))
+    return img.cpu().numpy()[pix].astype(np.float64), g
+
+
+def test_precision_report(setup):
+    S = setup
+    from paper_2510_08491_gb300 import _lib as L
+    fields = ["centers", "log_scales", "quats", "W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3",
+              "bc3"]
+    ref32 = _oracle(S, S["sc"])
+    refbf = _oracle(S, S["sc_bf"])
+    dL_pix = S["rng"].normal(size=(len(S["pix"]), 3))
+    dL_pix[~(_mask(S, S["sc"], *ref32) & _mask(S, S["sc_bf"], *refbf))] = 0.0
+    grads_ref = {}
+    for name, sc, (out, tl, lp, gt) in (("f32", S["sc"], ref32), ("bf16", S["sc_bf"], refbf)):
+        _, grads_ref[name] = S["G"].grads(sc, S["cam"], S["pix"], gt, tl.tile_off, lp, dL_pix)
+    rows = {}
+    for wname, sc in (("f32", S["sc"]), ("bf16", S["sc_bf"])):
+        out, _, _, _ = ref32 if wname == "f32" else refbf
+        plain = out.flags == 0
+        for fname, form in (("stable", L.FORM_STABLE), ("literal", L.FORM_NAIVE)):
+            img, g = _gpu(S, sc, form, dL_pix)
+            err = np.abs(img - out.rgb).max(axis=1)
+            ge = grad_rel_errors(g, {k: grads_ref[wname][k] for k in fields})
+            row = dict(img_max=float(err[plain].max()), img_mean=float(err.mean()),
+                       img_flag_max=float(err[~plain].max()) if (~plain).any() else 0.0,
+                       grad_norm_max=max(v[1] for v in ge.values()),
+                       grad_elem_max=max(v[0] for v in ge.values()),
+                       worst_group=max(ge, key=lambda k: ge[k][1]))
+            if wname == "bf16":
+                tot = np.abs(img - ref32[0].rgb).max(axis=1)
+                row["img_total_max"], row["img_total_mean"] = float(tot.max()), float(tot.mean())
+            rows[(wname, fname)] = row
+    print("\nprecision stress: thin50k_1080p,", len(S["pix"]), "sampled pixels")
+    for k, r in rows.items():
+        print(k, {a: (f"{b:.2e}" if isinstance(b, float) else b) for a, b in r.items()})
+    for w in ("f32", "bf16"):
+        st = rows[(w, "stable")]
+        assert st["img_max"] <= 1e-4 and st["img_flag_max"] <= 2e-4, (w, st)
+        assert st["grad_norm_max"] <= 1e-3, (w, st)
+        assert rows[(w, "literal")]["img_max"] > st["img_max"], (w, rows[(w, "literal")], st)
