@@ -31,52 +31,116 @@ __host__ __device__ constexpr int grad_stride(int ns, int nc)
     return nc == 0 ? ga_col(ns) : ga_col(ns) + 4 * nc + nc * nc + 4 * nc;
 }
 
+// Vector atomic add of the four values at acc[s[0..3]] (zeroed afterwards) to the
+// 16-byte aligned dst[0..3]; a source index < 0 contributes 0 (destination padding).
+__device__ __forceinline__ void flush4(float *acc, const int (&s)[4], float *dst)
+{
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[i] = s[i] >= 0 ? acc[s[i]] : 0.0f;
+        if (s[i] >= 0) acc[s[i]] = 0.0f;
+    }
+    if (v[0] != 0.0f || v[1] != 0.0f || v[2] != 0.0f || v[3] != 0.0f)
+        atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
+}
+
+__device__ __forceinline__ void flush1(float *acc, int s, float *dst)
+{
+    const float v = acc[s];
+    acc[s] = 0.0f;
+    if (v != 0.0f) atomicAdd(dst, v);
+}
+
+// Add one entry's gradient sums to the caller's arrays and clear them.  Groups
+// of four consecutive destination elements go out as one 16-byte vector atomic
+// (every network field is 8-element aligned and padded, so a group that runs
+// past a field's end only adds zeros to its padding).
 template <int NC>
-__device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int64_t prim, int64_t vprim, int vg,
-                                            int tid, int nt)
+__device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int64_t prim, int64_t vprim, int tid,
+                                            int nt)
 {
     const int ns = a.n_sigma;
-    const int64_t nb = prim * a.stride;
-    for (int q = tid; q < vg; q += nt) {
-        const float val = acc[q];
-        if (val == 0.0f) continue;
-        acc[q] = 0.0f;
-        if (q < ga_geo(ns)) {
-            if (!a.g_net) continue;
-            int64_t dst;
-            if (q < 3 * ns) dst = nb + a.off_W1 + q;
-            else if (q < 4 * ns) dst = nb + a.off_b1 + (q - 3 * ns);
-            else if (q < 5 * ns) dst = nb + a.off_w2 + (q - 4 * ns);
-            else if (q == 5 * ns) dst = nb + a.off_b2;
-            else continue;
-            atomicAdd(a.g_net + dst, val);
-        } else if (q < ga_bc3(ns)) {
-            atomicAdd(a.g_view + vprim * kGvFloats + (q - ga_geo(ns)), val);
-        } else if (q < ga_col(ns)) {
-            const int r = q - ga_bc3(ns);
-            if (a.g_net && r < 3) atomicAdd(a.g_net + nb + a.off_bc3 + r, val);
-        } else if constexpr (NC > 0) {
-            int t = q - ga_col(ns);
-            if (t < 4 * NC) {
-                const int j = t >> 2, r = t & 3;
-                if (r < 3) {
-                    if (a.g_net) atomicAdd(a.g_net + nb + a.off_Wc1 + j * (3 + kFeat) + r, val);
-                } else {
-                    atomicAdd(a.g_h0 + prim * NC + j, val);
-                }
-            } else if ((t -= 4 * NC) < NC * NC) {
-                // fragment order (see warp_color_bwd): ((mn * NC/8 + nk) * 4 + i) * 32 + lane
-                const int ln = t & 31, i = (t >> 5) & 3, tile = t >> 7;
-                const int n = 16 * (tile / (NC / 8)) + (ln >> 2) + 8 * (i >> 1);
-                const int k = 8 * (tile % (NC / 8)) + 2 * (ln & 3) + (i & 1);
-                if (a.g_net) atomicAdd(a.g_net + nb + a.off_Wc2 + n * NC + k, val);
+    float *gn = a.g_net ? a.g_net + prim * a.stride : nullptr;
+    const int gW1 = (3 * ns + 3) / 4, gB1 = (ns + 3) / 4;
+    const int e0 = gW1, e1 = e0 + gB1, e2 = e1 + gB1;  // W1 | b1 | w2 groups end
+    const int e3 = e2 + 1;                              // b2
+    const int e4 = e3 + kGvFloats / 4;                  // per-(view, primitive) record
+    const int e5 = e4 + 3;                              // bc3
+    int total = e5;
+    constexpr int NG8 = NC / 8;
+    const int e6 = e5 + 3 * NC, e7 = e6 + NC / 4, e8 = e7 + NC * NC / 4, e9 = e8 + 3 * NC / 4, e10 = e9 + NC / 4;
+    if constexpr (NC > 0) total = e10;
+    for (int g = tid; g < total; g += nt) {
+        if (g < e2) {
+            if (!gn) {
+                const int base = g < e0 ? 4 * g : (g < e1 ? 3 * ns + 4 * (g - e0) : 4 * ns + 4 * (g - e1));
+                const int lim = g < e0 ? 3 * ns : (g < e1 ? 4 * ns : 5 * ns);
+                for (int i = 0; i < 4; ++i)
+                    if (base + i < lim) acc[base + i] = 0.0f;
+                continue;
+            }
+            int sidx[4];
+            float *dst;
+            if (g < e0) {
+                const int q = 4 * g;
+                for (int i = 0; i < 4; ++i) sidx[i] = q + i < 3 * ns ? q + i : -1;
+                dst = gn + a.off_W1 + q;
+            } else if (g < e1) {
+                const int q = 4 * (g - e0);
+                for (int i = 0; i < 4; ++i) sidx[i] = q + i < ns ? 3 * ns + q + i : -1;
+                dst = gn + a.off_b1 + q;
             } else {
-                t -= NC * NC;
-                const int j = t >> 2, r = t & 3;
-                if (a.g_net) {
-                    if (r < 3) atomicAdd(a.g_net + nb + a.off_Wc3 + r * NC + j, val);
-                    else atomicAdd(a.g_net + nb + a.off_bc2 + j, val);
-                }
+                const int q = 4 * (g - e1);
+                for (int i = 0; i < 4; ++i) sidx[i] = q + i < ns ? 4 * ns + q + i : -1;
+                dst = gn + a.off_w2 + q;
+            }
+            flush4(acc, sidx, dst);
+        } else if (g < e3) {
+            if (gn) flush1(acc, 5 * ns, gn + a.off_b2);
+            else acc[5 * ns] = 0.0f;
+        } else if (g < e4) {
+            const int q = 4 * (g - e3);
+            const int sidx[4] = {ga_geo(ns) + q, ga_geo(ns) + q + 1, ga_geo(ns) + q + 2, ga_geo(ns) + q + 3};
+            flush4(acc, sidx, a.g_view + vprim * kGvFloats + q);
+        } else if (g < e5) {
+            const int r = g - e4;
+            if (gn) flush1(acc, ga_bc3(ns) + r, gn + a.off_bc3 + r);
+            else acc[ga_bc3(ns) + r] = 0.0f;
+        } else if constexpr (NC > 0) {
+            const int C1 = ga_col(ns), W2 = C1 + 4 * NC, W3 = W2 + NC * NC;
+            if (g < e6) {
+                // Wc1 direction columns: 3 scalars per unit (rows of Wc1 are 11 wide)
+                const int j = (g - e5) / 3, r = (g - e5) - 3 * j;
+                if (gn) flush1(acc, C1 + 4 * j + r, gn + a.off_Wc1 + j * (3 + kFeat) + r);
+                else acc[C1 + 4 * j + r] = 0.0f;
+            } else if (g < e7) {
+                const int j = 4 * (g - e6);
+                const int sidx[4] = {C1 + 4 * j + 3, C1 + 4 * j + 7, C1 + 4 * j + 11, C1 + 4 * j + 15};
+                flush4(acc, sidx, a.g_h0 + prim * NC + j);
+            } else if (g < e8) {
+                // Wc2 row n, columns k0..k0+3, from the mma fragment-order accumulator
+                const int q = g - e7, n = q / (NC / 4), k0 = 4 * (q - n * (NC / 4));
+                const int mn = n >> 4, gg = n & 7, hi = (n >> 3) & 1, nk = k0 >> 3, t0 = (k0 & 7) >> 1;
+                const int tile = (mn * NG8 + nk) * 128;
+                const int sidx[4] = {W2 + tile + (2 * hi) * 32 + 4 * gg + t0, W2 + tile + (2 * hi + 1) * 32 + 4 * gg + t0,
+                                     W2 + tile + (2 * hi) * 32 + 4 * gg + t0 + 1,
+                                     W2 + tile + (2 * hi + 1) * 32 + 4 * gg + t0 + 1};
+                if (gn) flush4(acc, sidx, gn + a.off_Wc2 + n * NC + k0);
+                else
+                    for (int i = 0; i < 4; ++i) acc[sidx[i]] = 0.0f;
+            } else if (g < e9) {
+                const int q = g - e8, r = q / (NC / 4), j = 4 * (q - r * (NC / 4));
+                const int sidx[4] = {W3 + 4 * j + r, W3 + 4 * j + 4 + r, W3 + 4 * j + 8 + r, W3 + 4 * j + 12 + r};
+                if (gn) flush4(acc, sidx, gn + a.off_Wc3 + r * NC + j);
+                else
+                    for (int i = 0; i < 4; ++i) acc[sidx[i]] = 0.0f;
+            } else {
+                const int j = 4 * (g - e9);
+                const int sidx[4] = {W3 + 4 * j + 3, W3 + 4 * j + 7, W3 + 4 * j + 11, W3 + 4 * j + 15};
+                if (gn) flush4(acc, sidx, gn + a.off_bc2 + j);
+                else
+                    for (int i = 0; i < 4; ++i) acc[sidx[i]] = 0.0f;
             }
         }
     }
@@ -517,7 +581,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             __syncthreads();
             for (int e = 0; e < cnt; ++e) {
                 const int64_t gid = s_gid[e];
-                flush_entry<NC>(a, acc + e * vg, gid - vn, gid, vg, tid, NT);
+                flush_entry<NC>(a, acc + e * vg, gid - vn, gid, tid, NT);
             }
         }
         __syncthreads();
