@@ -127,7 +127,7 @@ struct snp_context {
     bool reserved = false;
     // device workspace
     Buf views, rec, trect, counts, offsets, scan_tmp, keys, vals, keys_alt, vals_alt, hist, hist_scan, ranges,
-        px_state, px_nwalk, stats, small, g_view, g_h0, qkeys, qvals, qkeys_alt, qvals_alt, qhist, qhist_scan;
+        px_state, px_nwalk, stats, small, g_view, g_h0, qkeys, qvals, qkeys_alt, qvals_alt, qhist, qhist_scan, npack;
     // loss reduction: kLossSlots FP64 block sums, then the completion counter
     Buf loss_part;
     // pinned host staging
@@ -301,6 +301,8 @@ static void fill_args(RasterArgs &a, const snp_context *ctx, const snp_scene_des
     a.t_min = ctx->cfg.t_min;
     for (int k = 0; k < 3; ++k) a.bg[k] = ctx->cfg.bg[k];
     a.chunk = ctx->chunk;
+    a.npack = (float *)ctx->npack.p;
+    a.npack_stride = raster_npack_stride(d->color_mode, d->n_c, d->n_sigma);
 }
 
 extern "C" {
@@ -344,7 +346,7 @@ void snp_destroy(snp_context *ctx)
                    &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
                    &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0,
                    &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan,
-                   &ctx->loss_part};
+                   &ctx->npack, &ctx->loss_part};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_views) cudaFreeHost(ctx->h_views);
@@ -388,7 +390,7 @@ static snp_status ensure_frame(snp_context *ctx, int64_t n, int n_views, int64_t
     ENS(qvals_alt, (size_t)tiles * 4);
     ENS(qhist, (size_t)sort_hist_words(tiles) * 4);
     ENS(qhist_scan, (size_t)sort_hist_words(tiles) * 4);
-    (void)d;
+    ENS(npack, (size_t)n * raster_npack_stride(d->color_mode, d->n_c, d->n_sigma) * 4);
     return SNP_OK;
 }
 
@@ -514,6 +516,12 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     STAGE_BEGIN(SNP_STAGE_PROJECT);
     launch_project((const float *)scene->geom, n, (const View *)ctx->views.p, n_cams, ts, (float *)ctx->rec.p,
                    (int4 *)ctx->trect.p, (uint32_t *)ctx->counts.p, st);
+    {
+        RasterArgs pa;
+        fill_args(pa, ctx, desc, scene, nullptr);
+        if ((s = launch_pack_net(pa, desc->color_mode, desc->n_c, desc->weight_dtype == SNP_BF16, st)) != SNP_OK)
+            return fail(ctx, s, "network pack launch failed");
+    }
     STAGE_END();
     STAGE_BEGIN(SNP_STAGE_SCAN);
     scan_u32((const uint32_t *)ctx->counts.p, (uint32_t *)ctx->offsets.p, vn, d_total, (uint32_t *)ctx->scan_tmp.p,

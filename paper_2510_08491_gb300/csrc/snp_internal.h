@@ -63,6 +63,9 @@ struct RasterArgs {
     // persistent scheduling
     int *work_counter;        // next queue item (zeroed before each launch)
     const uint32_t *queue;    // tile ids ordered by decreasing list length (NULL: 0..n_tiles-1)
+    // per-primitive network blocks in the staged shared-memory layout (k_pack_net)
+    float *npack;             // [n][npack_stride]
+    int32_t npack_stride;     // floats per primitive
 };
 
 // snp_raster_*.cu
@@ -75,6 +78,8 @@ snp_status launch_mse_loss(const float *img, const float *tgt, int64_t n, float 
 snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
 size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);
+int raster_npack_stride(int color_mode, int n_c, int n_sigma);
+snp_status launch_pack_net(const RasterArgs &a, int color_mode, int n_c, int bf16, cudaStream_t st);
 size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);
 int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts);
 snp_status launch_fwd_ts8(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);

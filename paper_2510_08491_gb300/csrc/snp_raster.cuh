@@ -39,68 +39,99 @@ __host__ __device__ constexpr int cb_B2(int nc) { return 4 * nc + nc * w2_ld(nc)
 __host__ __device__ constexpr int cb_C3(int nc) { return 5 * nc + nc * w2_ld(nc); }
 __host__ __device__ constexpr int cb_B3(int nc) { return 9 * nc + nc * w2_ld(nc); }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Stage `cnt` list entries (global record ids s_gid[0..cnt)) of view offset vn
-// into shared memory.  All threads of the block participate.
-template <int NC, bool BF16>
+// into shared memory: the projection record and the primitive's packed network
+// block (already in the staged layout, see k_pack_net) as 16-byte asynchronous
+// copies.  All threads of the block participate; the caller synchronises.
 __device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
                                             const RasterArgs &a, int es)
 {
-    const int ns = a.n_sigma;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int idx = tid; idx < cnt * kRecFloats; idx += nt) {
-        const int e = idx / kRecFloats, k = idx - e * kRecFloats;
-        sm[e * es + k] = a.rec[(int64_t)s_gid[e] * kRecFloats + k];
+    constexpr int kRec16 = kRecFloats / 4;
+    const int per = es / 4;  // 16-byte pieces per entry: record, then the network block
+    for (int e = 0; e < cnt; ++e) {
+        const int64_t gid = s_gid[e];
+        const float *rec = a.rec + gid * kRecFloats;
+        const float *net = a.npack + (gid - vn) * a.npack_stride;
+        float *dst = sm + e * es;
+        for (int q = tid; q < per; q += nt) cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
     }
-    const int dper = 5 * ns + 1;
-    for (int idx = tid; idx < cnt * dper; idx += nt) {
-        const int e = idx / dper, k = idx - e * dper;
-        const int64_t base = ((int64_t)s_gid[e] - vn) * a.stride;
-        float *D = sm + e * es + kRecFloats;
-        if (k < 3 * ns) {
-            const int kk = k / 3, j = k - 3 * kk;
-            D[4 * kk + j] = a.omega0 * ld_w<BF16>(a.net, base + a.off_W1 + k);
-        } else if (k < 4 * ns) {
-            const int kk = k - 3 * ns;
-            D[4 * kk + 3] = a.omega0 * ld_w<BF16>(a.net, base + a.off_b1 + kk);
-        } else if (k < 5 * ns) {
-            const int kk = k - 4 * ns;
-            D[4 * ns + kk] = ld_w<BF16>(a.net, base + a.off_w2 + kk);
-        } else {
-            D[5 * ns] = ld_w<BF16>(a.net, base + a.off_b2);
+    cp_async_wait_all();
+}
+
+// Network block of primitive p in the staged layout (density block, then the
+// colour block), one warp per primitive; written once per forward and copied
+// into shared memory for every (tile, primitive) pair.
+template <int NC, bool BF16>
+__global__ void __launch_bounds__(256) k_pack_net(RasterArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= a.n) return;
+    const int ns = a.n_sigma;
+    const int64_t base = p * a.stride;
+    float *D = a.npack + p * a.npack_stride;
+    const int dstr = den_stride(ns);
+    for (int idx = lane; idx < dstr; idx += 32) {
+        float v = 0.0f;
+        if (idx < 4 * ns) {
+            const int k = idx >> 2, j = idx & 3;
+            v = a.omega0 * (j < 3 ? ld_w<BF16>(a.net, base + a.off_W1 + 3 * k + j) : ld_w<BF16>(a.net, base + a.off_b1 + k));
+        } else if (idx < 5 * ns) {
+            v = ld_w<BF16>(a.net, base + a.off_w2 + (idx - 4 * ns));
+        } else if (idx == 5 * ns) {
+            v = ld_w<BF16>(a.net, base + a.off_b2);
         }
+        D[idx] = v;
     }
     if constexpr (NC > 0) {
-        const int dstr = den_stride(ns);
-        for (int idx = tid; idx < cnt * NC; idx += nt) {
-            const int e = idx / NC, j = idx - e * NC;
-            const int64_t base = ((int64_t)s_gid[e] - vn) * a.stride;
-            float *C = sm + e * es + kRecFloats + dstr;
+        float *C = D + dstr;
+        for (int idx = lane; idx < 4 * NC; idx += 32) {
+            const int j = idx >> 2, r = idx & 3;
             const int64_t w = base + a.off_Wc1 + (int64_t)j * (3 + kFeat);
-            float h = ld_w<BF16>(a.net, base + a.off_bc1 + j);
+            float v;
+            if (r < 3) {
+                v = ld_w<BF16>(a.net, w + r);
+            } else {
+                // h0_j = bc1_j + Wc1[j][3..10] . feat (the per-primitive part of the first layer)
+                v = ld_w<BF16>(a.net, base + a.off_bc1 + j);
 #pragma unroll
-            for (int f = 0; f < kFeat; ++f)
-                h = fmaf(ld_w<BF16>(a.net, w + 3 + f), ld_w<BF16>(a.net, base + a.off_feat + f), h);
-            C[4 * j + 0] = ld_w<BF16>(a.net, w + 0);
-            C[4 * j + 1] = ld_w<BF16>(a.net, w + 1);
-            C[4 * j + 2] = ld_w<BF16>(a.net, w + 2);
-            C[4 * j + 3] = h;
+                for (int f = 0; f < kFeat; ++f)
+                    v = fmaf(ld_w<BF16>(a.net, w + 3 + f), ld_w<BF16>(a.net, base + a.off_feat + f), v);
+            }
+            C[cb_C1(NC) + idx] = v;
+        }
+        // Wc2 rows as bf16 hi / lo pairs, padded to w2_ld(NC) columns
+        uint32_t *W = reinterpret_cast<uint32_t *>(C + cb_W2(NC));
+        constexpr int rowp = w2_ld(NC) / 2;
+        for (int q = lane; q < NC * rowp; q += 32) {
+            const int row = q / rowp, k = 2 * (q - row * rowp);
+            Split2 sp{0u, 0u};
+            if (k < NC) {
+                const int64_t w = base + a.off_Wc2 + row * NC + k;
+                sp = split2<!BF16>(ld_w<BF16>(a.net, w), ld_w<BF16>(a.net, w + 1));
+            }
+            W[q] = sp.hi;
+            W[NC * rowp + q] = sp.lo;
+        }
+        for (int j = lane; j < NC; j += 32) {
             C[cb_B2(NC) + j] = ld_w<BF16>(a.net, base + a.off_bc2 + j);
             C[cb_C3(NC) + 4 * j + 0] = ld_w<BF16>(a.net, base + a.off_Wc3 + j);
             C[cb_C3(NC) + 4 * j + 1] = ld_w<BF16>(a.net, base + a.off_Wc3 + NC + j);
             C[cb_C3(NC) + 4 * j + 2] = ld_w<BF16>(a.net, base + a.off_Wc3 + 2 * NC + j);
             C[cb_C3(NC) + 4 * j + 3] = 0.0f;
-            if (j < 4) C[cb_B3(NC) + j] = j < 3 ? ld_w<BF16>(a.net, base + a.off_bc3 + j) : 0.0f;
         }
-        constexpr int half = NC * NC / 2;
-        for (int idx = tid; idx < cnt * half; idx += nt) {
-            const int e = idx / half, q = idx - e * half;
-            const int row = q / (NC / 2), k = 2 * (q - row * (NC / 2));
-            const int64_t w = ((int64_t)s_gid[e] - vn) * a.stride + a.off_Wc2 + row * NC + k;
-            const Split2 sp = split2<!BF16>(ld_w<BF16>(a.net, w), ld_w<BF16>(a.net, w + 1));
-            uint32_t *W = reinterpret_cast<uint32_t *>(sm + e * es + kRecFloats + dstr + cb_W2(NC));
-            W[(row * w2_ld(NC) + k) / 2] = sp.hi;
-            if constexpr (!BF16) W[((NC + row) * w2_ld(NC) + k) / 2] = sp.lo;
-        }
+        if (lane < 4) C[cb_B3(NC) + lane] = lane < 3 ? ld_w<BF16>(a.net, base + a.off_bc3 + lane) : 0.0f;
     }
 }
 

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 s_na[tid] = 0;
             }
             __syncthreads();
-            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
+            stage_chunk(sm, s_gid, cnt, vn, a, es);
             __syncthreads();
 
             // P1: hits among the entries this pixel walked in the forward

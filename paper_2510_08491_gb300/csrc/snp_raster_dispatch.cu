@@ -39,6 +39,30 @@ int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, in
     return ch;
 }
 
+int raster_npack_stride(int color_mode, int n_c, int n_sigma)
+{
+    return den_stride(n_sigma) + col_stride(nc_of(color_mode, n_c));
+}
+
+template <int NC, bool BF16>
+static snp_status run_pack(const RasterArgs &a, cudaStream_t st)
+{
+    if (a.n <= 0) return SNP_OK;
+    const int64_t blocks = (a.n * 32 + 255) / 256;
+    k_pack_net<NC, BF16><<<(unsigned)blocks, 256, 0, st>>>(a);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SNP_OK : SNP_ERR_CUDA;
+}
+
+snp_status launch_pack_net(const RasterArgs &a, int color_mode, int n_c, int bf16, cudaStream_t st)
+{
+    const int nc = nc_of(color_mode, n_c);
+    if (nc == 0) return bf16 ? run_pack<0, true>(a, st) : run_pack<0, false>(a, st);
+    if (nc == 32) return bf16 ? run_pack<32, true>(a, st) : run_pack<32, false>(a, st);
+    if (nc == 64) return bf16 ? run_pack<64, true>(a, st) : run_pack<64, false>(a, st);
+    return SNP_ERR_UNSUPPORTED;
+}
+
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st)
 {

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
                 s_na[tid] = 0;
             }
             __syncthreads();
-            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es);
+            stage_chunk(sm, s_gid, cnt, vn, a, es);
             __syncthreads();
 
             // P1: which pixels' rays enter which ellipsoids
