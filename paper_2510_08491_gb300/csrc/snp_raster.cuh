@@ -318,17 +318,33 @@ __device__ __forceinline__ PixRay load_ray(const float4 *s_ray, int slot)
     return r;
 }
 
-// ---- colour MLP (Sec. 3.1) over a warp batch: 32 pixel rays of one primitive,
-// lane r holding ray r.  z1 = relu(Wc1_d d + h0), a2 = Wc2 z1 + bc2, z2 = relu(a2),
-// c = sigmoid(Wc3 z2 + bc3).  The rays are the rows of the tensor-core tiles; a
-// batch runs in two passes of 16 rows, lane (g, t) holding rows 16 p + g and
-// 16 p + g + 8 of pass p.  Per-unit values of a pass live in accumulator layout:
-// x[nt][i] is row (i < 2 ? first : second), unit 8 nt + 2 t + (i & 1).
+// ---- colour MLP (Sec. 3.1) over a pass of 16 pixel rays of one primitive, one
+// warp.  z1 = relu(Wc1_d d + h0), a2 = Wc2 z1 + bc2, z2 = relu(a2),
+// c = sigmoid(Wc3 z2 + bc3).  The rays are the rows of the tensor-core tiles:
+// lane (g, t) = (lane / 4, lane % 4) holds rows g and g + 8 of the pass, and
+// per-unit values live in accumulator layout: x[nt][i] is row (i < 2 ? g : g + 8),
+// unit 8 nt + 2 t + (i & 1).
 
-__device__ __forceinline__ float3 shfl_f3(float3 v, int src)
+// The two rows of lane (g, t) in a pass over positions r0 .. r0+15 of an entry's
+// composited list (n entries): their pixel slots (0 past the end), validity and
+// unit ray directions.
+struct PassRows {
+    int pix0, pix1;
+    bool v0, v1;
+    float3 d0, d1;
+};
+
+__device__ __forceinline__ PassRows pass_rows(const float4 *s_ray, const uint16_t *list, int r0, int n)
 {
-    return make_float3(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                       __shfl_sync(0xffffffffu, v.z, src));
+    const int g = (threadIdx.x & 31) >> 2;
+    PassRows p;
+    p.v0 = r0 + g < n;
+    p.v1 = r0 + g + 8 < n;
+    p.pix0 = p.v0 ? list[r0 + g] : 0;
+    p.pix1 = p.v1 ? list[r0 + g + 8] : 0;
+    p.d0 = unit_dir(load_ray(s_ray, p.pix0));
+    p.d1 = unit_dir(load_ray(s_ray, p.pix1));
+    return p;
 }
 
 // First layer for the pass rows with directions d0, d1.
@@ -412,84 +428,79 @@ __device__ __forceinline__ void color_gemm_gw(const uint32_t (&gh)[NC / 16][4], 
 // Unit index of slot m (= 2 nt + j) of lane column t in accumulator layout.
 __device__ __forceinline__ int acc_unit(int m, int t) { return 8 * (m >> 1) + 2 * t + (m & 1); }
 
-// Colour of the batch's rays.  Lane r holds ray r: direction d, output slot pix,
-// valid; the valid rays are lanes 0 .. nrows-1 (nrows is warp-uniform, so a batch
-// of at most 16 rays runs one pass).  Colour channel c of a valid ray goes to
-// out[c * plane + pix].
+// Colour of the composited pairs at positions r0 .. r0+15 of an entry's list
+// (n entries; list holds pixel slots).  Channel c of the pair at slot q goes to
+// out[c * plane + q].
 template <int NC, bool BF16>
-__device__ __forceinline__ void warp_color(const float *Cb, float3 d, int pix, bool valid, int nrows, float *out,
-                                           int plane)
+__device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s_ray, const uint16_t *list, int r0,
+                                                int n, float *out, int plane)
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int lane = threadIdx.x & 31, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
     const float *B2 = Cb + cb_B2(NC);
     const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
     const float4 B3 = *reinterpret_cast<const float4 *>(Cb + cb_B3(NC));
     const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
-    const int vp = valid ? pix : -1;
-    const int passes = nrows > 16 ? 2 : 1;
     __syncwarp();
-#pragma unroll 1
-    for (int p = 0; p < passes; ++p) {
-        const int r0 = 16 * p + g, r1 = r0 + 8;
-        const float3 d0 = shfl_f3(d, r0), d1 = shfl_f3(d, r1);
-        float z[NC / 8][4];
-        color_layer1<NC>(C1, d0, d1, z);
-        uint32_t zh[NC / 16][4], zl[NC / 16][4];
-        acc_to_afrag<NC>(z, zh, zl);
-        float acc[NC / 8][4];
+    const PassRows pr = pass_rows(s_ray, list, r0, n);
+    float z[NC / 8][4];
+    color_layer1<NC>(C1, pr.d0, pr.d1, z);
+    uint32_t zh[NC / 16][4], zl[NC / 16][4];
+    acc_to_afrag<NC>(z, zh, zl);
+    float acc[NC / 8][4];
 #pragma unroll
-        for (int nt = 0; nt < NC / 8; ++nt) {
-            const float2 b = *reinterpret_cast<const float2 *>(B2 + 8 * nt + 2 * t);
-            acc[nt][0] = acc[nt][2] = b.x;
-            acc[nt][1] = acc[nt][3] = b.y;
-        }
-        color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
-        float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int nt = 0; nt < NC / 8; ++nt) {
+        const float2 b = *reinterpret_cast<const float2 *>(B2 + 8 * nt + 2 * t);
+        acc[nt][0] = acc[nt][2] = b.x;
+        acc[nt][1] = acc[nt][3] = b.y;
+    }
+    color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
+    float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int nt = 0; nt < NC / 8; ++nt) {
+    for (int nt = 0; nt < NC / 8; ++nt) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float4 w = C3[acc_unit(2 * nt + j, t)];
-                const float za = fmaxf(acc[nt][j], 0.0f), zb = fmaxf(acc[nt][2 + j], 0.0f);
-                c[0] = fmaf(w.x, za, c[0]);
-                c[1] = fmaf(w.y, za, c[1]);
-                c[2] = fmaf(w.z, za, c[2]);
-                c[3] = fmaf(w.x, zb, c[3]);
-                c[4] = fmaf(w.y, zb, c[4]);
-                c[5] = fmaf(w.z, zb, c[5]);
-            }
+        for (int j = 0; j < 2; ++j) {
+            const float4 w = C3[acc_unit(2 * nt + j, t)];
+            const float za = fmaxf(acc[nt][j], 0.0f), zb = fmaxf(acc[nt][2 + j], 0.0f);
+            c[0] = fmaf(w.x, za, c[0]);
+            c[1] = fmaf(w.y, za, c[1]);
+            c[2] = fmaf(w.z, za, c[2]);
+            c[3] = fmaf(w.x, zb, c[3]);
+            c[4] = fmaf(w.y, zb, c[4]);
+            c[5] = fmaf(w.z, zb, c[5]);
         }
+    }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            c[q] += __shfl_xor_sync(0xffffffffu, c[q], 1);
-            c[q] += __shfl_xor_sync(0xffffffffu, c[q], 2);
-        }
-        const int q0 = __shfl_sync(0xffffffffu, vp, r0), q1 = __shfl_sync(0xffffffffu, vp, r1);
-        const int q = t == 0 ? q0 : q1;
-        if (t < 2 && q >= 0) {
-            const int o = 3 * t;
-            out[q] = sigmoidf_fast(c[o + 0] + B3.x);
-            out[plane + q] = sigmoidf_fast(c[o + 1] + B3.y);
-            out[2 * plane + q] = sigmoidf_fast(c[o + 2] + B3.z);
-        }
+    for (int q = 0; q < 6; ++q) {
+        c[q] += __shfl_xor_sync(0xffffffffu, c[q], 1);
+        c[q] += __shfl_xor_sync(0xffffffffu, c[q], 2);
+    }
+    const bool v = t == 0 ? pr.v0 : pr.v1;
+    if (t < 2 && v) {
+        const int q = t == 0 ? pr.pix0 : pr.pix1, o = 3 * t;
+        out[q] = sigmoidf_fast(c[o + 0] + B3.x);
+        out[plane + q] = sigmoidf_fast(c[o + 1] + B3.y);
+        out[2 * plane + q] = sigmoidf_fast(c[o + 2] + B3.z);
     }
 }
 
-// Backward of the colour MLP for the batch: lane r holds ray r's direction d and
-// dL/da3 (the pre-sigmoid colour gradient; zero for lanes without a pair); rows
-// at or beyond nrows (warp-uniform) carry no pair, so nrows <= 16 runs one pass.
-// Accumulates dL/d(Wc1_d, h0) into AC1 [NC][4], dL/dWc2 into AW2 [NC * NC] (in
-// mma fragment order: element i of lane l of output tile (mn, nk), i.e. of row
-// 16 mn + l/4 + 8 (i >> 1), column 8 nk + 2 (l % 4) + (i & 1), at
-// ((mn NC/8 + nk) 4 + i) 32 + l) and
-// dL/d(Wc3, bc2) into AW3 [NC][4] (shared memory, atomics).  The three
-// contractions a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays
-// dL/da2 z1^T run on the tensor cores; the last uses movmatrix transposes of the
-// pass's register fragments with the rays as the reduction dimension.
+// Backward of the colour MLP for the composited pairs at positions r0 .. r0+15 of
+// an entry's list.  Per pair: dL/dc = w dL (w: compositing weight at w_e[slot],
+// dL: dl[c * npix + slot]) and dL/da3 = dL/dc c (1 - c) (c at col_e[c * plane +
+// slot]).  Accumulates, with shared-memory atomics:
+//   AC1 [NC][4]   dL/d(Wc1_d, h0);
+//   AW2 [NC * NC] dL/dWc2 in mma fragment order (element i of lane l of output
+//                 tile (mn, nk), i.e. row 16 mn + l/4 + 8 (i >> 1), column
+//                 8 nk + 2 (l % 4) + (i & 1), at ((mn NC/8 + nk) 4 + i) 32 + l);
+//   AW3 [NC][4]   dL/d(Wc3, bc2);  AB3 [3] dL/dbc3.
+// a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays dL/da2 z1^T run on
+// the tensor cores; the last takes movmatrix transposes of the pass's register
+// fragments, with the 16 rays as the reduction dimension.
 template <int NC, bool BF16>
-__device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3 g_a3, int nrows, float *AC1,
-                                               float *AW2, float *AW3)
+__device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float4 *s_ray, const uint16_t *list,
+                                                    int r0, int n, const float *w_e, const float *dl, int npix,
+                                                    const float *col_e, int plane, float *AC1, float *AW2,
+                                                    float *AW3, float *AB3)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
@@ -497,111 +508,122 @@ __device__ __forceinline__ void warp_color_bwd(const float *Cb, float3 d, float3
     const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
     const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
     __syncwarp();
-    const int passes = nrows > 16 ? 2 : 1;
-#pragma unroll 1
-    for (int p = 0; p < passes; ++p) {
-        const int r0 = 16 * p + g, r1 = r0 + 8;
-        const float3 d0 = shfl_f3(d, r0), d1 = shfl_f3(d, r1);
-        const float3 e0 = shfl_f3(g_a3, r0), e1 = shfl_f3(g_a3, r1);
-        float z[NC / 8][4];
-        color_layer1<NC>(C1, d0, d1, z);
-        uint32_t zh[NC / 16][4], zl[NC / 16][4];
-        acc_to_afrag<NC>(z, zh, zl);
-        float acc[NC / 8][4];
+    const PassRows pr = pass_rows(s_ray, list, r0, n);
+    const float3 d0 = pr.d0, d1 = pr.d1;
+    auto ga3 = [&](bool v, int q) {
+        if (!v) return make_float3(0.f, 0.f, 0.f);
+        const float w = w_e[q];
+        const float cx = col_e[q], cy = col_e[plane + q], cz = col_e[2 * plane + q];
+        return make_float3(w * dl[q] * cx * (1.0f - cx), w * dl[npix + q] * cy * (1.0f - cy),
+                           w * dl[2 * npix + q] * cz * (1.0f - cz));
+    };
+    const float3 e0 = ga3(pr.v0, pr.pix0), e1 = ga3(pr.v1, pr.pix1);
+    // dL/dbc3 = sum of dL/da3 over the pass (one lane per row pair contributes)
+    {
+        float b[3] = {t == 0 ? e0.x + e1.x : 0.0f, t == 0 ? e0.y + e1.y : 0.0f, t == 0 ? e0.z + e1.z : 0.0f};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            b[k] = warp_sum(b[k]);
+            if (lane == k && b[k] != 0.0f) atomicAdd(AB3 + k, b[k]);
+        }
+    }
+    float z[NC / 8][4];
+    color_layer1<NC>(C1, d0, d1, z);
+    uint32_t zh[NC / 16][4], zl[NC / 16][4];
+    acc_to_afrag<NC>(z, zh, zl);
+    float acc[NC / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < NC / 8; ++nt) {
+        const float2 b = *reinterpret_cast<const float2 *>(B2 + 8 * nt + 2 * t);
+        acc[nt][0] = acc[nt][2] = b.x;
+        acc[nt][1] = acc[nt][3] = b.y;
+    }
+    color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
+    // dL/dz2 = Wc3^T dL/da3, dL/da2 (ReLU), and the (Wc3, bc2) partials of the two rows
+    {
+        float pw[NC];
 #pragma unroll
         for (int nt = 0; nt < NC / 8; ++nt) {
-            const float2 b = *reinterpret_cast<const float2 *>(B2 + 8 * nt + 2 * t);
-            acc[nt][0] = acc[nt][2] = b.x;
-            acc[nt][1] = acc[nt][3] = b.y;
-        }
-        color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
-        // dL/dz2 = Wc3^T dL/da3, dL/da2 (ReLU), and the (Wc3, bc2) partials of the two rows
-        {
-            float pw[NC];
 #pragma unroll
-            for (int nt = 0; nt < NC / 8; ++nt) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int m = 2 * nt + j;
-                    const float4 w = C3[acc_unit(m, t)];
-                    const float a = acc[nt][j], b = acc[nt][2 + j];
-                    const float za = fmaxf(a, 0.0f), zb = fmaxf(b, 0.0f);
-                    const float ga = a > 0.0f ? fmaf(w.x, e0.x, fmaf(w.y, e0.y, w.z * e0.z)) : 0.0f;
-                    const float gb = b > 0.0f ? fmaf(w.x, e1.x, fmaf(w.y, e1.y, w.z * e1.z)) : 0.0f;
-                    pw[4 * m + 0] = fmaf(e0.x, za, e1.x * zb);
-                    pw[4 * m + 1] = fmaf(e0.y, za, e1.y * zb);
-                    pw[4 * m + 2] = fmaf(e0.z, za, e1.z * zb);
-                    pw[4 * m + 3] = ga + gb;
-                    acc[nt][j] = ga;
-                    acc[nt][2 + j] = gb;
-                }
-            }
-            reduce_scatter_rows<NC>(pw);
-#pragma unroll
-            for (int i = 0; i < NC / 8; ++i) {
-                const int idx = g * (NC / 8) + i;
-                if (pw[i] != 0.0f) atomicAdd(AW3 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pw[i]);
+            for (int j = 0; j < 2; ++j) {
+                const int m = 2 * nt + j;
+                const float4 w = C3[acc_unit(m, t)];
+                const float a = acc[nt][j], b = acc[nt][2 + j];
+                const float za = fmaxf(a, 0.0f), zb = fmaxf(b, 0.0f);
+                const float ga = a > 0.0f ? fmaf(w.x, e0.x, fmaf(w.y, e0.y, w.z * e0.z)) : 0.0f;
+                const float gb = b > 0.0f ? fmaf(w.x, e1.x, fmaf(w.y, e1.y, w.z * e1.z)) : 0.0f;
+                pw[4 * m + 0] = fmaf(e0.x, za, e1.x * zb);
+                pw[4 * m + 1] = fmaf(e0.y, za, e1.y * zb);
+                pw[4 * m + 2] = fmaf(e0.z, za, e1.z * zb);
+                pw[4 * m + 3] = ga + gb;
+                acc[nt][j] = ga;
+                acc[nt][2 + j] = gb;
             }
         }
-        uint32_t gh[NC / 16][4], gl[NC / 16][4];
-        acc_to_afrag<NC>(acc, gh, gl);
-        // dL/dz1 = Wc2^T dL/da2, dL/da1 (ReLU) and the (Wc1_d, h0) partials
-        {
-            float gz[NC / 8][4];
+        reduce_scatter_rows<NC>(pw);
 #pragma unroll
-            for (int nk = 0; nk < NC / 8; ++nk) gz[nk][0] = gz[nk][1] = gz[nk][2] = gz[nk][3] = 0.0f;
-            color_gemm_gw<NC, BF16>(gh, gl, Wh, gz);
-            float pc[NC];
-#pragma unroll
-            for (int nk = 0; nk < NC / 8; ++nk) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int m = 2 * nk + j;
-                    const float ga = z[nk][j] > 0.0f ? gz[nk][j] : 0.0f;
-                    const float gb = z[nk][2 + j] > 0.0f ? gz[nk][2 + j] : 0.0f;
-                    pc[4 * m + 0] = fmaf(ga, d0.x, gb * d1.x);
-                    pc[4 * m + 1] = fmaf(ga, d0.y, gb * d1.y);
-                    pc[4 * m + 2] = fmaf(ga, d0.z, gb * d1.z);
-                    pc[4 * m + 3] = ga + gb;
-                }
-            }
-            reduce_scatter_rows<NC>(pc);
-#pragma unroll
-            for (int i = 0; i < NC / 8; ++i) {
-                const int idx = g * (NC / 8) + i;
-                if (pc[i] != 0.0f) atomicAdd(AC1 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pc[i]);
-            }
+        for (int i = 0; i < NC / 8; ++i) {
+            const int idx = g * (NC / 8) + i;
+            if (pw[i] != 0.0f) atomicAdd(AW3 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pw[i]);
         }
-        // dL/dWc2 += GA^T Z over the pass rows: A = transposed dL/da2 blocks,
-        // B = transposed z1 blocks, the 16 rows as the reduction dimension
-        uint32_t tzh[NC / 8][2], tzl[NC / 8][2];
+    }
+    uint32_t gh[NC / 16][4], gl[NC / 16][4];
+    acc_to_afrag<NC>(acc, gh, gl);
+    // dL/dz1 = Wc2^T dL/da2, dL/da1 (ReLU) and the (Wc1_d, h0) partials
+    {
+        float gz[NC / 8][4];
+#pragma unroll
+        for (int nk = 0; nk < NC / 8; ++nk) gz[nk][0] = gz[nk][1] = gz[nk][2] = gz[nk][3] = 0.0f;
+        color_gemm_gw<NC, BF16>(gh, gl, Wh, gz);
+        float pc[NC];
 #pragma unroll
         for (int nk = 0; nk < NC / 8; ++nk) {
-            const int kt = nk >> 1, o = 2 * (nk & 1);
-            tzh[nk][0] = movm_trans(zh[kt][o]);
-            tzh[nk][1] = movm_trans(zh[kt][o + 1]);
-            tzl[nk][0] = movm_trans(zl[kt][o]);
-            tzl[nk][1] = movm_trans(zl[kt][o + 1]);
-        }
 #pragma unroll
-        for (int mn = 0; mn < NC / 16; ++mn) {
-            const uint32_t th[4] = {movm_trans(gh[mn][0]), movm_trans(gh[mn][2]), movm_trans(gh[mn][1]),
-                                    movm_trans(gh[mn][3])};
-            const uint32_t tl[4] = {movm_trans(gl[mn][0]), movm_trans(gl[mn][2]), movm_trans(gl[mn][1]),
-                                    movm_trans(gl[mn][3])};
-#pragma unroll
-            for (int nk = 0; nk < NC / 8; ++nk) {
-                float d4[4] = {0.f, 0.f, 0.f, 0.f};
-                mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
-                mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
-                mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
-                // fragment order: element i of lane l of tile (mn, nk) at ((mn NC/8 + nk) 4 + i) 32 + l,
-                // so each atomic of the warp hits 32 consecutive words (no bank conflicts)
-                float *dst = AW2 + (mn * (NC / 8) + nk) * 128 + lane;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (d4[i] != 0.0f) atomicAdd(dst + 32 * i, d4[i]);
+            for (int j = 0; j < 2; ++j) {
+                const int m = 2 * nk + j;
+                const float ga = z[nk][j] > 0.0f ? gz[nk][j] : 0.0f;
+                const float gb = z[nk][2 + j] > 0.0f ? gz[nk][2 + j] : 0.0f;
+                pc[4 * m + 0] = fmaf(ga, d0.x, gb * d1.x);
+                pc[4 * m + 1] = fmaf(ga, d0.y, gb * d1.y);
+                pc[4 * m + 2] = fmaf(ga, d0.z, gb * d1.z);
+                pc[4 * m + 3] = ga + gb;
             }
+        }
+        reduce_scatter_rows<NC>(pc);
+#pragma unroll
+        for (int i = 0; i < NC / 8; ++i) {
+            const int idx = g * (NC / 8) + i;
+            if (pc[i] != 0.0f) atomicAdd(AC1 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pc[i]);
+        }
+    }
+    // dL/dWc2 += GA^T Z over the pass rows: A = transposed dL/da2 blocks,
+    // B = transposed z1 blocks, the 16 rows as the reduction dimension
+    uint32_t tzh[NC / 8][2], tzl[NC / 8][2];
+#pragma unroll
+    for (int nk = 0; nk < NC / 8; ++nk) {
+        const int kt = nk >> 1, o = 2 * (nk & 1);
+        tzh[nk][0] = movm_trans(zh[kt][o]);
+        tzh[nk][1] = movm_trans(zh[kt][o + 1]);
+        tzl[nk][0] = movm_trans(zl[kt][o]);
+        tzl[nk][1] = movm_trans(zl[kt][o + 1]);
+    }
+#pragma unroll
+    for (int mn = 0; mn < NC / 16; ++mn) {
+        const uint32_t th[4] = {movm_trans(gh[mn][0]), movm_trans(gh[mn][2]), movm_trans(gh[mn][1]),
+                                movm_trans(gh[mn][3])};
+        const uint32_t tl[4] = {movm_trans(gl[mn][0]), movm_trans(gl[mn][2]), movm_trans(gl[mn][1]),
+                                movm_trans(gl[mn][3])};
+#pragma unroll
+        for (int nk = 0; nk < NC / 8; ++nk) {
+            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+            mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
+            mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
+            mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
+            // fragment order: each atomic of the warp hits 32 consecutive words (no bank conflicts)
+            float *dst = AW2 + (mn * (NC / 8) + nk) * 128 + lane;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (d4[i] != 0.0f) atomicAdd(dst + 32 * i, d4[i]);
         }
     }
 }
@@ -642,12 +664,12 @@ __device__ __forceinline__ void warp_prefix64(const int *count, int n, int *pre)
     else __shfl_sync(0xffffffffu, y, 31);
 }
 
-// Warp batches of 32 pairs per list entry: nb[e] = ceil(count[e] / 32) and its
-// exclusive prefix pre[0..n].  One warp.
-__device__ __forceinline__ void warp_batch_prefix(const int *count, int n, int *nb, int *pre)
+// Work items of (1 << sh) pairs per list entry: nb[e] = ceil(count[e] / 2^sh) and
+// its exclusive prefix pre[0..n].  One warp.
+__device__ __forceinline__ void warp_batch_prefix(const int *count, int n, int sh, int *nb, int *pre)
 {
     const unsigned lane = lane_id();
-    for (int e = (int)lane; e < n; e += 32) nb[e] = (count[e] + 31) >> 5;
+    for (int e = (int)lane; e < n; e += 32) nb[e] = (count[e] + (1 << sh) - 1) >> sh;
     __syncwarp();
     warp_prefix64(nb, n, pre);
 }

@@ -146,17 +146,16 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
     }
 }
 
-// Gradient of one (pixel, primitive) pair, reduced across the warp into the
-// entry's shared-memory accumulator A.  All 32 lanes call it together; lanes
-// without a pair pass contrib = false (their contributions are zero) and the
-// pairs occupy lanes 0 .. nrows-1.
-template <int NC, int FORM, bool BF16>
-__device__ __forceinline__ void pair_backward(const float *R, const float *D, const float *Cb, int ns, float w0,
-                                              const CamK &ck, const PixRay &ry, bool contrib, int nrows, float g_ah,
-                                              float3 g_c, float3 col, float *A)
+// Density and geometry gradient of one (pixel, primitive) pair, reduced across
+// the warp into the entry's shared-memory accumulator A (the colour MLP's part is
+// a separate work item, warp_color_bwd_pass).  All 32 lanes call it together;
+// lanes without a pair pass contrib = false (their contributions are zero).
+// g_c: dL/dcolour, used for a constant colour only.
+template <int NC, int FORM>
+__device__ __forceinline__ void pair_backward(const float *R, const float *D, int ns, float w0, const CamK &ck,
+                                              const PixRay &ry, bool contrib, float g_ah, float3 g_c, float *A)
 {
     const unsigned lane = lane_id();
-    const float3 d = unit_dir(ry);
     Hit h;
     if (!contrib || !intersect(R, ck, ry, h)) {
         // benign geometry for lanes that only take part in the warp reductions
@@ -169,7 +168,6 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
         h.half = 1.0f;
         g_ah = 0.0f;
         g_c = make_float3(0.f, 0.f, 0.f);
-        col = make_float3(0.f, 0.f, 0.f);
     }
     // ---- density (closed-form integral)
     const float inv_m = R[kRecInvM];
@@ -309,11 +307,6 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
     const float g_dy = g_f.x * R[kRecG + 1] + g_f.y * R[kRecG + 4] + g_f.z * R[kRecG + 7] +
                        g_dg.x * ck.r1.x + g_dg.y * ck.r1.y + g_dg.z * ck.r1.z;
 
-    float3 g_a3 = make_float3(0.f, 0.f, 0.f);
-    if constexpr (NC > 0) {
-        g_a3 = make_float3(g_c.x * col.x * (1.0f - col.x), g_c.y * col.y * (1.0f - col.y),
-                           g_c.z * col.z * (1.0f - col.z));
-    }
     {
         float vv[32];
         vv[kGvG + 0] = g_f.x * h.dx; vv[kGvG + 1] = g_f.x * h.dy;
@@ -332,22 +325,15 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, co
         vv[22] = 0.0f;
         vv[23] = 0.0f;
         vv[24] = g_b2;
-        vv[25] = g_a3.x; vv[26] = g_a3.y; vv[27] = g_a3.z;
 #pragma unroll
-        for (int q = 28; q < 32; ++q) vv[q] = 0.0f;
+        for (int q = 25; q < 32; ++q) vv[q] = 0.0f;
         const float r = warp_reduce_scatter32(vv);
         if (r != 0.0f) {
             if (lane < (unsigned)kGvFloats) atomicAdd(A + ga_geo(ns) + lane, r);
             else if (lane == 24) atomicAdd(A + 5 * ns, r);
-            else if (lane < 28) atomicAdd(A + ga_bc3(ns) + (lane - 25), r);
         }
     }
 
-    // ---- colour MLP backward (whole warp)
-    if constexpr (NC > 0) {
-        float *AC1 = A + ga_col(ns);
-        warp_color_bwd<NC, BF16>(Cb, d, g_a3, nrows, AC1, AC1 + 4 * NC, AC1 + 4 * NC + NC * NC);
-    }
 }
 
 template <int TS>
@@ -379,7 +365,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + 3 * CH * NPIX);  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
     __shared__ uint32_t s_gid[kMaxChunk];
-    __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65];
+    __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
     __shared__ uint32_t s_maxwalk;
 
@@ -507,7 +493,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             __syncthreads();
             if (tid < 32) {
                 warp_prefix64(s_na, cnt, s_pa);
-                warp_batch_prefix(s_na, cnt, s_nb, s_pb);
+                warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
+                warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
             }
             __syncthreads();
             // P4: colour of every composited pair
@@ -523,15 +510,12 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     s_col[(2 * CH + e) * NPIX + pix] = R[kRecRgb + 2];
                 }
             } else {
-                const int nb = s_pb[cnt];
+                const int np = s_pp[cnt];
                 int e = 0;
-                for (int b = wid; b < nb; b += NT / 32) {
-                    while (b >= s_pb[e + 1]) ++e;
-                    const int k0 = (b - s_pb[e]) * 32, kk = k0 + (int)lane;
-                    const bool valid = kk < s_na[e];
-                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
-                    warp_color<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)),
-                                         pix, valid, s_na[e] - k0, s_col + e * NPIX, CH * NPIX);
+                for (int q = wid; q < np; q += NT / 32) {
+                    while (q >= s_pp[e + 1]) ++e;
+                    warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
+                                              (q - s_pp[e]) * 16, s_na[e], s_col + e * NPIX, CH * NPIX);
                 }
             }
             __syncthreads();
@@ -557,25 +541,38 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            // P6: per-pair gradients in warp batches of one entry each
+            // P6: per-pair gradients.  Work items: density / geometry batches of 32 pairs
+            // of one entry (per-lane chain, warp reductions), then colour-MLP passes of
+            // 16 pairs of one entry (tensor cores); any warp takes any item.
             {
-                const int nb = s_pb[cnt];
-                int e = 0;
-                for (int b = wid; b < nb; b += NT / 32) {
-                    while (b >= s_pb[e + 1]) ++e;
-                    const int k0 = (b - s_pb[e]) * 32, kk = k0 + (int)lane;
-                    const bool valid = kk < s_na[e];
-                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
-                    const PixRay r = load_ray(s_ray, pix);
-                    const float *R = sm + e * es;
-                    // dL/dc_i = w_i dL
-                    const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
-                    const float3 g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
-                    const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + pix], s_col[(1 * CH + e) * NPIX + pix],
-                                                   s_col[(2 * CH + e) * NPIX + pix]);
-                    pair_backward<NC, FORM, BF16>(R, R + kRecFloats, R + kRecFloats + den_stride(ns), ns, w0, ck, r,
-                                                  valid, s_na[e] - k0, s_ah[e * NPIX + pix], g_c, col,
-                                                  acc + e * vg);
+                const int nb = s_pb[cnt], np = NC > 0 ? s_pp[cnt] : 0;
+                int e = 0, ec = 0;
+                for (int it = wid; it < nb + np; it += NT / 32) {
+                    if (it < nb) {
+                        while (it >= s_pb[e + 1]) ++e;
+                        const int kk = (it - s_pb[e]) * 32 + (int)lane;
+                        const bool valid = kk < s_na[e];
+                        const int pix = valid ? s_al[e * NPIX + kk] : 0;
+                        const PixRay r = load_ray(s_ray, pix);
+                        const float *R = sm + e * es;
+                        float3 g_c = make_float3(0.f, 0.f, 0.f);
+                        if constexpr (NC == 0) {
+                            // dL/dc_i = w_i dL
+                            const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
+                            g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
+                        }
+                        pair_backward<NC, FORM>(R, R + kRecFloats, ns, w0, ck, r, valid, s_ah[e * NPIX + pix], g_c,
+                                                acc + e * vg);
+                    } else if constexpr (NC > 0) {
+                        const int q = it - nb;
+                        while (q >= s_pp[ec + 1]) ++ec;
+                        float *A = acc + ec * vg;
+                        float *AC1 = A + ga_col(ns);
+                        warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
+                                                      s_al + ec * NPIX, (q - s_pp[ec]) * 16, s_na[ec],
+                                                      s_w + ec * NPIX, s_dl, NPIX, s_col + ec * NPIX, CH * NPIX, AC1,
+                                                      AC1 + 4 * NC, AC1 + 4 * NC + NC * NC, A + ga_bc3(ns));
+                    }
                 }
             }
             __syncthreads();

@@ -11,8 +11,8 @@
 //                   T = exp(-sum alpha_hat) (Eq. 4, 9) and early termination --
 //                   transmittance does not depend on colour, so it is settled
 //                   before any colour is evaluated; composited pairs are listed;
-//   P4 (per warp)   colour MLP of the composited pairs in warp batches of 32
-//                   pairs of one list entry (tensor cores for the hidden layer);
+//   P4 (per warp)   colour MLP of the composited pairs in passes of 16 pairs of
+//                   one list entry (tensor cores for the hidden layer);
 //   P5 (per pixel)  C += w * colour in list order.
 // The result is the sequential front-to-back composite.  The per-pixel composited
 // colour, optical depth and number of list entries walked are saved for the
@@ -174,18 +174,15 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
 
             if constexpr (NC > 0) {
                 __syncthreads();
-                if (tid < 32) warp_batch_prefix(s_na, cnt, s_nb, s_pb);
+                if (tid < 32) warp_batch_prefix(s_na, cnt, 4, s_nb, s_pb);
                 __syncthreads();
-                // P4: colour of every composited pair, in warp batches of one entry each
-                const int nb = s_pb[cnt];
+                // P4: colour of every composited pair, one warp per pass of 16 pairs of one entry
+                const int np = s_pb[cnt];
                 int e = 0;
-                for (int b = tid >> 5; b < nb; b += NT / 32) {
-                    while (b >= s_pb[e + 1]) ++e;
-                    const int k0 = (b - s_pb[e]) * 32, kk = k0 + (int)lane_id();
-                    const bool valid = kk < s_na[e];
-                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
-                    warp_color<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), unit_dir(load_ray(s_ray, pix)),
-                                         pix, valid, s_na[e] - k0, s_col + e * NPIX, CH * NPIX);
+                for (int q = tid >> 5; q < np; q += NT / 32) {
+                    while (q >= s_pb[e + 1]) ++e;
+                    warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
+                                              (q - s_pb[e]) * 16, s_na[e], s_col + e * NPIX, CH * NPIX);
                 }
                 __syncthreads();
                 // P5: accumulate in list order
