@@ -246,10 +246,30 @@ __device__ __forceinline__ bool intersect(const float *R, const CamK &ck, const 
     return true;
 }
 
+// Whether the ray enters the ellipsoid: the sign of h^2 A = |e+f|^2 - mu_z^2 |e x f|^2
+// (no reciprocal, no chord), with the same FP64 re-evaluation band |h^2| < 1e-4
+// as intersect(), so both always agree.
 __device__ __forceinline__ bool hit_test(const float *R, const CamK &ck, const PixRay &ry)
 {
-    Hit h;
-    return intersect(R, ck, ry, h);
+    const float4 g0 = reinterpret_cast<const float4 *>(R)[0];  // G00 G01 G02 G10
+    const float4 g1 = reinterpret_cast<const float4 *>(R)[1];  // G11 G12 G20 G21
+    const float4 g2 = reinterpret_cast<const float4 *>(R)[2];  // G22 ex ey ez
+    const float4 g3 = reinterpret_cast<const float4 *>(R)[3];  // mz mz2 Uhi Ulo
+    const float4 g4 = reinterpret_cast<const float4 *>(R)[4];  // Vhi Vlo ...
+    const float dx = ((ry.pxh - g3.z) - g3.w) * ck.ifx;
+    const float dy = ((ry.pyh - g4.x) - g4.y) * ck.ify;
+    const float3 f = make_float3(fmaf(g0.x, dx, g0.y * dy), fmaf(g0.w, dx, g1.x * dy), fmaf(g1.z, dx, g1.w * dy));
+    const float3 e = make_float3(g2.y, g2.z, g2.w);
+    const float3 dp = make_float3(e.x + f.x, e.y + f.y, e.z + f.z);
+    const float A = fmaf(dp.x, dp.x, fmaf(dp.y, dp.y, dp.z * dp.z));
+    const float3 w = make_float3(fmaf(e.y, f.z, -e.z * f.y), fmaf(e.z, f.x, -e.x * f.z), fmaf(e.x, f.y, -e.y * f.x));
+    const float W2 = fmaf(w.x, w.x, fmaf(w.y, w.y, w.z * w.z));
+    const float hA = fmaf(-g3.y, W2, A);
+    if (fabsf(hA) < kRefineH2 * A) {
+        Hit h;
+        return intersect(R, ck, ry, h);
+    }
+    return hA > 0.0f;
 }
 
 // alpha_hat of one (ray, primitive) pair.  With u_mid = s a_c + (t / m) dg,
