@@ -189,7 +189,9 @@ const char *snp_last_error(const snp_context *ctx);
  * cameras and configuration, with room for max_keys tile keys (0 = estimate:
  * grow on demand).  After a successful reserve no render call on the same
  * shapes allocates device memory; a forward that would exceed max_keys returns
- * SNP_ERR_CAPACITY instead of growing (required before stream capture). */
+ * SNP_ERR_CAPACITY instead of growing (required before stream capture).  While
+ * reserved, every forward must use the reserved tile size (SNP_ERR_INVALID_ARG
+ * otherwise); a later reserve replaces the reservation. */
 snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_camera *cams, int32_t n_cams,
                        const snp_config *cfg, int64_t max_keys);
 

@@ -127,7 +127,8 @@ struct snp_context {
     bool reserved = false;
     // device workspace
     Buf views, rec, trect, counts, offsets, scan_tmp, keys, vals, keys_alt, vals_alt, hist, hist_scan, ranges,
-        px_state, px_nwalk, stats, small, g_view, g_h0, qkeys, qvals, qkeys_alt, qvals_alt, qhist, qhist_scan, npack;
+        px_state, px_nwalk, stats, small, g_view, g_h0, qkeys, qvals, qkeys_alt, qvals_alt, qhist, qhist_scan, npack,
+        cmask;
     // loss reduction: kLossSlots FP64 block sums, then the completion counter
     Buf loss_part;
     // pinned host staging
@@ -302,6 +303,7 @@ static void fill_args(RasterArgs &a, const snp_context *ctx, const snp_scene_des
     for (int k = 0; k < 3; ++k) a.bg[k] = ctx->cfg.bg[k];
     a.chunk = ctx->chunk;
     a.npack = (float *)ctx->npack.p;
+    a.cmask = (uint32_t *)ctx->cmask.p;
     a.npack_stride = raster_npack_stride(d->color_mode, d->n_c, d->n_sigma);
 }
 
@@ -346,7 +348,7 @@ void snp_destroy(snp_context *ctx)
                    &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
                    &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0,
                    &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan,
-                   &ctx->npack, &ctx->loss_part};
+                   &ctx->npack, &ctx->cmask, &ctx->loss_part};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_views) cudaFreeHost(ctx->h_views);
@@ -358,9 +360,10 @@ void snp_destroy(snp_context *ctx)
 
 const char *snp_last_error(const snp_context *ctx) { return ctx ? ctx->err : "null context"; }
 
-static snp_status ensure_keys(snp_context *ctx, int64_t K)
+static snp_status ensure_keys(snp_context *ctx, int64_t K, int ts)
 {
     ENS(keys, (size_t)K * 8);
+    ENS(cmask, (size_t)K * (ts * ts / 32) * 4);
     ENS(keys_alt, (size_t)K * 8);
     ENS(vals, (size_t)K * 4);
     ENS(vals_alt, (size_t)K * 4);
@@ -421,7 +424,7 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
     if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) return s;
     if (max_keys <= 0) max_keys = 4 * desc->n * n_cams + 1024;
     if ((s = ensure_frame(ctx, desc->n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
-    if ((s = ensure_keys(ctx, max_keys)) != SNP_OK) return s;
+    if ((s = ensure_keys(ctx, max_keys, ts)) != SNP_OK) return s;
     if ((s = ensure_scan_tmp(ctx, desc->n * n_cams, max_keys, tiles)) != SNP_OK) return s;
     // the view table of the reserved cameras stays on the device for captured forwards
     CK(cudaMemcpy(ctx->views.p, ctx->h_views, sizeof(View) * n_cams, cudaMemcpyHostToDevice));
@@ -487,6 +490,8 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     } else if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) {
         return s;
     }
+    if (ctx->reserved && ts != ctx->res_ts)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "the context is reserved for tile size %d, not %d", ctx->res_ts, ts);
     const int64_t n = desc->n, vn = n * n_cams;
     if ((s = ensure_frame(ctx, n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
     ctx->token++;  // invalidates the previous forward's state from here on
@@ -531,7 +536,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         CK(cudaMemcpyAsync(ctx->h_small, d_total, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         key_bound = ctx->h_small[0];
-        if ((s = ensure_keys(ctx, key_bound)) != SNP_OK) return s;
+        if ((s = ensure_keys(ctx, key_bound, ts)) != SNP_OK) return s;
         if ((s = ensure_scan_tmp(ctx, vn, key_bound, tiles)) != SNP_OK) return s;
         ctx->K = key_bound;
     } else {

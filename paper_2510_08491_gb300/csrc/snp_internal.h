@@ -63,6 +63,10 @@ struct RasterArgs {
     // persistent scheduling
     int *work_counter;        // next queue item (zeroed before each launch)
     const uint32_t *queue;    // tile ids ordered by decreasing list length (NULL: 0..n_tiles-1)
+    // composited pixels of every (tile, list entry) pair, one bit per pixel slot of the
+    // tile: [K][tile pixels / 32] words indexed by the sorted key position (written by
+    // the forward, read by the backward)
+    uint32_t *cmask;
     // per-primitive network blocks in the staged shared-memory layout (k_pack_net)
     float *npack;             // [n][npack_stride]
     int32_t npack_stride;     // floats per primitive

@@ -440,26 +440,33 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             stage_chunk(sm, s_gid, cnt, vn, a, es);
             __syncthreads();
 
-            // P1: hits among the entries this pixel walked in the forward
+            // P1: the pixels that composited each entry, from the forward's masks (entries
+            // at or past the tile's walk length were composited by no pixel)
+            uint32_t cm[PPT];  // per pixel: entries of this chunk it composited
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) cm[k] = 0u;
             for (int e = 0; e < cnt; ++e) {
                 const uint32_t pos = c0 - rg.x + e;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    const bool hit = pos < nwalk[k] && hit_test(sm + e * es, ck, ry[k]);
-                    s_ah[e * NPIX + k * NT + tid] = 0.0f;
-                    list_append(hit, (uint16_t)(k * NT + tid), &s_nh[e], s_hl + e * NPIX);
+                    const int slot = k * NT + tid;
+                    const unsigned word = pos < maxwalk ? a.cmask[(int64_t)(c0 + e) * (NPIX / 32) + (slot >> 5)] : 0u;
+                    const bool act = (word >> lane) & 1u;
+                    cm[k] |= (uint32_t)act << e;
+                    s_w[e * NPIX + slot] = -1.0f;
+                    list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
                 }
             }
             __syncthreads();
-            if (tid < 32) warp_prefix64(s_nh, cnt, s_ph);
+            if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
             __syncthreads();
-            // P2: alpha_hat of every hit
+            // P2: alpha_hat of every composited pair
             {
-                const int nh = s_ph[cnt];
+                const int na = s_pa[cnt];
                 int e = 0;
-                for (int q = tid; q < nh; q += NT) {
-                    while (q >= s_ph[e + 1]) ++e;
-                    const int pix = s_hl[e * NPIX + (q - s_ph[e])];
+                for (int q = tid; q < na; q += NT) {
+                    while (q >= s_pa[e + 1]) ++e;
+                    const int pix = s_al[e * NPIX + (q - s_pa[e])];
                     const float *R = sm + e * es;
                     const PixRay r = load_ray(s_ray, pix);
                     Hit h;
@@ -469,30 +476,22 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            // P3: replay of the compositing weights
+            // P3: replay of the compositing weights over each pixel's composited entries
             float tau_c[PPT];  // optical depth at the chunk start, for P5
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) tau_c[k] = tau[k];
-            for (int e = 0; e < cnt; ++e) {
-                const uint32_t pos = c0 - rg.x + e;
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const int slot = k * NT + tid;
+            for (int k = 0; k < PPT; ++k) {
+                tau_c[k] = tau[k];
+                const int slot = k * NT + tid;
+                for (uint32_t m = cm[k]; m != 0u; m &= m - 1u) {
+                    const int e = __ffs(m) - 1;
                     const float ah = s_ah[e * NPIX + slot];
-                    const bool act = pos < nwalk[k] && ah > 0.0f;
-                    if (act) {
-                        const float Ti = __expf(-tau[k]);
-                        s_w[e * NPIX + slot] = Ti * (1.0f - __expf(-ah));
-                        tau[k] += ah;
-                    } else {
-                        s_w[e * NPIX + slot] = -1.0f;
-                    }
-                    list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
+                    const float Ti = __expf(-tau[k]);
+                    s_w[e * NPIX + slot] = Ti * (1.0f - __expf(-ah));
+                    tau[k] += ah;
                 }
             }
             __syncthreads();
             if (tid < 32) {
-                warp_prefix64(s_na, cnt, s_pa);
                 warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
                 warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
             }

@@ -15,8 +15,8 @@
 //                   one list entry (tensor cores for the hidden layer);
 //   P5 (per pixel)  C += w * colour in list order.
 // The result is the sequential front-to-back composite.  The per-pixel composited
-// colour, optical depth and number of list entries walked are saved for the
-// backward pass.
+// colour, optical depth, number of list entries walked and, per (tile, entry), the
+// mask of pixels that composited it are saved for the backward pass.
 #pragma once
 
 #include "snp_raster.cuh"
@@ -165,6 +165,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_ra
                             if (T[k] < a.t_min) alive[k] = false;
                         }
                     }
+                    // composited-pixel mask of this (tile, entry), one word per warp
+                    const unsigned word = __ballot_sync(0xffffffffu, act);
+                    if (lane_id() == 0 && a.cmask)
+                        a.cmask[(int64_t)(c0 + e) * (NPIX / 32) + (slot >> 5)] = word;
                     if constexpr (NC > 0) {
                         s_w[e * NPIX + slot] = act ? w : -1.0f;
                         list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
