@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     float *sm = s_dl + 3 * NPIX;                           // [CH][es] staged entries
     float *acc = sm + CH * es;                             // [CH][vg] per-entry gradient sums
     float *s_ah = acc + CH * vg;                           // [CH][NPIX] alpha_hat, then dL/dalpha_hat
-    float *s_w = s_ah + CH * NPIX;                         // [CH][NPIX] weights (-1: not composited)
+    float *s_w = s_ah + CH * NPIX;                         // [CH][NPIX] weights of the composited pairs
     float *s_col = s_w + CH * NPIX;                        // [3][CH][NPIX] colours
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + 3 * CH * NPIX);  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
@@ -453,14 +453,18 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     const unsigned word = pos < maxwalk ? a.cmask[(int64_t)(c0 + e) * (NPIX / 32) + (slot >> 5)] : 0u;
                     const bool act = (word >> lane) & 1u;
                     cm[k] |= (uint32_t)act << e;
-                    s_w[e * NPIX + slot] = -1.0f;
                     list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
                 }
             }
             __syncthreads();
-            if (tid < 32) warp_prefix64(s_na, cnt, s_pa);
+            if (tid < 32) {
+                warp_prefix64(s_na, cnt, s_pa);
+                warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
+                warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
+            }
             __syncthreads();
-            // P2: alpha_hat of every composited pair
+            // P2: alpha_hat of every composited pair (per thread), then P4: their colours
+            // (per warp, 16 pairs of one entry); independent, so one phase
             {
                 const int na = s_pa[cnt];
                 int e = 0;
@@ -473,42 +477,14 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     float ah = 0.0f;
                     if (intersect(R, ck, r, h)) ah = integral<FORM>(R, R + kRecFloats, ns, ck, r, h);
                     s_ah[e * NPIX + pix] = ah;
+                    if constexpr (NC == 0) {
+                        s_col[(0 * CH + e) * NPIX + pix] = R[kRecRgb + 0];
+                        s_col[(1 * CH + e) * NPIX + pix] = R[kRecRgb + 1];
+                        s_col[(2 * CH + e) * NPIX + pix] = R[kRecRgb + 2];
+                    }
                 }
             }
-            __syncthreads();
-            // P3: replay of the compositing weights over each pixel's composited entries
-            float tau_c[PPT];  // optical depth at the chunk start, for P5
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                tau_c[k] = tau[k];
-                const int slot = k * NT + tid;
-                for (uint32_t m = cm[k]; m != 0u; m &= m - 1u) {
-                    const int e = __ffs(m) - 1;
-                    const float ah = s_ah[e * NPIX + slot];
-                    const float Ti = __expf(-tau[k]);
-                    s_w[e * NPIX + slot] = Ti * (1.0f - __expf(-ah));
-                    tau[k] += ah;
-                }
-            }
-            __syncthreads();
-            if (tid < 32) {
-                warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
-                warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
-            }
-            __syncthreads();
-            // P4: colour of every composited pair
-            if constexpr (NC == 0) {
-                const int na = s_pa[cnt];
-                int e = 0;
-                for (int q = tid; q < na; q += NT) {
-                    while (q >= s_pa[e + 1]) ++e;
-                    const int pix = s_al[e * NPIX + (q - s_pa[e])];
-                    const float *R = sm + e * es;
-                    s_col[(0 * CH + e) * NPIX + pix] = R[kRecRgb + 0];
-                    s_col[(1 * CH + e) * NPIX + pix] = R[kRecRgb + 1];
-                    s_col[(2 * CH + e) * NPIX + pix] = R[kRecRgb + 2];
-                }
-            } else {
+            if constexpr (NC > 0) {
                 const int np = s_pp[cnt];
                 int e = 0;
                 for (int q = wid; q < np; q += NT / 32) {
@@ -518,25 +494,27 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            // P5: dL/dalpha_hat = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg
-            for (int e = 0; e < cnt; ++e) {
+            // P3/P5 (per pixel, over its composited entries in list order): the weights
+            // w_i = T_i (1 - e^{-alpha_hat_i}) and
+            // dL/dalpha_hat_i = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const int slot = k * NT + tid;
-                    const float w = s_w[e * NPIX + slot];
-                    if (w >= 0.0f) {
-                        const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + slot],
-                                                       s_col[(1 * CH + e) * NPIX + slot],
-                                                       s_col[(2 * CH + e) * NPIX + slot]);
-                        tau_c[k] += s_ah[e * NPIX + slot];
-                        const float Tn = __expf(-tau_c[k]);
-                        pref[k].x = fmaf(w, col.x, pref[k].x);
-                        pref[k].y = fmaf(w, col.y, pref[k].y);
-                        pref[k].z = fmaf(w, col.z, pref[k].z);
-                        s_ah[e * NPIX + slot] = dL[k].x * (Tn * col.x - (Cf[k].x - pref[k].x)) +
-                                                dL[k].y * (Tn * col.y - (Cf[k].y - pref[k].y)) +
-                                                dL[k].z * (Tn * col.z - (Cf[k].z - pref[k].z)) - bgdot[k];
-                    }
+            for (int k = 0; k < PPT; ++k) {
+                const int slot = k * NT + tid;
+                for (uint32_t m = cm[k]; m != 0u; m &= m - 1u) {
+                    const int e = __ffs(m) - 1;
+                    const float ah = s_ah[e * NPIX + slot];
+                    const float w = __expf(-tau[k]) * (1.0f - __expf(-ah));
+                    tau[k] += ah;
+                    const float Tn = __expf(-tau[k]);
+                    s_w[e * NPIX + slot] = w;
+                    const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + slot], s_col[(1 * CH + e) * NPIX + slot],
+                                                   s_col[(2 * CH + e) * NPIX + slot]);
+                    pref[k].x = fmaf(w, col.x, pref[k].x);
+                    pref[k].y = fmaf(w, col.y, pref[k].y);
+                    pref[k].z = fmaf(w, col.z, pref[k].z);
+                    s_ah[e * NPIX + slot] = dL[k].x * (Tn * col.x - (Cf[k].x - pref[k].x)) +
+                                            dL[k].y * (Tn * col.y - (Cf[k].y - pref[k].y)) +
+                                            dL[k].z * (Tn * col.z - (Cf[k].z - pref[k].z)) - bgdot[k];
                 }
             }
             __syncthreads();
