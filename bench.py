@@ -327,7 +327,8 @@ def run_ours(args, rank, world):
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = tr.get(kern, {}).get("bytes_per_launch")
+        if tr.get("workload") == args.workload:
+            traffic = tr.get(kern, {}).get("bytes_per_launch")
     except Exception:
         pass
 
