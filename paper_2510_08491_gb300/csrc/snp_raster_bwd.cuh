@@ -20,6 +20,10 @@
 
 namespace snp {
 
+// Shared words for the composited masks of one backward chunk (chunk x tile
+// pixels / 32; the backward chunk is at most 8 entries).
+constexpr int kMaskWords = 512;
+
 // Per-entry gradient accumulator layout (floats).
 __host__ __device__ constexpr int ga_geo(int ns) { return round4(5 * ns + 1); }
 __host__ __device__ constexpr int ga_bc3(int ns) { return ga_geo(ns) + kGvFloats; }
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + 3 * CH * NPIX);  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
     __shared__ uint32_t s_gid[kMaxChunk];
+    __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
     __shared__ uint32_t s_maxwalk;
@@ -436,6 +441,11 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 s_nh[tid] = 0;
                 s_na[tid] = 0;
             }
+            // composited masks of the chunk's entries (none past the tile's walk length)
+            for (int i = tid; i < cnt * (NPIX / 32); i += NT) {
+                const int e = i / (NPIX / 32);
+                s_cmw[i] = c0 - rg.x + e < maxwalk ? a.cmask[(int64_t)c0 * (NPIX / 32) + i] : 0u;
+            }
             __syncthreads();
             stage_chunk(sm, s_gid, cnt, vn, a, es);
             __syncthreads();
@@ -446,11 +456,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
 #pragma unroll
             for (int k = 0; k < PPT; ++k) cm[k] = 0u;
             for (int e = 0; e < cnt; ++e) {
-                const uint32_t pos = c0 - rg.x + e;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     const int slot = k * NT + tid;
-                    const unsigned word = pos < maxwalk ? a.cmask[(int64_t)(c0 + e) * (NPIX / 32) + (slot >> 5)] : 0u;
+                    const unsigned word = s_cmw[e * (NPIX / 32) + (slot >> 5)];
                     const bool act = (word >> lane) & 1u;
                     cm[k] |= (uint32_t)act << e;
                     list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
