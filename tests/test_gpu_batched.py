@@ -135,3 +135,20 @@ def test_autotune_picks_a_working_configuration(R, tmp_path):
     img = R.forward(ps, cams, best).cpu().numpy()
     ref = R.forward(ps, cams, L.make_config()).cpu().numpy()
     assert np.array_equal(img, ref)
+
+
+def test_reserved_context_rejects_another_tile_size(R):
+    """A reservation fixes the tile size (the composited masks and key capacity are
+    sized for it): a forward with another tile size is refused, not overrun."""
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import Renderer, pack_scene
+    sc = synth.make_scene(500, seed=81, center_half=1.5, n_sigma=8)
+    cams = synth.ring_cameras(1, 6.0, 96, 64)
+    r = Renderer(0)
+    ps = pack_scene(sc)
+    r.reserve(ps, cams, L.make_config(tile_size=16))
+    with pytest.raises(L.SnpError) as ei:
+        r.forward(ps, cams, L.make_config(tile_size=32))
+    assert ei.value.status == L.SNP_ERR_INVALID_ARG
+    img = r.forward(ps, cams, L.make_config(tile_size=16))
+    assert torch.isfinite(img).all()
