@@ -52,6 +52,26 @@ def flops(counts, per_unit):
                   counts["comp"] * per_unit["comp"])
 
 
+# ----------------------------------------------------------------------------- multi-rank
+def max_over_ranks(x: float) -> float:
+    """The maximum of x over all ranks of the default process group (x itself when
+    torch.distributed is not initialised).  NCCL reduces a CUDA tensor, gloo a CPU one."""
+    import torch
+    import torch.distributed as D
+    if not (D.is_available() and D.is_initialized()) or D.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if D.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    D.all_reduce(t, op=D.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput of N independent replicas (weak scaling): the units all
+    ranks processed, over the slowest rank's time, in millions per second."""
+    return world * units_per_rank / (ms_max * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
@@ -250,11 +270,8 @@ def run_ours(args, rank, world):
     else:
         launches = (L.kernel_launches() - l0) // max(args.steps, 1)
         st = r.ctx.stage_times(reset=True)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        D.all_reduce(t, op=D.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * P / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms)
+    value = replica_throughput(P, ms, world)
 
     # forward only (same workload), for the "vs plain FP32 forward" comparison
     for _ in range(2):
