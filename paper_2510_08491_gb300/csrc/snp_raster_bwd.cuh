@@ -37,12 +37,12 @@ __host__ __device__ constexpr int grad_stride(int ns, int nc)
 
 // Vector atomic add of the four values at acc[s[0..3]] (zeroed afterwards) to the
 // 16-byte aligned dst[0..3]; a source index < 0 contributes 0 (destination padding).
-__device__ __forceinline__ void flush4(float *acc, const int (&s)[4], float *dst)
+__device__ __forceinline__ void flush4(float *acc, const int (&s)[4], float *dst, float scale = 1.0f)
 {
     float v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        v[i] = s[i] >= 0 ? acc[s[i]] : 0.0f;
+        v[i] = s[i] >= 0 ? scale * acc[s[i]] : 0.0f;
         if (s[i] >= 0) acc[s[i]] = 0.0f;
     }
     if (v[0] != 0.0f || v[1] != 0.0f || v[2] != 0.0f || v[3] != 0.0f)
@@ -86,6 +86,8 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
             }
             int sidx[4];
             float *dst;
+            // W1 and b1 sums are gradients w.r.t. the staged rows w0 W1, w0 b1
+            const float scale = g < e1 ? a.omega0 : 1.0f;
             if (g < e0) {
                 const int q = 4 * g;
                 for (int i = 0; i < 4; ++i) sidx[i] = q + i < 3 * ns ? q + i : -1;
@@ -99,7 +101,7 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
                 for (int i = 0; i < 4; ++i) sidx[i] = q + i < ns ? 4 * ns + q + i : -1;
                 dst = gn + a.off_w2 + q;
             }
-            flush4(acc, sidx, dst);
+            flush4(acc, sidx, dst, scale);
         } else if (g < e3) {
             if (gn) flush1(acc, 5 * ns, gn + a.off_b2);
             else acc[5 * ns] = 0.0f;
@@ -156,7 +158,7 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
 // lanes without a pair pass contrib = false (their contributions are zero).
 // g_c: dL/dcolour, used for a constant colour only.
 template <int NC, int FORM>
-__device__ __forceinline__ void pair_backward(const float *R, const float *D, int ns, float w0, const CamK &ck,
+__device__ __forceinline__ void pair_backward(const float *R, const float *D, int ns, const CamK &ck,
                                               const PixRay &ry, bool contrib, float g_ah, float3 g_c, float *A)
 {
     const unsigned lane = lane_id();
@@ -214,18 +216,19 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, in
                     float sp, cp, st, ct;
                     __sincosf(ph, &sp, &cp);
                     __sincosf(th, &st, &ct);
-                    const float t2 = th * th;
-                    const float sc = fabsf(th) < 0.05f ? fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f)
-                                                       : __fdividef(st, th);
-                    const float scp = sincf_deriv(th, st, ct);
+                    // sinc(th) and its derivative, series below |th| < 0.05, else one reciprocal
+                    const float t2 = th * th, rt = __fdividef(1.0f, th);
+                    const bool small = fabsf(th) < 0.05f;
+                    const float sc = small ? fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f) : st * rt;
+                    const float scp = small ? th * fmaf(t2, 1.0f / 30.0f, -1.0f / 3.0f) : fmaf(th, ct, -st) * rt * rt;
                     S = fmaf(wk * cp, sc, S);
                     const float gphi = -gS * wk * sp * sc;
                     const float gth = gS * wk * cp * scp;
                     gw2 = gS * cp * sc;
-                    gw[0] = w0 * fmaf(gphi, u.x, gth * hm * ry.g.x);
-                    gw[1] = w0 * fmaf(gphi, u.y, gth * hm * ry.g.y);
-                    gw[2] = w0 * fmaf(gphi, u.z, gth * hm * ry.g.z);
-                    gb1 = w0 * gphi;
+                    gw[0] = fmaf(gphi, u.x, gth * hm * ry.g.x);
+                    gw[1] = fmaf(gphi, u.y, gth * hm * ry.g.y);
+                    gw[2] = fmaf(gphi, u.z, gth * hm * ry.g.z);
+                    gb1 = gphi;
                     g_u.x = fmaf(gphi, w.x, g_u.x);
                     g_u.y = fmaf(gphi, w.y, g_u.y);
                     g_u.z = fmaf(gphi, w.z, g_u.z);
@@ -240,10 +243,10 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, in
                     gw2 = gscale * (s1 - s0) * ia;
                     const float gpsi = gscale * wk * (c1 - c0v) * ia;
                     const float ga = gscale * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
-                    gw[0] = w0 * fmaf(gpsi, ocm.x, ga * inv_m * ry.g.x);
-                    gw[1] = w0 * fmaf(gpsi, ocm.y, ga * inv_m * ry.g.y);
-                    gw[2] = w0 * fmaf(gpsi, ocm.z, ga * inv_m * ry.g.z);
-                    gb1 = w0 * gpsi;
+                    gw[0] = fmaf(gpsi, ocm.x, ga * inv_m * ry.g.x);
+                    gw[1] = fmaf(gpsi, ocm.y, ga * inv_m * ry.g.y);
+                    gw[2] = fmaf(gpsi, ocm.z, ga * inv_m * ry.g.z);
+                    gb1 = gpsi;
                     g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
                     g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
                     g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
@@ -377,7 +380,6 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const int tid = threadIdx.x;
     const unsigned lane = lane_id();
     const int wid = tid >> 5;
-    const float w0 = a.omega0;
     for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
 
     for (;;) {
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                             const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
                             g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
                         }
-                        pair_backward<NC, FORM>(R, R + kRecFloats, ns, w0, ck, r, valid, s_ah[e * NPIX + pix], g_c,
+                        pair_backward<NC, FORM>(R, R + kRecFloats, ns, ck, r, valid, s_ah[e * NPIX + pix], g_c,
                                                 acc + e * vg);
                     } else if constexpr (NC > 0) {
                         const int q = it - nb;
