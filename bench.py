@@ -188,7 +188,7 @@ def run_ours(args, rank, world):
     P = sum(c.n_pixels for c in cams)
     batched = args.workload in BATCHED
     use_graph = args.graph or batched
-    cfg = L.make_config(t_min=wl.t_min, timing=not use_graph)
+    cfg = L.make_config(tile_size=args.tile, t_min=wl.t_min, timing=not use_graph)
     if args.autotune or batched:
         cfg = r.autotune(ps, cams, cfg, backward=True)
         cfg.flags = L.FLAG_STAGE_TIMING if not use_graph else 0
@@ -423,6 +423,7 @@ def main():
                     help="also time the oracle sample on a workload other than the default one")
     ap.add_argument("--graph", action="store_true", help="time replays of a captured CUDA graph of the step")
     ap.add_argument("--autotune", action="store_true", help="pick tile size and chunk with snp_autotune first")
+    ap.add_argument("--tile", type=int, default=16, choices=(8, 16, 32), help="tile size (without --autotune)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -507,20 +507,20 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 // Backward of the colour MLP for the composited pairs at positions r0 .. r0+15 of
 // an entry's list.  Per pair: dL/dc = w dL (w: compositing weight at w_e[slot],
 // dL: dl[c * npix + slot]) and dL/da3 = dL/dc c (1 - c) (c at col_e[c * plane +
-// slot]).  Accumulates, with shared-memory atomics:
-//   AC1 [NC][4]   dL/d(Wc1_d, h0);
+// slot]).  Accumulates, with shared-memory atomics, in the network record layout:
+//   WC1 [NC][11]  dL/dWc1 for the direction columns 0..2;   H0 [NC] dL/dh0;
 //   AW2 [NC * NC] dL/dWc2 in mma fragment order (element i of lane l of output
 //                 tile (mn, nk), i.e. row 16 mn + l/4 + 8 (i >> 1), column
 //                 8 nk + 2 (l % 4) + (i & 1), at ((mn NC/8 + nk) 4 + i) 32 + l);
-//   AW3 [NC][4]   dL/d(Wc3, bc2);  AB3 [3] dL/dbc3.
+//   W3 [3][NC]    dL/dWc3;  BC2 [NC] dL/dbc2;  AB3 [3] dL/dbc3.
 // a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays dL/da2 z1^T run on
 // the tensor cores; the last takes movmatrix transposes of the pass's register
 // fragments, with the 16 rays as the reduction dimension.
 template <int NC, bool BF16>
 __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float4 *s_ray, const uint16_t *list,
                                                     int r0, int n, const float *w_e, const float *dl, int npix,
-                                                    const float *col_e, int plane, float *AC1, float *AW2,
-                                                    float *AW3, float *AB3)
+                                                    const float *col_e, int plane, float *WC1, float *H0,
+                                                    float *AW2, float *W3, float *BC2, float *AB3)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
@@ -584,7 +584,8 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
 #pragma unroll
         for (int i = 0; i < NC / 8; ++i) {
             const int idx = g * (NC / 8) + i;
-            if (pw[i] != 0.0f) atomicAdd(AW3 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pw[i]);
+            const int n = acc_unit(idx >> 2, t), c = idx & 3;
+            if (pw[i] != 0.0f) atomicAdd(c < 3 ? W3 + c * NC + n : BC2 + n, pw[i]);
         }
     }
     uint32_t gh[NC / 16][4], gl[NC / 16][4];
@@ -613,7 +614,8 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
 #pragma unroll
         for (int i = 0; i < NC / 8; ++i) {
             const int idx = g * (NC / 8) + i;
-            if (pc[i] != 0.0f) atomicAdd(AC1 + 4 * acc_unit(idx >> 2, t) + (idx & 3), pc[i]);
+            const int j = acc_unit(idx >> 2, t), c = idx & 3;
+            if (pc[i] != 0.0f) atomicAdd(c < 3 ? WC1 + j * (3 + kFeat) + c : H0 + j, pc[i]);
         }
     }
     // dL/dWc2 += GA^T Z over the pass rows: A = transposed dL/da2 blocks,

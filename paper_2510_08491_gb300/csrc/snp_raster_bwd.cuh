@@ -13,7 +13,7 @@
 // ellipsoid geometry down to the projection record.  Per-pair gradients are
 // reduced across each warp by a 32-value reduce-scatter, accumulated per list
 // entry in shared memory across the warps, and added to the caller's gradient
-// arrays with one global atomic per parameter per (tile, primitive).
+// arrays with bulk asynchronous reductions, one per block per (tile, primitive).
 #pragma once
 
 #include "snp_raster.cuh"
@@ -24,132 +24,95 @@ namespace snp {
 // pixels / 32; the backward chunk is at most 8 entries).
 constexpr int kMaskWords = 512;
 
-// Per-entry gradient accumulator layout (floats).
-__host__ __device__ constexpr int ga_geo(int ns) { return round4(5 * ns + 1); }
-__host__ __device__ constexpr int ga_bc3(int ns) { return ga_geo(ns) + kGvFloats; }
-__host__ __device__ constexpr int ga_col(int ns) { return ga_bc3(ns) + 4; }
-// colour: C1G [nc][4] (Wc1[j][0..2], h0_j), W2G [nc * nc] in mma fragment order (see
-// warp_color_bwd), W3G [nc][4] (Wc3[0..2][j], bc2_j)
-__host__ __device__ constexpr int grad_stride(int ns, int nc)
+// Elements of one primitive's network record (snp_net_layout): every field
+// 8-element aligned and padded.
+__host__ __device__ constexpr int round8i(int x) { return (x + 7) & ~7; }
+__host__ __device__ constexpr int net_stride(int ns, int nc)
 {
-    return nc == 0 ? ga_col(ns) : ga_col(ns) + 4 * nc + nc * nc + 4 * nc;
+    return round8i(3 * ns) + 2 * round8i(ns) + 8 +
+           (nc == 0 ? 0 : 8 + round8i(11 * nc) + round8i(nc) + round8i(nc * nc) + round8i(nc) + round8i(3 * nc) + 8);
 }
 
-// Vector atomic add of the four values at acc[s[0..3]] (zeroed afterwards) to the
-// 16-byte aligned dst[0..3]; a source index < 0 contributes 0 (destination padding).
-__device__ __forceinline__ void flush4(float *acc, const int (&s)[4], float *dst, float scale = 1.0f)
+// Per-entry gradient accumulator (floats):
+//   [0, stride)             the primitive's network-gradient record in the caller's
+//                           layout (snp_net_layout).  W1 and b1 hold gradients w.r.t.
+//                           the staged rows w0 W1, w0 b1, and Wc2 is in mma fragment
+//                           order (see warp_color_bwd_pass), until the flush;
+//   [stride, +kGvFloats)    the per-(view, primitive) geometry gradient record;
+//   [.., +n_c)              dL/dh0 (the folded first-layer bias).
+// The flush adds the three blocks to global memory with bulk asynchronous
+// reductions (cp.reduce.async.bulk ... add.f32), one per block.
+__host__ __device__ constexpr int acc_stride(int ns, int nc) { return net_stride(ns, nc) + kGvFloats + nc; }
+
+__device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, uint32_t bytes)
 {
-    float v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        v[i] = s[i] >= 0 ? scale * acc[s[i]] : 0.0f;
-        if (s[i] >= 0) acc[s[i]] = 0.0f;
-    }
-    if (v[0] != 0.0f || v[1] != 0.0f || v[2] != 0.0f || v[3] != 0.0f)
-        atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;\n" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes)
+                 : "memory");
 }
 
-__device__ __forceinline__ void flush1(float *acc, int s, float *dst)
-{
-    const float v = acc[s];
-    acc[s] = 0.0f;
-    if (v != 0.0f) atomicAdd(dst, v);
-}
-
-// Add one entry's gradient sums to the caller's arrays and clear them.  Groups
-// of four consecutive destination elements go out as one 16-byte vector atomic
-// (every network field is 8-element aligned and padded, so a group that runs
-// past a field's end only adds zeros to its padding).
-template <int NC>
-__device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int64_t prim, int64_t vprim, int tid,
-                                            int nt)
+// Flush the chunk's cnt entry accumulators: permute the Wc2 blocks to row-major
+// and scale W1 / b1 by w0 in place, reduce every block into the caller's arrays
+// with bulk asynchronous adds (issued by thread 0), wait until they have read
+// shared memory, then clear the accumulators.  All threads call it.
+template <int NC, int NT>
+__device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int vg, const uint32_t *s_gid, int cnt,
+                                            int64_t vn, int tid, int nt)
 {
     const int ns = a.n_sigma;
-    float *gn = a.g_net ? a.g_net + prim * a.stride : nullptr;
-    const int gW1 = (3 * ns + 3) / 4, gB1 = (ns + 3) / 4;
-    const int e0 = gW1, e1 = e0 + gB1, e2 = e1 + gB1;  // W1 | b1 | w2 groups end
-    const int e3 = e2 + 1;                              // b2
-    const int e4 = e3 + kGvFloats / 4;                  // per-(view, primitive) record
-    const int e5 = e4 + 3;                              // bc3
-    int total = e5;
-    constexpr int NG8 = NC / 8;
-    const int e6 = e5 + 3 * NC, e7 = e6 + NC / 4, e8 = e7 + NC * NC / 4, e9 = e8 + 3 * NC / 4, e10 = e9 + NC / 4;
-    if constexpr (NC > 0) total = e10;
-    for (int g = tid; g < total; g += nt) {
-        if (g < e2) {
-            if (!gn) {
-                const int base = g < e0 ? 4 * g : (g < e1 ? 3 * ns + 4 * (g - e0) : 4 * ns + 4 * (g - e1));
-                const int lim = g < e0 ? 3 * ns : (g < e1 ? 4 * ns : 5 * ns);
-                for (int i = 0; i < 4; ++i)
-                    if (base + i < lim) acc[base + i] = 0.0f;
-                continue;
-            }
-            int sidx[4];
-            float *dst;
-            // W1 and b1 sums are gradients w.r.t. the staged rows w0 W1, w0 b1
-            const float scale = g < e1 ? a.omega0 : 1.0f;
-            if (g < e0) {
-                const int q = 4 * g;
-                for (int i = 0; i < 4; ++i) sidx[i] = q + i < 3 * ns ? q + i : -1;
-                dst = gn + a.off_W1 + q;
-            } else if (g < e1) {
-                const int q = 4 * (g - e0);
-                for (int i = 0; i < 4; ++i) sidx[i] = q + i < ns ? 3 * ns + q + i : -1;
-                dst = gn + a.off_b1 + q;
-            } else {
-                const int q = 4 * (g - e1);
-                for (int i = 0; i < 4; ++i) sidx[i] = q + i < ns ? 4 * ns + q + i : -1;
-                dst = gn + a.off_w2 + q;
-            }
-            flush4(acc, sidx, dst, scale);
-        } else if (g < e3) {
-            if (gn) flush1(acc, 5 * ns, gn + a.off_b2);
-            else acc[5 * ns] = 0.0f;
-        } else if (g < e4) {
-            const int q = 4 * (g - e3);
-            const int sidx[4] = {ga_geo(ns) + q, ga_geo(ns) + q + 1, ga_geo(ns) + q + 2, ga_geo(ns) + q + 3};
-            flush4(acc, sidx, a.g_view + vprim * kGvFloats + q);
-        } else if (g < e5) {
-            const int r = g - e4;
-            if (gn) flush1(acc, ga_bc3(ns) + r, gn + a.off_bc3 + r);
-            else acc[ga_bc3(ns) + r] = 0.0f;
-        } else if constexpr (NC > 0) {
-            const int C1 = ga_col(ns), W2 = C1 + 4 * NC, W3 = W2 + NC * NC;
-            if (g < e6) {
-                // Wc1 direction columns: 3 scalars per unit (rows of Wc1 are 11 wide)
-                const int j = (g - e5) / 3, r = (g - e5) - 3 * j;
-                if (gn) flush1(acc, C1 + 4 * j + r, gn + a.off_Wc1 + j * (3 + kFeat) + r);
-                else acc[C1 + 4 * j + r] = 0.0f;
-            } else if (g < e7) {
-                const int j = 4 * (g - e6);
-                const int sidx[4] = {C1 + 4 * j + 3, C1 + 4 * j + 7, C1 + 4 * j + 11, C1 + 4 * j + 15};
-                flush4(acc, sidx, a.g_h0 + prim * NC + j);
-            } else if (g < e8) {
-                // Wc2 row n, columns k0..k0+3, from the mma fragment-order accumulator
-                const int q = g - e7, n = q / (NC / 4), k0 = 4 * (q - n * (NC / 4));
-                const int mn = n >> 4, gg = n & 7, hi = (n >> 3) & 1, nk = k0 >> 3, t0 = (k0 & 7) >> 1;
-                const int tile = (mn * NG8 + nk) * 128;
-                const int sidx[4] = {W2 + tile + (2 * hi) * 32 + 4 * gg + t0, W2 + tile + (2 * hi + 1) * 32 + 4 * gg + t0,
-                                     W2 + tile + (2 * hi) * 32 + 4 * gg + t0 + 1,
-                                     W2 + tile + (2 * hi + 1) * 32 + 4 * gg + t0 + 1};
-                if (gn) flush4(acc, sidx, gn + a.off_Wc2 + n * NC + k0);
-                else
-                    for (int i = 0; i < 4; ++i) acc[sidx[i]] = 0.0f;
-            } else if (g < e9) {
-                const int q = g - e8, r = q / (NC / 4), j = 4 * (q - r * (NC / 4));
-                const int sidx[4] = {W3 + 4 * j + r, W3 + 4 * j + 4 + r, W3 + 4 * j + 8 + r, W3 + 4 * j + 12 + r};
-                if (gn) flush4(acc, sidx, gn + a.off_Wc3 + r * NC + j);
-                else
-                    for (int i = 0; i < 4; ++i) acc[sidx[i]] = 0.0f;
-            } else {
-                const int j = 4 * (g - e9);
-                const int sidx[4] = {W3 + 4 * j + 3, W3 + 4 * j + 7, W3 + 4 * j + 11, W3 + 4 * j + 15};
-                if (gn) flush4(acc, sidx, gn + a.off_bc2 + j);
-                else
-                    for (int i = 0; i < 4; ++i) acc[sidx[i]] = 0.0f;
+    if constexpr (NC > 0) {
+        // The fragment-order tiles (mn, nk) of row block mn hold exactly the rows
+        // 16 mn .. 16 mn + 15 of Wc2, and in both layouts that block occupies the
+        // same 16 NC words: permute block by block, in rounds of BR blocks held in
+        // registers (PB words per thread and block).
+        constexpr int NG8 = NC / 8, PB = 16 * NC / NT, BR = (16 / PB < 1 ? 1 : (16 / PB > NC / 16 ? NC / 16 : 16 / PB));
+        static_assert(PB * NT == 16 * NC, "a row block must split evenly over the threads");
+        for (int e = 0; e < cnt; ++e) {
+            float *W = acc + e * vg + a.off_Wc2;
+            for (int b0 = 0; b0 < NC / 16; b0 += BR) {
+                float v[BR][PB];
+#pragma unroll
+                for (int b = 0; b < BR; ++b)
+#pragma unroll
+                    for (int j = 0; j < PB; ++j) v[b][j] = W[(b0 + b) * 16 * NC + tid + j * NT];
+                __syncthreads();
+#pragma unroll
+                for (int b = 0; b < BR; ++b) {
+#pragma unroll
+                    for (int j = 0; j < PB; ++j) {
+                        // fragment order ((mn NC/8 + nk) 4 + i) 32 + l -> row n, column k
+                        const int q = (b0 + b) * 16 * NC + tid + j * NT;
+                        const int ln = q & 31, i = (q >> 5) & 3, tile = q >> 7;
+                        const int n = 16 * (tile / NG8) + (ln >> 2) + 8 * (i >> 1);
+                        const int k = 8 * (tile % NG8) + 2 * (ln & 3) + (i & 1);
+                        W[n * NC + k] = v[b][j];
+                    }
+                }
+                __syncthreads();
             }
         }
     }
+    for (int q = tid; q < cnt * (4 * ns); q += nt) {
+        const int e = q / (4 * ns), r = q - e * (4 * ns);
+        float *A = acc + e * vg;
+        if (r < 3 * ns) A[a.off_W1 + r] *= a.omega0;
+        else A[a.off_b1 + (r - 3 * ns)] *= a.omega0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        for (int e = 0; e < cnt; ++e) {
+            const int64_t gid = s_gid[e], prim = gid - vn;
+            const float *A = acc + e * vg;
+            if (a.g_net) bulk_reduce_add(a.g_net + prim * a.stride, A, (uint32_t)a.stride * 4u);
+            bulk_reduce_add(a.g_view + gid * kGvFloats, A + a.stride, kGvFloats * 4u);
+            if constexpr (NC > 0) bulk_reduce_add(a.g_h0 + prim * NC, A + a.stride + kGvFloats, NC * 4u);
+        }
+        asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    float4 *A4 = reinterpret_cast<float4 *>(acc);
+    for (int q = tid; q < cnt * vg / 4; q += nt) A4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Density and geometry gradient of one (pixel, primitive) pair, reduced across
@@ -158,7 +121,8 @@ __device__ __forceinline__ void flush_entry(const RasterArgs &a, float *acc, int
 // lanes without a pair pass contrib = false (their contributions are zero).
 // g_c: dL/dcolour, used for a constant colour only.
 template <int NC, int FORM>
-__device__ __forceinline__ void pair_backward(const float *R, const float *D, int ns, const CamK &ck,
+__device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *R, const float *D, int ns,
+                                              const CamK &ck,
                                               const PixRay &ry, bool contrib, float g_ah, float3 g_c, float *A)
 {
     const unsigned lane = lane_id();
@@ -266,7 +230,7 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, in
         const float r = warp_reduce_scatter32(vv);
         const int kk = lane / 5, c = lane - 5 * kk, k = k0 + kk;
         if (lane < 30 && k < ns && r != 0.0f) {
-            const int dst = c < 3 ? 3 * k + c : (c == 3 ? 3 * ns + k : 4 * ns + k);
+            const int dst = c < 3 ? a.off_W1 + 3 * k + c : (c == 3 ? a.off_b1 + k : a.off_w2 + k);
             atomicAdd(A + dst, r);
         }
     }
@@ -336,8 +300,8 @@ __device__ __forceinline__ void pair_backward(const float *R, const float *D, in
         for (int q = 25; q < 32; ++q) vv[q] = 0.0f;
         const float r = warp_reduce_scatter32(vv);
         if (r != 0.0f) {
-            if (lane < (unsigned)kGvFloats) atomicAdd(A + ga_geo(ns) + lane, r);
-            else if (lane == 24) atomicAdd(A + 5 * ns, r);
+            if (lane < (unsigned)kGvFloats) atomicAdd(A + a.stride + lane, r);
+            else if (lane == 24) atomicAdd(A + a.off_b2, r);
         }
     }
 
@@ -347,7 +311,7 @@ template <int TS>
 __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
-    const size_t per_entry = (size_t)(entry_stride(ns, nc) + grad_stride(ns, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2 * 2);
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(ns, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2 * 2);
     return NPIX * (32 + 12) + (size_t)chunk * per_entry;
 }
 
@@ -361,7 +325,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const int CH = a.chunk;
     const int ns = a.n_sigma;
     const int es = entry_stride(ns, NC);
-    const int vg = grad_stride(ns, NC);
+    const int vg = acc_stride(ns, NC);
     float4 *s_ray = smem4;                                 // [2 NPIX] pixel rays
     float *s_dl = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [3][NPIX] dL/dC of the tile's pixels
     float *sm = s_dl + 3 * NPIX;                           // [CH][es] staged entries
@@ -549,28 +513,27 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                             const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
                             g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
                         }
-                        pair_backward<NC, FORM>(R, R + kRecFloats, ns, ck, r, valid, s_ah[e * NPIX + pix], g_c,
+                        pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_ah[e * NPIX + pix], g_c,
                                                 acc + e * vg);
                     } else if constexpr (NC > 0) {
                         const int q = it - nb;
                         while (q >= s_pp[ec + 1]) ++ec;
                         float *A = acc + ec * vg;
-                        float *AC1 = A + ga_col(ns);
                         warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
                                                       s_al + ec * NPIX, (q - s_pp[ec]) * 16, s_na[ec],
-                                                      s_w + ec * NPIX, s_dl, NPIX, s_col + ec * NPIX, CH * NPIX, AC1,
-                                                      AC1 + 4 * NC, AC1 + 4 * NC + NC * NC, A + ga_bc3(ns));
+                                                      s_w + ec * NPIX, s_dl, NPIX, s_col + ec * NPIX, CH * NPIX,
+                                                      A + a.off_Wc1, A + a.stride + kGvFloats, A + a.off_Wc2,
+                                                      A + a.off_Wc3, A + a.off_bc2, A + a.off_bc3);
                     }
                 }
             }
             __syncthreads();
-            for (int e = 0; e < cnt; ++e) {
-                const int64_t gid = s_gid[e];
-                flush_entry<NC>(a, acc + e * vg, gid - vn, gid, tid, NT);
-            }
+            flush_chunk<NC, NT>(a, acc, vg, s_gid, cnt, vn, tid, NT);
         }
         __syncthreads();
     }
+    // the bulk reductions must complete before the CTA exits
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
 }  // namespace snp
