@@ -703,7 +703,7 @@ struct TileCfg {
     static constexpr int NPIX = TS * TS;
     static constexpr int NT = TS == 8 ? 64 : 256;
     static constexpr int PPT = NPIX / NT;
-    static constexpr int MIN_BLOCKS = TS == 8 ? 4 : 2;
+    static constexpr int MIN_BLOCKS = TS == 8 ? 4 : (TS == 16 ? 3 : 2);
 };
 
 // CTAs per SM the backward kernel is built for: two (128 registers, a staging
