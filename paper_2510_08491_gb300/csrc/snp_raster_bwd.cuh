@@ -1,10 +1,12 @@
-// snp_raster_bwd.cu -- backward per-tile rasterizer.
+// snp_raster_bwd.cuh -- backward per-tile rasterizer.
 //
-// Persistent CTAs take tiles from the same length-ordered queue as the forward.
-// Each pixel replays its list
-// front to back up to the number of entries the forward walked, recomputing
-// alpha_hat, alpha and the colour of every composited entry.  With the forward's
-// final colour C (no background) and optical depth tau_f:
+// Persistent CTAs take tiles as in the forward and walk each tile's list in
+// staged chunks.  Per chunk: the pixels that composited each entry come from the
+// forward's composited masks (P1); alpha_hat and the colour of every composited
+// pair are recomputed (P2 / P4); each pixel replays its weights and the gradient
+// of its colour with respect to alpha_hat in list order (P3 / P5); then the
+// per-pair gradients run as work items (P6).  With the forward's final colour C
+// (no background) and optical depth tau_f:
 //   C = sum_i c_i alpha_i T_i + T_f bg,  T_i = exp(-sum_{j<i} alpha_hat_j),
 //   dC/dc_i = alpha_i T_i,
 //   dC/dalpha_hat_i = T_{i+1} c_i - R_i - T_f bg,  R_i = sum_{j>i} c_j alpha_j T_j = C - prefix_i,

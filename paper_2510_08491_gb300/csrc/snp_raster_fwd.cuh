@@ -1,9 +1,10 @@
 // snp_raster_fwd.cuh -- forward per-tile rasterizer ("render kernel", App. A).
 //
-// Persistent CTAs take screen tiles from a queue ordered by decreasing list
-// length.  A tile's depth-sorted list is walked in chunks staged in shared
-// memory; each chunk runs in phases so that the expensive per-pair work is done
-// by fully occupied warps:
+// Persistent CTAs take screen tiles (of all views) from an atomic counter, in
+// tile order or, on request, by decreasing list length.  A tile's depth-sorted
+// list is walked in chunks staged in shared memory (cp.async copies of the
+// projection records and the packed network blocks); each chunk runs in phases
+// so that the expensive per-pair work is done by fully occupied warps:
 //   P1 (per pixel)  ray / ellipsoid test for every entry of the chunk; hits are
 //                   appended to per-entry pixel lists;
 //   P2 (per hit)    closed-form integral alpha_hat (Eq. 7/8);
