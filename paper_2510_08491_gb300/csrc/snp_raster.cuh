@@ -504,12 +504,10 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
     }
 }
 
-// Colour MLP, forward and backward, for the composited pairs at positions r0 ..
-// r0+15 of an entry's list.  The colour c of the pair at slot q is evaluated and
-// written to col_e[ch * plane + q] (for the compositing gradient), and with
-// dL/dc = w dL (w: compositing weight at w_e[q], dL: dl[ch * npix + q]) and
-// dL/da3 = dL/dc c (1 - c) the pass accumulates, with shared-memory atomics, in
-// the network record layout:
+// Backward of the colour MLP for the composited pairs at positions r0 .. r0+15 of
+// an entry's list.  Per pair: dL/dc = w dL (w: compositing weight at w_e[slot],
+// dL: dl[c * npix + slot]) and dL/da3 = dL/dc c (1 - c) (c at col_e[c * plane +
+// slot]).  Accumulates, with shared-memory atomics, in the network record layout:
 //   WC1 [NC][11]  dL/dWc1 for the direction columns 0..2;   H0 [NC] dL/dh0;
 //   AW2 [NC * NC] dL/dWc2 in mma fragment order (element i of lane l of output
 //                 tile (mn, nk), i.e. row 16 mn + l/4 + 8 (i >> 1), column
@@ -521,18 +519,34 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 template <int NC, bool BF16>
 __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float4 *s_ray, const uint16_t *list,
                                                     int r0, int n, const float *w_e, const float *dl, int npix,
-                                                    float *col_e, int plane, float *WC1, float *H0, float *AW2,
-                                                    float *W3, float *BC2, float *AB3)
+                                                    const float *col_e, int plane, float *WC1, float *H0,
+                                                    float *AW2, float *W3, float *BC2, float *AB3)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
     const float *B2 = Cb + cb_B2(NC);
     const float4 *C3 = reinterpret_cast<const float4 *>(Cb + cb_C3(NC));
-    const float4 B3 = *reinterpret_cast<const float4 *>(Cb + cb_B3(NC));
     const __nv_bfloat16 *Wh = reinterpret_cast<const __nv_bfloat16 *>(Cb + cb_W2(NC));
     __syncwarp();
     const PassRows pr = pass_rows(s_ray, list, r0, n);
     const float3 d0 = pr.d0, d1 = pr.d1;
+    auto ga3 = [&](bool v, int q) {
+        if (!v) return make_float3(0.f, 0.f, 0.f);
+        const float w = w_e[q];
+        const float cx = col_e[q], cy = col_e[plane + q], cz = col_e[2 * plane + q];
+        return make_float3(w * dl[q] * cx * (1.0f - cx), w * dl[npix + q] * cy * (1.0f - cy),
+                           w * dl[2 * npix + q] * cz * (1.0f - cz));
+    };
+    const float3 e0 = ga3(pr.v0, pr.pix0), e1 = ga3(pr.v1, pr.pix1);
+    // dL/dbc3 = sum of dL/da3 over the pass (one lane per row pair contributes)
+    {
+        float b[3] = {t == 0 ? e0.x + e1.x : 0.0f, t == 0 ? e0.y + e1.y : 0.0f, t == 0 ? e0.z + e1.z : 0.0f};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            b[k] = warp_sum(b[k]);
+            if (lane == k && b[k] != 0.0f) atomicAdd(AB3 + k, b[k]);
+        }
+    }
     float z[NC / 8][4];
     color_layer1<NC>(C1, d0, d1, z);
     uint32_t zh[NC / 16][4], zl[NC / 16][4];
@@ -545,57 +559,6 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
         acc[nt][1] = acc[nt][3] = b.y;
     }
     color_gemm_zw<NC, BF16>(zh, zl, Wh, acc);
-    // colours of the two rows: c = sigmoid(Wc3 z2 + bc3), summed over the four lanes of a row
-    float3 c0, c1;
-    {
-        float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int nt = 0; nt < NC / 8; ++nt) {
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float4 w = C3[acc_unit(2 * nt + j, t)];
-                const float za = fmaxf(acc[nt][j], 0.0f), zb = fmaxf(acc[nt][2 + j], 0.0f);
-                c[0] = fmaf(w.x, za, c[0]);
-                c[1] = fmaf(w.y, za, c[1]);
-                c[2] = fmaf(w.z, za, c[2]);
-                c[3] = fmaf(w.x, zb, c[3]);
-                c[4] = fmaf(w.y, zb, c[4]);
-                c[5] = fmaf(w.z, zb, c[5]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            c[q] += __shfl_xor_sync(0xffffffffu, c[q], 1);
-            c[q] += __shfl_xor_sync(0xffffffffu, c[q], 2);
-        }
-        c0 = make_float3(sigmoidf_fast(c[0] + B3.x), sigmoidf_fast(c[1] + B3.y), sigmoidf_fast(c[2] + B3.z));
-        c1 = make_float3(sigmoidf_fast(c[3] + B3.x), sigmoidf_fast(c[4] + B3.y), sigmoidf_fast(c[5] + B3.z));
-        const bool v = t == 0 ? pr.v0 : pr.v1;
-        if (t < 2 && v) {
-            const int q = t == 0 ? pr.pix0 : pr.pix1;
-            const float3 cc = t == 0 ? c0 : c1;
-            col_e[q] = cc.x;
-            col_e[plane + q] = cc.y;
-            col_e[2 * plane + q] = cc.z;
-        }
-    }
-    // dL/da3 = w dL c (1 - c) of the two rows
-    auto ga3 = [&](bool v, int q, float3 cc) {
-        if (!v) return make_float3(0.f, 0.f, 0.f);
-        const float w = w_e[q];
-        return make_float3(w * dl[q] * cc.x * (1.0f - cc.x), w * dl[npix + q] * cc.y * (1.0f - cc.y),
-                           w * dl[2 * npix + q] * cc.z * (1.0f - cc.z));
-    };
-    const float3 e0 = ga3(pr.v0, pr.pix0, c0), e1 = ga3(pr.v1, pr.pix1, c1);
-    // dL/dbc3 = sum of dL/da3 over the pass (one lane per row pair contributes)
-    {
-        float b[3] = {t == 0 ? e0.x + e1.x : 0.0f, t == 0 ? e0.y + e1.y : 0.0f, t == 0 ? e0.z + e1.z : 0.0f};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            b[k] = warp_sum(b[k]);
-            if (lane == k && b[k] != 0.0f) atomicAdd(AB3 + k, b[k]);
-        }
-    }
     // dL/dz2 = Wc3^T dL/da3, dL/da2 (ReLU), and the (Wc3, bc2) partials of the two rows
     {
         float pw[NC];

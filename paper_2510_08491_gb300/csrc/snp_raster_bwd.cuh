@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
             }
             __syncthreads();
-            // P2: alpha_hat of every composited pair (per thread)
+            // P2: alpha_hat of every composited pair (per thread), then P4: their colours
+            // (per warp, 16 pairs of one entry); independent, so one phase
             {
                 const int na = s_pa[cnt];
                 int e = 0;
@@ -460,48 +461,29 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     }
                 }
             }
-            __syncthreads();
-            // P3 (per pixel, over its composited entries in list order): the weights
-            // w_i = T_i (1 - e^{-alpha_hat_i})
-            float tau_c[PPT];  // optical depth at the chunk start, for P5
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                tau_c[k] = tau[k];
-                const int slot = k * NT + tid;
-                for (uint32_t m = cm[k]; m != 0u; m &= m - 1u) {
-                    const int e = __ffs(m) - 1;
-                    const float ah = s_ah[e * NPIX + slot];
-                    s_w[e * NPIX + slot] = __expf(-tau[k]) * (1.0f - __expf(-ah));
-                    tau[k] += ah;
-                }
-            }
             if constexpr (NC > 0) {
-                __syncthreads();
-                // P4: colour MLP forward and backward of the composited pairs, one warp per
-                // pass of 16 pairs of one entry (needs only the pairs' own weights); the
-                // colours go to s_col for P5
                 const int np = s_pp[cnt];
                 int e = 0;
                 for (int q = wid; q < np; q += NT / 32) {
                     while (q >= s_pp[e + 1]) ++e;
-                    float *A = acc + e * vg;
-                    warp_color_bwd_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
-                                                  (q - s_pp[e]) * 16, s_na[e], s_w + e * NPIX, s_dl, NPIX,
-                                                  s_col + e * NPIX, CH * NPIX, A + a.off_Wc1,
-                                                  A + a.stride + kGvFloats, A + a.off_Wc2, A + a.off_Wc3,
-                                                  A + a.off_bc2, A + a.off_bc3);
+                    warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
+                                              (q - s_pp[e]) * 16, s_na[e], s_col + e * NPIX, CH * NPIX);
                 }
             }
             __syncthreads();
-            // P5 (per pixel, in list order): dL/dalpha_hat_i = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg
+            // P3/P5 (per pixel, over its composited entries in list order): the weights
+            // w_i = T_i (1 - e^{-alpha_hat_i}) and
+            // dL/dalpha_hat_i = dL . (T_{i+1} c_i - (C - prefix_i)) - T_f dL . bg
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const int slot = k * NT + tid;
                 for (uint32_t m = cm[k]; m != 0u; m &= m - 1u) {
                     const int e = __ffs(m) - 1;
-                    const float w = s_w[e * NPIX + slot];
-                    tau_c[k] += s_ah[e * NPIX + slot];
-                    const float Tn = __expf(-tau_c[k]);
+                    const float ah = s_ah[e * NPIX + slot];
+                    const float w = __expf(-tau[k]) * (1.0f - __expf(-ah));
+                    tau[k] += ah;
+                    const float Tn = __expf(-tau[k]);
+                    s_w[e * NPIX + slot] = w;
                     const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + slot], s_col[(1 * CH + e) * NPIX + slot],
                                                    s_col[(2 * CH + e) * NPIX + slot]);
                     pref[k].x = fmaf(w, col.x, pref[k].x);
@@ -513,26 +495,38 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            // P6: per-pair density / geometry gradients in batches of 32 pairs of one
-            // entry (per-lane chain, warp reductions)
+            // P6: per-pair gradients.  Work items: density / geometry batches of 32 pairs
+            // of one entry (per-lane chain, warp reductions), then colour-MLP passes of
+            // 16 pairs of one entry (tensor cores); any warp takes any item.
             {
-                const int nb = s_pb[cnt];
-                int e = 0;
-                for (int it = wid; it < nb; it += NT / 32) {
-                    while (it >= s_pb[e + 1]) ++e;
-                    const int kk = (it - s_pb[e]) * 32 + (int)lane;
-                    const bool valid = kk < s_na[e];
-                    const int pix = valid ? s_al[e * NPIX + kk] : 0;
-                    const PixRay r = load_ray(s_ray, pix);
-                    const float *R = sm + e * es;
-                    float3 g_c = make_float3(0.f, 0.f, 0.f);
-                    if constexpr (NC == 0) {
-                        // dL/dc_i = w_i dL
-                        const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
-                        g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
+                const int nb = s_pb[cnt], np = NC > 0 ? s_pp[cnt] : 0;
+                int e = 0, ec = 0;
+                for (int it = wid; it < nb + np; it += NT / 32) {
+                    if (it < nb) {
+                        while (it >= s_pb[e + 1]) ++e;
+                        const int kk = (it - s_pb[e]) * 32 + (int)lane;
+                        const bool valid = kk < s_na[e];
+                        const int pix = valid ? s_al[e * NPIX + kk] : 0;
+                        const PixRay r = load_ray(s_ray, pix);
+                        const float *R = sm + e * es;
+                        float3 g_c = make_float3(0.f, 0.f, 0.f);
+                        if constexpr (NC == 0) {
+                            // dL/dc_i = w_i dL
+                            const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
+                            g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
+                        }
+                        pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_ah[e * NPIX + pix], g_c,
+                                                acc + e * vg);
+                    } else if constexpr (NC > 0) {
+                        const int q = it - nb;
+                        while (q >= s_pp[ec + 1]) ++ec;
+                        float *A = acc + ec * vg;
+                        warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
+                                                      s_al + ec * NPIX, (q - s_pp[ec]) * 16, s_na[ec],
+                                                      s_w + ec * NPIX, s_dl, NPIX, s_col + ec * NPIX, CH * NPIX,
+                                                      A + a.off_Wc1, A + a.stride + kGvFloats, A + a.off_Wc2,
+                                                      A + a.off_Wc3, A + a.off_bc2, A + a.off_bc3);
                     }
-                    pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_ah[e * NPIX + pix], g_c,
-                                            acc + e * vg);
                 }
             }
             __syncthreads();
