@@ -703,8 +703,16 @@ struct TileCfg {
     static constexpr int NPIX = TS * TS;
     static constexpr int NT = TS == 8 ? 64 : 256;
     static constexpr int PPT = NPIX / NT;
-    static constexpr int MIN_BLOCKS = TS == 8 ? 4 : (TS == 16 ? 3 : 2);
+    static constexpr int MIN_BLOCKS = TS == 8 ? 4 : 2;
 };
+
+// CTAs per SM the forward kernel is built for: three (80 registers, a staging
+// chunk in a third of the SM's shared memory) at 16-pixel tiles with a colour
+// network at most 32 wide, else TileCfg's.
+__host__ __device__ constexpr int fwd_min_blocks(int ts, int nc)
+{
+    return (ts == 16 && nc <= 32) ? 3 : (ts == 8 ? 4 : 2);
+}
 
 // CTAs per SM the backward kernel is built for: two (128 registers, a staging
 // chunk that fits two CTAs' shared memory) where the colour network is at most

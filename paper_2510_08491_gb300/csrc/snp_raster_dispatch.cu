@@ -28,7 +28,8 @@ size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
 // where it is built for two CTAs per SM, else most of one.
 int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts)
 {
-    const size_t fwd_budget = ts == 8 ? 52 * 1024 : (ts == 16 ? 70 * 1024 : 104 * 1024);
+    const int fmb = fwd_min_blocks(ts, nc_of(color_mode, n_c));
+    const size_t fwd_budget = fmb == 4 ? 52 * 1024 : (fmb == 3 ? 70 * 1024 : 104 * 1024);
     const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2 ? 110 * 1024 : 200 * 1024;
     int ch = backward ? 8 : 32;
     if (backward) {

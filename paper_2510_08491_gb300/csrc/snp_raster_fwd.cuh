@@ -34,7 +34,7 @@ __host__ __device__ inline size_t fwd_smem_bytes(int nc, int ns, int chunk)
 }
 
 template <int TS, int NC, int FORM, bool BF16>
-__global__ void __launch_bounds__(TileCfg<TS>::NT, TileCfg<TS>::MIN_BLOCKS) k_raster_fwd(RasterArgs a)
+__global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_raster_fwd(RasterArgs a)
 {
     constexpr int NT = TileCfg<TS>::NT;
     constexpr int NPIX = TileCfg<TS>::NPIX;
