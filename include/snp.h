@@ -44,7 +44,7 @@ typedef enum {
     SNP_ERR_UNSUPPORTED = 5  /* combination of modes not built */
 } snp_status;
 
-enum { SNP_COLOR_CONST = 0, SNP_COLOR_MLP = 1 };
+enum { SNP_COLOR_CONST = 0, SNP_COLOR_MLP = 1, SNP_COLOR_SH = 2 };
 enum { SNP_F32 = 0, SNP_BF16 = 1 };
 enum { SNP_FORM_STABLE = 0, SNP_FORM_NAIVE = 1 };
 
@@ -72,12 +72,18 @@ typedef struct {
  *   n            number of primitives (0 allowed: renders background)
  *   n_sigma      density network width N_sigma (1..64)
  *   omega0       boosting frequency w0 of Eq. 6
- *   color_mode   SNP_COLOR_CONST (rgb in the geometry array) or SNP_COLOR_MLP
+ *   color_mode   SNP_COLOR_CONST (rgb in the geometry array), SNP_COLOR_MLP
  *                (per-primitive colour MLP: z0 = [d, f] with d the unit ray
  *                direction of the pixel and f an 8-d feature; z1 = relu(Wc1 z0 + bc1),
  *                z2 = relu(Wc2 z1 + bc2), colour = sigmoid(Wc3 z2 + bc3); two hidden
- *                layers of width n_c, the neural colour field of App. D.2)
- *   n_c          colour MLP width: 32 or 64 (ignored for SNP_COLOR_CONST)
+ *                layers of width n_c, the neural colour field of App. D.2) or
+ *                SNP_COLOR_SH (the view-dependent colour of Sec. 3.1: four bands of
+ *                real spherical harmonics per channel, evaluated once per (view,
+ *                primitive) along the unit direction v from the camera centre to
+ *                the primitive centre: colour = max(0, 1/2 + sum_i Y_i(v) sh[i]);
+ *                Y_i the real harmonics of degree l = 0..3, index l^2 + l + m,
+ *                in the tesseral form 1/2 sqrt(1/pi); sqrt(3/(4pi)) (y, z, x); ...)
+ *   n_c          colour MLP width: 32 or 64 (ignored unless SNP_COLOR_MLP)
  *   weight_dtype SNP_F32 or SNP_BF16: element type of the `net` array.  All
  *                arithmetic is FP32 either way. */
 typedef struct {
@@ -95,11 +101,12 @@ typedef struct {
  * elements (16 bytes in BF16, 32 in FP32).  Fields, row-major:
  *   [0] W1 [n_sigma][3]  [1] b1 [n_sigma]  [2] w2 [n_sigma]  [3] b2 [1]
  *   [4] feat [8]  [5] Wc1 [n_c][11]  [6] bc1 [n_c]  [7] Wc2 [n_c][n_c]  [8] bc2 [n_c]
- *   [9] Wc3 [3][n_c]  [10] bc3 [3]   (colour fields only with SNP_COLOR_MLP; their
- *   offsets are -1 otherwise).  Padding elements are ignored on input and left
- *   untouched in gradients.  Pure function; never fails for valid sizes. */
+ *   [9] Wc3 [3][n_c]  [10] bc3 [3]   (colour fields only with SNP_COLOR_MLP)
+ *   [11] sh [16][3] (only with SNP_COLOR_SH); absent fields have offset -1.
+ *   Padding elements are ignored on input and left untouched in gradients.  Pure
+ *   function; never fails for valid sizes. */
 typedef struct {
-    int32_t off[11];
+    int32_t off[12];
     int32_t stride;
 } snp_net_layout;
 snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out);

@@ -10,13 +10,16 @@ with torch float64 ops so that autograd yields d(sum dL/dC . C)/d(params):
   * Eq. 9 alpha = 1 - exp(-max(0, alpha_hat));
   * Eq. 4 front-to-back compositing in the given candidate order, with the
     early-termination rule: after compositing entry i stop if T_{i+1} < t_min;
-  * colour: constant or the ReLU/sigmoid colour MLP on [ray direction, feature].
+  * colour: constant, the ReLU/sigmoid colour MLP on [ray direction, feature], or
+    four bands of real spherical harmonics along the camera-to-centre direction,
+    c = max(0, 1/2 + sum_i Y_i(v) sh_i).
 Candidate lists (which primitives a pixel walks, in which order) are inputs:
 they come from the C oracle's FP32 key specification and are not differentiated.
 Pinned by central finite differences of the independent C oracle forward.
 """
 from __future__ import annotations
 
+import math
 from typing import Dict, Optional
 
 import numpy as np
@@ -46,6 +49,30 @@ def pixel_rays(cam, pix: np.ndarray) -> torch.Tensor:
     r = x[:, None] * R[0][None] + y[:, None] * R[1][None] + R[2][None]
     r /= np.linalg.norm(r, axis=1, keepdims=True)
     return torch.tensor(r, dtype=F64)
+
+
+def sh_basis(v: torch.Tensor) -> torch.Tensor:
+    """Real spherical harmonics of degrees 0..3 (index l^2 + l + m, tesseral form)
+    at unit vectors v [..., 3]; returns [..., 16]."""
+    x, y, z = v[..., 0], v[..., 1], v[..., 2]
+    pi = math.pi
+    k1 = math.sqrt(3.0 / (4.0 * pi))
+    a2, b2, c2 = 0.5 * math.sqrt(15.0 / pi), 0.25 * math.sqrt(5.0 / pi), 0.25 * math.sqrt(15.0 / pi)
+    a3, b3 = 0.25 * math.sqrt(35.0 / (2.0 * pi)), 0.5 * math.sqrt(105.0 / pi)
+    c3, d3, e3 = 0.25 * math.sqrt(21.0 / (2.0 * pi)), 0.25 * math.sqrt(7.0 / pi), 0.25 * math.sqrt(105.0 / pi)
+    return torch.stack([
+        torch.full_like(x, 0.5 * math.sqrt(1.0 / pi)),
+        k1 * y, k1 * z, k1 * x,
+        a2 * x * y, a2 * y * z, b2 * (3 * z * z - 1), a2 * x * z, c2 * (x * x - y * y),
+        a3 * y * (3 * x * x - y * y), b3 * x * y * z, c3 * y * (5 * z * z - 1), d3 * z * (5 * z * z - 3),
+        c3 * x * (5 * z * z - 1), e3 * z * (x * x - y * y), a3 * x * (x * x - 3 * y * y)], dim=-1)
+
+
+def _sh_preact(params, pi: torch.Tensor, eye: torch.Tensor) -> torch.Tensor:
+    """1/2 + sum_i Y_i(v) sh_i per channel, v the unit camera-to-centre direction."""
+    v = params["centers"][pi] - eye[None]
+    v = v / torch.linalg.norm(v, dim=-1, keepdim=True)
+    return 0.5 + torch.einsum("qb,qbc->qc", sh_basis(v), params["sh"][pi])
 
 
 def _rotation(q: torch.Tensor) -> torch.Tensor:
@@ -115,6 +142,8 @@ def render(params: Dict[str, torch.Tensor], scene, cam, pix: np.ndarray, pix_lis
         z2 = torch.relu(torch.einsum("qjk,qk->qj", params["Wc2"][ps_], z1) + params["bc2"][ps_])
         c_sel = torch.sigmoid(torch.einsum("qjk,qk->qj", params["Wc3"][ps_], z2) + params["bc3"][ps_])
         col = torch.zeros(len(pi), 3, dtype=F64).index_put((sel,), c_sel)
+    elif scene.color == "sh":
+        col = torch.relu(_sh_preact(params, pi, eye))
     else:
         col = params["rgb"][pi]
 
@@ -181,6 +210,8 @@ def pair_diagnostics(scene, cam, pix, pix_list, list_off, list_prim):
         a1 = torch.einsum("qjk,qk->qj", params["Wc1"][pi], z0) + params["bc1"][pi]
         a2 = torch.einsum("qjk,qk->qj", params["Wc2"][pi], torch.relu(a1)) + params["bc2"][pi]
         amin = torch.minimum(a1.abs().min(-1).values, a2.abs().min(-1).values)
+    elif scene.color == "sh":
+        amin = _sh_preact(params, pi, eye).abs().min(-1).values
     return pair_prim, h2.numpy(), ah.numpy(), amin.numpy()
 
 

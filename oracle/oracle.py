@@ -51,7 +51,7 @@ class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_sigma", C.c_int32), ("color_mode", C.c_int32),
                 ("n_c", C.c_int32), ("pad_", C.c_int32), ("omega0", C.c_double)] + \
                [(f, C.c_void_p) for f in ("centers", "log_scales", "quats", "W1", "b1", "w2", "b2",
-                                          "rgb", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3")]
+                                          "rgb", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")]
 
 
 class _Camera(C.Structure):
@@ -79,7 +79,8 @@ def lib():
         L.ora_integral.argtypes = [P(_Scene), C.c_int64, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                                    C.c_int32]
         L.ora_integral.restype = C.c_double
-        L.ora_color.argtypes = [P(_Scene), C.c_int64, C.c_void_p, C.c_void_p]
+        L.ora_color.argtypes = [P(_Scene), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.ora_sh_basis.argtypes = [C.c_void_p, C.c_void_p]
         L.ora_pixel_ray.argtypes = [P(_Camera), C.c_int32, C.c_int32, C.c_void_p]
         _lib = L
     return _lib
@@ -98,12 +99,12 @@ class CScene:
         s = _Scene()
         s.n = scene.n
         s.n_sigma = scene.n_sigma
-        s.color_mode = 1 if scene.color == "mlp" else 0
+        s.color_mode = {"const": 0, "mlp": 1, "sh": 2}[scene.color]
         s.n_c = scene.n_c if scene.color == "mlp" else 0
         s.omega0 = float(scene.omega0)
         for f in ("centers", "log_scales", "quats", "W1", "b1", "w2", "b2", "rgb", "feat", "Wc1", "bc1",
-                  "Wc2", "bc2", "Wc3", "bc3"):
-            a = getattr(scene, f)
+                  "Wc2", "bc2", "Wc3", "bc3", "sh"):
+            a = getattr(scene, f, None)
             if a is not None:
                 a = np.ascontiguousarray(a, dtype=np.float64)
                 self.keep[f] = a
@@ -318,11 +319,21 @@ def integral(scene, i: int, o, d, t0: float, t1: float, form: int = FORM_STABLE,
     return float(lib().ora_integral(cs.ref(), int(i), _ptr(o), _ptr(d), float(t0), float(t1), int(form)))
 
 
-def color(scene, i: int, d, cs: Optional[CScene] = None) -> np.ndarray:
+def color(scene, i: int, d, cs: Optional[CScene] = None, eye=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Colour of primitive i seen from a camera at `eye` along the unit pixel ray d."""
     cs = cs or CScene(scene)
     d = np.ascontiguousarray(d, np.float64)
+    o = np.ascontiguousarray(eye, np.float64)
     out = np.zeros(3, np.float64)
-    lib().ora_color(cs.ref(), int(i), _ptr(d), _ptr(out))
+    lib().ora_color(cs.ref(), int(i), _ptr(o), _ptr(d), _ptr(out))
+    return out
+
+
+def sh_basis(v) -> np.ndarray:
+    """The 16 real spherical harmonics of degrees 0..3 at the unit vector v."""
+    v = np.ascontiguousarray(v, np.float64)
+    out = np.zeros(16, np.float64)
+    lib().ora_sh_basis(_ptr(v), _ptr(out))
     return out
 
 

@@ -20,6 +20,9 @@
  *   - Sec. 2.1, Eq. 4: front-to-back alpha blending over depth-sorted primitives.
  *   - App. D.2 (Eq. color_render): per-primitive colour MLP, here with input
  *     [view direction, 8-d feature], two hidden ReLU layers, sigmoid output.
+ *   - Sec. 3.1 / 3.3 (Primitives): view-dependent colour in four bands of real
+ *     spherical harmonics (48 coefficients), evaluated along the direction from
+ *     the camera to the primitive centre: c = max(0, 1/2 + sum_i Y_i(d) k_i).
  *
  * Readings where the paper is silent (camera model, depth key, near plane, early
  * termination, tile keys) follow the conventions documented in the design doc of this
@@ -38,6 +41,7 @@
 
 #define ORA_COLOR_CONST 0
 #define ORA_COLOR_MLP 1
+#define ORA_COLOR_SH 2
 #define ORA_FORM_STABLE 0
 #define ORA_FORM_NAIVE 1
 #define ORA_FEAT 8
@@ -55,6 +59,7 @@ typedef struct {
     const double *W1, *b1, *w2, *b2;            /* [n,Ns,3] [n,Ns] [n,Ns] [n] */
     const double *rgb;                          /* [n,3] */
     const double *feat, *Wc1, *bc1, *Wc2, *bc2, *Wc3, *bc3; /* [n,8] [n,Nc,11] [n,Nc] [n,Nc,Nc] [n,Nc] [n,3,Nc] [n,3] */
+    const double *sh;                           /* [n,16,3] spherical-harmonic coefficients */
 } ora_scene;
 
 /* Geometry for the FP32 key specification (the float32 inputs as given). */
@@ -338,13 +343,62 @@ static double integral_naive(const ora_scene *S, int64_t i, const prim64 *P, con
 
 static double relu(double x) { return x > 0.0 ? x : 0.0; }
 
-/* Colour of primitive i seen along unit direction d (App. D.2 colour field in the
- * ReLU/sigmoid form): z0 = [d, f], z1 = relu(Wc1 z0 + bc1), z2 = relu(Wc2 z1 + bc2),
- * c = sigmoid(Wc3 z2 + bc3).  Constant mode returns rgb. */
-static void color_eval(const ora_scene *S, int64_t i, const double d[3], double out[3])
+/* The 16 real spherical harmonics of degrees 0..3 at the unit vector v = (x, y, z),
+ * index l^2 + l + m, in the usual real (tesseral) form:
+ *   l = 0: 1/2 sqrt(1/pi)
+ *   l = 1: sqrt(3/(4 pi)) (y, z, x)
+ *   l = 2: 1/2 sqrt(15/pi) xy, 1/2 sqrt(15/pi) yz, 1/4 sqrt(5/pi) (3z^2 - 1),
+ *          1/2 sqrt(15/pi) xz, 1/4 sqrt(15/pi) (x^2 - y^2)
+ *   l = 3: 1/4 sqrt(35/(2 pi)) y (3x^2 - y^2), 1/2 sqrt(105/pi) xyz,
+ *          1/4 sqrt(21/(2 pi)) y (5z^2 - 1), 1/4 sqrt(7/pi) z (5z^2 - 3),
+ *          1/4 sqrt(21/(2 pi)) x (5z^2 - 1), 1/4 sqrt(105/pi) z (x^2 - y^2),
+ *          1/4 sqrt(35/(2 pi)) x (x^2 - 3y^2). */
+static void sh_basis(const double v[3], double Y[16])
+{
+    const double pi = acos(-1.0), x = v[0], y = v[1], z = v[2];
+    Y[0] = 0.5 * sqrt(1.0 / pi);
+    const double k1 = sqrt(3.0 / (4.0 * pi));
+    Y[1] = k1 * y;
+    Y[2] = k1 * z;
+    Y[3] = k1 * x;
+    Y[4] = 0.5 * sqrt(15.0 / pi) * x * y;
+    Y[5] = 0.5 * sqrt(15.0 / pi) * y * z;
+    Y[6] = 0.25 * sqrt(5.0 / pi) * (3.0 * z * z - 1.0);
+    Y[7] = 0.5 * sqrt(15.0 / pi) * x * z;
+    Y[8] = 0.25 * sqrt(15.0 / pi) * (x * x - y * y);
+    Y[9] = 0.25 * sqrt(35.0 / (2.0 * pi)) * y * (3.0 * x * x - y * y);
+    Y[10] = 0.5 * sqrt(105.0 / pi) * x * y * z;
+    Y[11] = 0.25 * sqrt(21.0 / (2.0 * pi)) * y * (5.0 * z * z - 1.0);
+    Y[12] = 0.25 * sqrt(7.0 / pi) * z * (5.0 * z * z - 3.0);
+    Y[13] = 0.25 * sqrt(21.0 / (2.0 * pi)) * x * (5.0 * z * z - 1.0);
+    Y[14] = 0.25 * sqrt(105.0 / pi) * z * (x * x - y * y);
+    Y[15] = 0.25 * sqrt(35.0 / (2.0 * pi)) * x * (x * x - 3.0 * y * y);
+}
+
+/* Colour of primitive i seen from a camera at o along the pixel's unit ray d.
+ * MLP (App. D.2 colour field in the ReLU/sigmoid form): z0 = [d, f],
+ * z1 = relu(Wc1 z0 + bc1), z2 = relu(Wc2 z1 + bc2), c = sigmoid(Wc3 z2 + bc3).
+ * Spherical harmonics: c = max(0, 1/2 + sum_i Y_i(v) sh_i) with v the unit
+ * direction from o to the primitive centre.  Constant mode returns rgb. */
+static void color_eval(const ora_scene *S, int64_t i, const double o[3], const double d[3], double out[3])
 {
     if (S->color_mode == ORA_COLOR_CONST) {
         for (int k = 0; k < 3; ++k) out[k] = S->rgb[3 * i + k];
+        return;
+    }
+    if (S->color_mode == ORA_COLOR_SH) {
+        const double *c = S->centers + 3 * i;
+        double v[3] = {c[0] - o[0], c[1] - o[1], c[2] - o[2]};
+        const double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int k = 0; k < 3; ++k) v[k] /= nv;
+        double Y[16];
+        sh_basis(v, Y);
+        const double *K = S->sh + (size_t)i * 48;
+        for (int ch = 0; ch < 3; ++ch) {
+            double a = 0.5;
+            for (int b = 0; b < 16; ++b) a += Y[b] * K[3 * b + ch];
+            out[ch] = relu(a);
+        }
         return;
     }
     int Nc = S->n_c, F = ORA_FEAT, fin = 3 + ORA_FEAT;
@@ -424,7 +478,7 @@ int64_t ora_render(const ora_scene *S, const ora_camera *cam, const int32_t *pix
             if (!(ah > 0.0)) continue;
             double alpha = -expm1(-ah);
             double col[3];
-            color_eval(S, i, d, col);
+            color_eval(S, i, o, d, col);
             for (int k = 0; k < 3; ++k) C[k] += T * alpha * col[k];
             tau += ah;
             T = exp(-tau);
@@ -468,6 +522,11 @@ double ora_integral(const ora_scene *S, int64_t i, const double *o, const double
     return integral_stable(S, i, &P, o, d, 0.5 * (t0 + t1), 0.5 * (t1 - t0));
 }
 
-void ora_color(const ora_scene *S, int64_t i, const double *d, double *out) { color_eval(S, i, d, out); }
+void ora_color(const ora_scene *S, int64_t i, const double *o, const double *d, double *out)
+{
+    color_eval(S, i, o, d, out);
+}
+
+void ora_sh_basis(const double *v, double *Y) { sh_basis(v, Y); }
 
 void ora_pixel_ray(const ora_camera *cam, int32_t px, int32_t py, double *d) { pixel_ray(cam, px, py, d); }

@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "snp.h")
 SNP_OK, SNP_ERR_INVALID_ARG, SNP_ERR_CUDA, SNP_ERR_CAPACITY, SNP_ERR_TIMEOUT, SNP_ERR_UNSUPPORTED = range(6)
 STATUS_NAMES = {0: "SNP_OK", 1: "SNP_ERR_INVALID_ARG", 2: "SNP_ERR_CUDA", 3: "SNP_ERR_CAPACITY",
                 4: "SNP_ERR_TIMEOUT", 5: "SNP_ERR_UNSUPPORTED"}
-COLOR_CONST, COLOR_MLP = 0, 1
+COLOR_CONST, COLOR_MLP, COLOR_SH = 0, 1, 2
 F32, BF16 = 0, 1
 FORM_STABLE, FORM_NAIVE = 0, 1
 FEAT_DIM = 8
@@ -42,7 +42,7 @@ class SceneDesc(C.Structure):
 
 
 class NetLayout(C.Structure):
-    _fields_ = [("off", C.c_int32 * 11), ("stride", C.c_int32)]
+    _fields_ = [("off", C.c_int32 * 12), ("stride", C.c_int32)]
 
 
 class ScenePtrs(C.Structure):

@@ -93,7 +93,7 @@ void layout_of(const snp_scene_desc &d, snp_net_layout &L)
 {
     int off = 0;
     const int ns = d.n_sigma;
-    for (int k = 0; k < 11; ++k) L.off[k] = -1;
+    for (int k = 0; k < 12; ++k) L.off[k] = -1;
     L.off[0] = off; off += round8(3 * ns);
     L.off[1] = off; off += round8(ns);
     L.off[2] = off; off += round8(ns);
@@ -107,6 +107,9 @@ void layout_of(const snp_scene_desc &d, snp_net_layout &L)
         L.off[8] = off; off += round8(nc);
         L.off[9] = off; off += round8(3 * nc);
         L.off[10] = off; off += 8;
+    }
+    if (d.color_mode == SNP_COLOR_SH) {
+        L.off[11] = off; off += 48;
     }
     L.stride = off;
 }
@@ -206,7 +209,7 @@ static snp_status check_desc(snp_context *ctx, const snp_scene_desc *d)
     if (!d) return fail(ctx, SNP_ERR_INVALID_ARG, "desc is NULL");
     if (d->n < 0 || d->n > (int64_t)1 << 28) return fail(ctx, SNP_ERR_INVALID_ARG, "n out of range: %lld", (long long)d->n);
     if (d->n_sigma < 1 || d->n_sigma > 64) return fail(ctx, SNP_ERR_INVALID_ARG, "n_sigma out of range: %d", d->n_sigma);
-    if (d->color_mode != SNP_COLOR_CONST && d->color_mode != SNP_COLOR_MLP)
+    if (d->color_mode != SNP_COLOR_CONST && d->color_mode != SNP_COLOR_MLP && d->color_mode != SNP_COLOR_SH)
         return fail(ctx, SNP_ERR_INVALID_ARG, "bad color_mode %d", d->color_mode);
     if (d->color_mode == SNP_COLOR_MLP && d->n_c != 32 && d->n_c != 64)
         return fail(ctx, SNP_ERR_UNSUPPORTED, "n_c must be 32 or 64, got %d", d->n_c);
@@ -296,7 +299,7 @@ static void fill_args(RasterArgs &a, const snp_context *ctx, const snp_scene_des
     a.n_tiles = ctx->n_tiles;
     a.off_W1 = L.off[0]; a.off_b1 = L.off[1]; a.off_w2 = L.off[2]; a.off_b2 = L.off[3];
     a.off_feat = L.off[4]; a.off_Wc1 = L.off[5]; a.off_bc1 = L.off[6]; a.off_Wc2 = L.off[7];
-    a.off_bc2 = L.off[8]; a.off_Wc3 = L.off[9]; a.off_bc3 = L.off[10];
+    a.off_bc2 = L.off[8]; a.off_Wc3 = L.off[9]; a.off_bc3 = L.off[10]; a.off_sh = L.off[11];
     a.stride = L.stride;
     a.omega0 = d->omega0;
     a.t_min = ctx->cfg.t_min;
@@ -526,6 +529,9 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         fill_args(pa, ctx, desc, scene, nullptr);
         if ((s = launch_pack_net(pa, desc->color_mode, desc->n_c, desc->weight_dtype == SNP_BF16, st)) != SNP_OK)
             return fail(ctx, s, "network pack launch failed");
+        if (desc->color_mode == SNP_COLOR_SH)
+            launch_sh_color((const float *)scene->geom, scene->net, desc->weight_dtype == SNP_BF16, n,
+                            (const View *)ctx->views.p, n_cams, pa.off_sh, pa.stride, (float *)ctx->rec.p, st);
     }
     STAGE_END();
     STAGE_BEGIN(SNP_STAGE_SCAN);
@@ -641,7 +647,11 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     STAGE_BEGIN(SNP_STAGE_POST_BWD);
     if (grads->geom)
         launch_project_bwd((const float *)scene->geom, n, (const View *)ctx->views.p, ctx->n_views,
-                           (const float *)ctx->g_view.p, grads->geom, st);
+                           (const float *)ctx->g_view.p, desc->color_mode == SNP_COLOR_CONST, grads->geom, st);
+    if (desc->color_mode == SNP_COLOR_SH && (grads->geom || grads->net))
+        launch_sh_bwd((const float *)scene->geom, scene->net, desc->weight_dtype == SNP_BF16, n,
+                      (const View *)ctx->views.p, ctx->n_views, a.off_sh, a.stride, (const float *)ctx->rec.p,
+                      (const float *)ctx->g_view.p, grads->net, grads->geom, st);
     if (grads->net && desc->color_mode == SNP_COLOR_MLP)
         launch_color_post(scene->net, desc->weight_dtype == SNP_BF16, n, desc->n_c, a.off_feat, a.off_Wc1,
                           a.off_bc1, a.stride, (const float *)ctx->g_h0.p, grads->net, st);

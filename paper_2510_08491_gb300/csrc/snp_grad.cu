@@ -16,7 +16,8 @@ namespace snp {
 
 __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ geom, int64_t n,
                                                      const View *__restrict__ views, int n_views,
-                                                     const float *__restrict__ g_view, float *__restrict__ g_geom)
+                                                     const float *__restrict__ g_view, int rgb_grad,
+                                                     float *__restrict__ g_geom)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -111,9 +112,11 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ g
     O[7] += (float)((gx - x * dot) * iq);
     O[8] += (float)((gy - y * dot) * iq);
     O[9] += (float)((gz - z * dot) * iq);
-    O[10] += (float)grgb[0];
-    O[11] += (float)grgb[1];
-    O[12] += (float)grgb[2];
+    if (rgb_grad) {
+        O[10] += (float)grgb[0];
+        O[11] += (float)grgb[1];
+        O[12] += (float)grgb[2];
+    }
 }
 
 template <bool BF16>
@@ -146,10 +149,10 @@ __global__ void __launch_bounds__(256) k_color_post(const void *__restrict__ net
 }
 
 void launch_project_bwd(const float *geom, int64_t n, const View *views, int n_views, const float *g_view,
-                        float *g_geom, cudaStream_t st)
+                        int rgb_grad, float *g_geom, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_project_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(geom, n, views, n_views, g_view, g_geom);
+    k_project_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(geom, n, views, n_views, g_view, rgb_grad, g_geom);
     note_launch();
 }
 

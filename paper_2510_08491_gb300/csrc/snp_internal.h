@@ -44,7 +44,7 @@ struct RasterArgs {
     int64_t n;
     int64_t n_tiles;
     const int32_t *lay;       // unused on device (layout passed by value below)
-    int32_t off_W1, off_b1, off_w2, off_b2, off_feat, off_Wc1, off_bc1, off_Wc2, off_bc2, off_Wc3, off_bc3;
+    int32_t off_W1, off_b1, off_w2, off_b2, off_feat, off_Wc1, off_bc1, off_Wc2, off_bc2, off_Wc3, off_bc3, off_sh;
     int32_t stride;
     float omega0;
     float t_min;
@@ -75,6 +75,13 @@ struct RasterArgs {
 // snp_raster_*.cu
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
+// snp_sh.cu
+void launch_sh_color(const float *geom, const void *net, int bf16, int64_t n, const View *views, int n_views,
+                     int off_sh, int stride, float *rec, cudaStream_t st);
+void launch_sh_bwd(const float *geom, const void *net, int bf16, int64_t n, const View *views, int n_views,
+                   int off_sh, int stride, const float *rec, const float *g_view, float *g_net, float *g_geom,
+                   cudaStream_t st);
+
 // snp_loss.cu
 constexpr int kLossSlots = 1024;
 snp_status launch_mse_loss(const float *img, const float *tgt, int64_t n, float *dL, float *loss, double *part,
@@ -97,7 +104,7 @@ void launch_tile_queue(const uint2 *ranges, int64_t n_tiles, uint64_t *qkeys, ui
 
 // snp_grad.cu
 void launch_project_bwd(const float *geom, int64_t n, const View *views, int n_views, const float *g_view,
-                        float *g_geom, cudaStream_t st);
+                        int rgb_grad, float *g_geom, cudaStream_t st);
 void launch_color_post(const void *net, int bf16, int64_t n, int n_c, int off_feat, int off_Wc1, int off_bc1,
                        int stride, const float *g_h0, float *g_net, cudaStream_t st);
 

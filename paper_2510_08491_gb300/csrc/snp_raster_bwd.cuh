@@ -29,10 +29,11 @@ constexpr int kMaskWords = 512;
 // Elements of one primitive's network record (snp_net_layout): every field
 // 8-element aligned and padded.
 __host__ __device__ constexpr int round8i(int x) { return (x + 7) & ~7; }
-__host__ __device__ constexpr int net_stride(int ns, int nc)
+__host__ __device__ constexpr int net_stride(int ns, int nc, bool sh)
 {
     return round8i(3 * ns) + 2 * round8i(ns) + 8 +
-           (nc == 0 ? 0 : 8 + round8i(11 * nc) + round8i(nc) + round8i(nc * nc) + round8i(nc) + round8i(3 * nc) + 8);
+           (nc == 0 ? 0 : 8 + round8i(11 * nc) + round8i(nc) + round8i(nc * nc) + round8i(nc) + round8i(3 * nc) + 8) +
+           (sh ? 48 : 0);
 }
 
 // Per-entry gradient accumulator (floats):
@@ -44,7 +45,7 @@ __host__ __device__ constexpr int net_stride(int ns, int nc)
 //   [.., +n_c)              dL/dh0 (the folded first-layer bias).
 // The flush adds the three blocks to global memory with bulk asynchronous
 // reductions (cp.reduce.async.bulk ... add.f32), one per block.
-__host__ __device__ constexpr int acc_stride(int ns, int nc) { return net_stride(ns, nc) + kGvFloats + nc; }
+__host__ __device__ constexpr int acc_stride(int stride, int nc) { return stride + kGvFloats + nc; }
 
 __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, uint32_t bytes)
 {
@@ -310,10 +311,10 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
 }
 
 template <int TS>
-__host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk)
+__host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk, int stride)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
-    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(ns, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2 * 2);
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(stride, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2 * 2);
     return NPIX * (32 + 12) + (size_t)chunk * per_entry;
 }
 
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const int CH = a.chunk;
     const int ns = a.n_sigma;
     const int es = entry_stride(ns, NC);
-    const int vg = acc_stride(ns, NC);
+    const int vg = acc_stride(a.stride, NC);
     float4 *s_ray = smem4;                                 // [2 NPIX] pixel rays
     float *s_dl = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [3][NPIX] dL/dC of the tile's pixels
     float *sm = s_dl + 3 * NPIX;                           // [CH][es] staged entries

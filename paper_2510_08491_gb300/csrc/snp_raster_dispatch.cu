@@ -18,9 +18,10 @@ size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
 size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
 {
     const int nc = nc_of(color_mode, n_c);
-    if (ts == 8) return bwd_smem_bytes<8>(nc, n_sigma, chunk);
-    if (ts == 32) return bwd_smem_bytes<32>(nc, n_sigma, chunk);
-    return bwd_smem_bytes<16>(nc, n_sigma, chunk);
+    const int stride = net_stride(n_sigma, nc, color_mode == SNP_COLOR_SH);
+    if (ts == 8) return bwd_smem_bytes<8>(nc, n_sigma, chunk, stride);
+    if (ts == 32) return bwd_smem_bytes<32>(nc, n_sigma, chunk, stride);
+    return bwd_smem_bytes<16>(nc, n_sigma, chunk, stride);
 }
 
 // Largest chunk (<= 32 forward, <= 8 backward) within the shared-memory budget:

@@ -16,7 +16,7 @@ import torch
 
 from . import _lib as L
 
-NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3")
+NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")
 
 
 @dataclass
@@ -41,7 +41,7 @@ def pack_scene(scene, device="cuda", weight_dtype: Optional[str] = None) -> Pack
     """Lay a synth.Scene out as the library's geometry [n, 16] and network [n, stride] arrays."""
     wd = weight_dtype or scene.weight_dtype
     mlp = scene.color == "mlp"
-    cm = L.COLOR_MLP if mlp else L.COLOR_CONST
+    cm = {"const": L.COLOR_CONST, "mlp": L.COLOR_MLP, "sh": L.COLOR_SH}[scene.color]
     offs, stride = L.net_layout(scene.n_sigma, cm, scene.n_c)
     n = scene.n
     geom = np.zeros((n, L.GEOM_STRIDE), np.float32)

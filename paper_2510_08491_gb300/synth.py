@@ -80,16 +80,19 @@ class Scene:
     bc2: Optional[np.ndarray] = None  # (n, Nc)
     Wc3: Optional[np.ndarray] = None  # (n, 3, Nc)
     bc3: Optional[np.ndarray] = None  # (n, 3)
+    sh: Optional[np.ndarray] = None  # (n, 16, 3) spherical-harmonic colour coefficients
     weight_dtype: str = "f32"
     extra: dict = field(default_factory=dict)
 
-    NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3")
+    NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")
     GEOM_FIELDS = ("centers", "log_scales", "quats", "rgb")
 
     def fields(self):
         names = list(self.GEOM_FIELDS) + ["W1", "b1", "w2", "b2"]
         if self.color == "mlp":
             names += ["feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"]
+        if self.color == "sh":
+            names += ["sh"]
         return names
 
     def subset(self, idx) -> "Scene":
@@ -181,6 +184,7 @@ def make_scene(n: int, seed: int = 0, *, center_half: float = 1.0, n_sigma: int 
     centres ~ U[-h, h]^3, log-scales ~ N(-2, 0.3) per axis, quaternions ~ N(0, I4),
     W1 ~ N(0, 1), b1 ~ U(-pi, pi), w2 ~ N(0, 0.5), b2 = 0.5, rgb ~ U(0, 1);
     colour MLP: feat ~ N(0, 1), Wc_l ~ N(0, 1/sqrt(fan_in)), biases 0.
+    spherical harmonics ("sh"): degree-0 coefficients ~ N(0, 0.6), degrees 1..3 ~ N(0, 0.2).
     thin_ratio_max: if set, axis 0 is the major axis ~ N(-2, 0.3) and the other two
     are major - ln r with r ~ logU[1, thin_ratio_max] (independently per axis).
     """
@@ -211,6 +215,10 @@ def make_scene(n: int, seed: int = 0, *, center_half: float = 1.0, n_sigma: int 
         sc.bc2 = np.zeros((n, n_c), dtype=f32)
         sc.Wc3 = g.normal(0.0, 1.0 / math.sqrt(n_c), size=(n, 3, n_c)).astype(f32)
         sc.bc3 = np.zeros((n, 3), dtype=f32)
+    if color == "sh":
+        sh = g.normal(0.0, 0.2, size=(n, 16, 3))
+        sh[:, 0, :] = g.normal(0.0, 0.6, size=(n, 3))
+        sc.sh = sh.astype(f32)
     return sc
 
 
@@ -310,8 +318,28 @@ def workload(name: str, seed: int = 0) -> Workload:
         g = np.random.Generator(np.random.PCG64(seed + 7))
         res = [RESOLUTIONS[i] for i in g.integers(0, 4, size=16)]
         return Workload(name, sc.to_bf16(), fibonacci_cameras(16, 10.0, res), 16)
+    if name == "fps100k_800px_sh":
+        # The speed protocol of App. A (Integration Cost): 100k random primitives in a
+        # volume, the primitive of Sec. 3.3 (Implementation Details: N_sigma = 8, w0 = 30,
+        # four SH bands) with its initialisation of the density weights,
+        # W1 ~ U(-1/3, 1/3) and w2 ~ U(-sqrt(6/N_sigma)/w0, +), seen by square 800 x 800
+        # views at a 39.6 degree field of view on a radius-4 ring (the camera set-up of
+        # the synthetic scenes).
+        sc = make_scene(100_000, seed, center_half=1.5, n_sigma=8, omega0=30.0, color="sh",
+                        log_scale_mean=-3.0)
+        g = np.random.Generator(np.random.PCG64(seed + 3))
+        sc.W1 = g.uniform(-1.0 / 3.0, 1.0 / 3.0, size=sc.W1.shape).astype(np.float32)
+        lim = math.sqrt(6.0 / sc.n_sigma) / sc.omega0
+        sc.w2 = g.uniform(-lim, lim, size=sc.w2.shape).astype(np.float32)
+        cams = []
+        for k in range(8):
+            t = 2.0 * math.pi * k / 8
+            eye = (4.0 * math.sin(t) * math.cos(math.radians(30.0)), 4.0 * math.sin(math.radians(30.0)),
+                   4.0 * math.cos(t) * math.cos(math.radians(30.0)))
+            cams.append(look_at_camera(eye, (0, 0, 0), 800, 800, fov_y_deg=39.6))
+        return Workload(name, sc, cams, 16)
     raise KeyError(name)
 
 
 WORKLOADS = ("tiny64_128px", "fwd100k_1080p_4view", "diff300k_720p", "thin50k_1080p",
-             "batch500k_16view")
+             "batch500k_16view", "fps100k_800px_sh")

@@ -24,10 +24,15 @@ def test_library_exports_every_header_symbol():
 def test_net_layout_is_aligned_and_complete():
     offs, stride = L.net_layout(16, L.COLOR_MLP, 32)
     sizes = [48, 16, 16, 1, 8, 32 * 11, 32, 32 * 32, 32, 96, 3]
+    assert offs[11] == -1
+    offs = offs[:11]
     assert all(o % 8 == 0 for o in offs) and stride % 8 == 0
     spans = sorted(zip(offs, sizes))
     for (o1, s1), (o2, _) in zip(spans, spans[1:]):
         assert o1 + s1 <= o2
     assert spans[-1][0] + spans[-1][1] <= stride
     offs_c, stride_c = L.net_layout(8, L.COLOR_CONST, 0)
-    assert offs_c[4:] == [-1] * 7 and stride_c == 24 + 8 + 8 + 8
+    assert offs_c[4:] == [-1] * 8 and stride_c == 24 + 8 + 8 + 8
+    # spherical harmonics: the density fields, then sh [16][3]
+    offs_s, stride_s = L.net_layout(8, L.COLOR_SH, 0)
+    assert offs_s[4:11] == [-1] * 7 and offs_s[11] == 48 and stride_s == 48 + 48

@@ -83,7 +83,7 @@ def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0), sil_eps=SIL_EPS, r
     for v, (cam, o) in enumerate(zip(cams, outs)):
         d = rng.normal(size=(cam.n_pixels, 3))
         d[o.flags != 0] = 0.0
-        if sil_eps > 0 or (relu_eps > 0 and scene.color == "mlp"):
+        if sil_eps > 0 or (relu_eps > 0 and scene.color in ("mlp", "sh")):
             pix = np.arange(cam.n_pixels, dtype=np.int32)
             gt = tl.view_tile_off[v] + O.pixel_tile(cam, 16, pix)
             lens = tl.tile_off[gt + 1] - tl.tile_off[gt]
@@ -91,7 +91,7 @@ def _dl(O, scene, cams, seed, t_min=1e-4, bg=(0.0, 0.0, 0.0), sil_eps=SIL_EPS, r
             _, h2, ah, amin = G.pair_diagnostics(scene, cam, pix, gt, tl.tile_off, lp)
             near = np.zeros(cam.n_pixels, bool)
             near[owner[np.abs(h2) < sil_eps]] = True
-            if scene.color == "mlp":
+            if scene.color in ("mlp", "sh"):
                 near[owner[(ah > 0) & (amin < relu_eps)]] = True
             d[near] = 0.0
         per_view.append(d)

@@ -63,7 +63,7 @@ def _loss(O, sc, cam, pix, gtile, off, lp, dL, cs=None):
     return float((out.rgb * dL).sum()), out.n_comp
 
 
-@pytest.mark.parametrize("color", ["const", "mlp"])
+@pytest.mark.parametrize("color", ["const", "mlp", "sh"])
 def test_torch_forward_equals_c_forward(oracle_lib, color):
     O = oracle_lib
     from oracle import grad as G
@@ -123,7 +123,7 @@ def _fd_group_directions(O, G, color, n_dirs, seed):
     return checked, skipped, worst
 
 
-@pytest.mark.parametrize("color", ["const", "mlp"])
+@pytest.mark.parametrize("color", ["const", "mlp", "sh"])
 def test_gradient_matches_fd_directional(oracle_lib, color):
     O = oracle_lib
     from oracle import grad as G
