@@ -60,12 +60,15 @@ enum { SNP_FORM_STABLE = 0, SNP_FORM_NAIVE = 1 };
  *          through its centre: d = normalize(R_wc^T ((px + .5 - cx)/fx, (py + .5 - cy)/fy, 1)).
  *   z_near a primitive is culled unless its whole bounding ellipsoid lies at
  *          camera depth > z_near (camera z of the centre minus max(s) > z_near).
- *   width, height  image size in pixels (1..32768). */
+ *   width, height  image size in pixels (1..32768).
+ *   time   timestamp xi_t in [0, 1] of this view; read only for dynamic scenes
+ *          (snp_scene_desc.dynamic), ignored otherwise. */
 typedef struct {
     float R_wc[9];
     float eye[3];
     float fx, fy, cx, cy, z_near;
     int32_t width, height;
+    float time;
 } snp_camera;
 
 /* Scene description (sizes and modes; no pointers).
@@ -85,7 +88,16 @@ typedef struct {
  *                in the tesseral form 1/2 sqrt(1/pi); sqrt(3/(4pi)) (y, z, x); ...)
  *   n_c          colour MLP width: 32 or 64 (ignored unless SNP_COLOR_MLP)
  *   weight_dtype SNP_F32 or SNP_BF16: element type of the `net` array.  All
- *                arithmetic is FP32 either way. */
+ *                arithmetic is FP32 either way.
+ *   dynamic      0: static scene.  1: time-conditioned density of the volumetric
+ *                dynamic scenes (App. Applications): every hidden unit's phase gains
+ *                xi_t W_t,k, i.e. sigma(x, xi_t) = w2 . cos(w0 (W1 u + b1) + xi_t W_t) + b2
+ *                with xi_t the view's camera time and W_t in R^{n_sigma} per primitive
+ *                (constant along a ray, so the closed-form integral keeps its form);
+ *                with SNP_COLOR_SH the degree-0 coefficient of each channel also
+ *                follows the time series sh[0] + sum_{i=1..4} a_i xi^i
+ *                + sum_{i=1..4} (b_i cos(i xi) + c_i sin(i xi)).  Built for
+ *                SNP_COLOR_CONST and SNP_COLOR_SH (SNP_ERR_UNSUPPORTED with the MLP). */
 typedef struct {
     int64_t n;
     int32_t n_sigma;
@@ -93,7 +105,7 @@ typedef struct {
     int32_t n_c;
     int32_t weight_dtype;
     float omega0;
-    int32_t reserved_;
+    int32_t dynamic;
 } snp_scene_desc;
 
 /* Per-primitive network layout of the `net` array: element offsets of each
@@ -102,11 +114,14 @@ typedef struct {
  *   [0] W1 [n_sigma][3]  [1] b1 [n_sigma]  [2] w2 [n_sigma]  [3] b2 [1]
  *   [4] feat [8]  [5] Wc1 [n_c][11]  [6] bc1 [n_c]  [7] Wc2 [n_c][n_c]  [8] bc2 [n_c]
  *   [9] Wc3 [3][n_c]  [10] bc3 [3]   (colour fields only with SNP_COLOR_MLP)
- *   [11] sh [16][3] (only with SNP_COLOR_SH); absent fields have offset -1.
- *   Padding elements are ignored on input and left untouched in gradients.  Pure
- *   function; never fails for valid sizes. */
+ *   [11] sh [16][3] (only with SNP_COLOR_SH)
+ *   [12] wt [n_sigma] (only when dynamic)
+ *   [13] sh_t [12][3]: a_1..a_4, b_1..b_4, c_1..c_4 per channel (only when dynamic
+ *        with SNP_COLOR_SH);
+ *   absent fields have offset -1.  Padding elements are ignored on input and left
+ *   untouched in gradients.  Pure function; never fails for valid sizes. */
 typedef struct {
-    int32_t off[12];
+    int32_t off[14];
     int32_t stride;
 } snp_net_layout;
 snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out);

@@ -12,7 +12,9 @@ with torch float64 ops so that autograd yields d(sum dL/dC . C)/d(params):
     early-termination rule: after compositing entry i stop if T_{i+1} < t_min;
   * colour: constant, the ReLU/sigmoid colour MLP on [ray direction, feature], or
     four bands of real spherical harmonics along the camera-to-centre direction,
-    c = max(0, 1/2 + sum_i Y_i(v) sh_i).
+    c = max(0, 1/2 + sum_i Y_i(v) sh_i);
+  * time-conditioned scenes (App. Applications): phase + xi_t W_t per hidden unit,
+    and the degree-0 SH coefficient sh_0 + sum_j a_j xi^j + b_j cos(j xi) + c_j sin(j xi).
 Candidate lists (which primitives a pixel walks, in which order) are inputs:
 they come from the C oracle's FP32 key specification and are not differentiated.
 Pinned by central finite differences of the independent C oracle forward.
@@ -68,11 +70,22 @@ def sh_basis(v: torch.Tensor) -> torch.Tensor:
         c3 * x * (5 * z * z - 1), e3 * z * (x * x - y * y), a3 * x * (x * x - 3 * y * y)], dim=-1)
 
 
-def _sh_preact(params, pi: torch.Tensor, eye: torch.Tensor) -> torch.Tensor:
-    """1/2 + sum_i Y_i(v) sh_i per channel, v the unit camera-to-centre direction."""
+def _time_series(xi: float) -> torch.Tensor:
+    """Basis of the degree-0 colour series at time xi: xi^1..4, cos(j xi), sin(j xi) for j = 1..4."""
+    j = np.arange(1, 5, dtype=np.float64)
+    return torch.tensor(np.concatenate([xi ** j, np.cos(j * xi), np.sin(j * xi)]), dtype=F64)
+
+
+def _sh_preact(params, pi: torch.Tensor, eye: torch.Tensor, xi: float = 0.0) -> torch.Tensor:
+    """1/2 + sum_i Y_i(v) sh_i per channel, v the unit camera-to-centre direction
+    (plus Y_0 times the degree-0 time series for a dynamic scene)."""
     v = params["centers"][pi] - eye[None]
     v = v / torch.linalg.norm(v, dim=-1, keepdim=True)
-    return 0.5 + torch.einsum("qb,qbc->qc", sh_basis(v), params["sh"][pi])
+    Y = sh_basis(v)
+    out = 0.5 + torch.einsum("qb,qbc->qc", Y, params["sh"][pi])
+    if "sh_t" in params:
+        out = out + Y[:, :1] * torch.einsum("j,qjc->qc", _time_series(xi), params["sh_t"][pi])
+    return out
 
 
 def _rotation(q: torch.Tensor) -> torch.Tensor:
@@ -123,8 +136,11 @@ def render(params: Dict[str, torch.Tensor], scene, cam, pix: np.ndarray, pix_lis
     m = s.max(dim=-1).values
     u = (oc + tm[:, None] * d) / m[:, None]
     w0 = float(scene.omega0)
+    xi = float(getattr(cam, "time", 0.0))
     W1 = params["W1"][pi]
     phi = w0 * (torch.einsum("qkj,qj->qk", W1, u) + params["b1"][pi])
+    if "wt" in params:
+        phi = phi + xi * params["wt"][pi]
     th = w0 * torch.einsum("qkj,qj->qk", W1, d) * (half / m)[:, None]
     small = th.abs() < 1e-4
     ths = torch.where(small, torch.ones_like(th), th)
@@ -143,7 +159,7 @@ def render(params: Dict[str, torch.Tensor], scene, cam, pix: np.ndarray, pix_lis
         c_sel = torch.sigmoid(torch.einsum("qjk,qk->qj", params["Wc3"][ps_], z2) + params["bc3"][ps_])
         col = torch.zeros(len(pi), 3, dtype=F64).index_put((sel,), c_sel)
     elif scene.color == "sh":
-        col = torch.relu(_sh_preact(params, pi, eye))
+        col = torch.relu(_sh_preact(params, pi, eye, xi))
     else:
         col = params["rgb"][pi]
 
@@ -197,7 +213,10 @@ def pair_diagnostics(scene, cam, pix, pix_list, list_off, list_prim):
     u = (oc + tm[:, None] * d) / m[:, None]
     W1 = params["W1"][pi]
     w0 = float(scene.omega0)
+    xi = float(getattr(cam, "time", 0.0))
     phi = w0 * (torch.einsum("qkj,qj->qk", W1, u) + params["b1"][pi])
+    if "wt" in params:
+        phi = phi + xi * params["wt"][pi]
     th = w0 * torch.einsum("qkj,qj->qk", W1, d) * (half / m)[:, None]
     small = th.abs() < 1e-4
     ths = torch.where(small, torch.ones_like(th), th)
@@ -211,7 +230,7 @@ def pair_diagnostics(scene, cam, pix, pix_list, list_off, list_prim):
         a2 = torch.einsum("qjk,qk->qj", params["Wc2"][pi], torch.relu(a1)) + params["bc2"][pi]
         amin = torch.minimum(a1.abs().min(-1).values, a2.abs().min(-1).values)
     elif scene.color == "sh":
-        amin = _sh_preact(params, pi, eye).abs().min(-1).values
+        amin = _sh_preact(params, pi, eye, xi).abs().min(-1).values
     return pair_prim, h2.numpy(), ah.numpy(), amin.numpy()
 
 

@@ -51,13 +51,14 @@ class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_sigma", C.c_int32), ("color_mode", C.c_int32),
                 ("n_c", C.c_int32), ("pad_", C.c_int32), ("omega0", C.c_double)] + \
                [(f, C.c_void_p) for f in ("centers", "log_scales", "quats", "W1", "b1", "w2", "b2",
-                                          "rgb", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")]
+                                          "rgb", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")] + \
+               [("time", C.c_double), ("wt", C.c_void_p), ("sh_t", C.c_void_p)]
 
 
 class _Camera(C.Structure):
     _fields_ = [("R_wc", C.c_float * 9), ("eye", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
                 ("cx", C.c_float), ("cy", C.c_float), ("z_near", C.c_float), ("width", C.c_int32),
-                ("height", C.c_int32)]
+                ("height", C.c_int32), ("time", C.c_float)]
 
 
 _lib = None
@@ -103,7 +104,7 @@ class CScene:
         s.n_c = scene.n_c if scene.color == "mlp" else 0
         s.omega0 = float(scene.omega0)
         for f in ("centers", "log_scales", "quats", "W1", "b1", "w2", "b2", "rgb", "feat", "Wc1", "bc1",
-                  "Wc2", "bc2", "Wc3", "bc3", "sh"):
+                  "Wc2", "bc2", "Wc3", "bc3", "sh", "wt", "sh_t"):
             a = getattr(scene, f, None)
             if a is not None:
                 a = np.ascontiguousarray(a, dtype=np.float64)
@@ -118,7 +119,10 @@ class CScene:
             setattr(g, f, a.ctypes.data)
         self.g = g
 
-    def ref(self):
+    def ref(self, time: float = 0.0):
+        """The C scene; `time` is the timestamp xi_t used by the single-pair calls
+        (pair, integral, color) of a dynamic scene (renders take the camera's)."""
+        self.s.time = float(time)
         return C.byref(self.s)
 
     def gref(self):
@@ -132,6 +136,7 @@ def c_camera(cam) -> _Camera:
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.z_near = float(cam.z_near)
     c.width, c.height = int(cam.width), int(cam.height)
+    c.time = float(getattr(cam, "time", 0.0))
     return c
 
 
@@ -302,30 +307,30 @@ def render_image(scene, cams, ts: int = 16, t_min: float = 1e-4, bg=(0.0, 0.0, 0
     return imgs, tl, outs
 
 
-def pair(scene, i: int, o, d, form: int = FORM_STABLE, cs: Optional[CScene] = None):
+def pair(scene, i: int, o, d, form: int = FORM_STABLE, cs: Optional[CScene] = None, time: float = 0.0):
     cs = cs or CScene(scene)
     o = np.ascontiguousarray(o, np.float64)
     d = np.ascontiguousarray(d, np.float64)
     out = np.zeros(4, np.float64)
-    lib().ora_pair(cs.ref(), int(i), _ptr(o), _ptr(d), int(form), _ptr(out))
+    lib().ora_pair(cs.ref(time), int(i), _ptr(o), _ptr(d), int(form), _ptr(out))
     return bool(out[0]), out[1], out[2], out[3]
 
 
 def integral(scene, i: int, o, d, t0: float, t1: float, form: int = FORM_STABLE,
-             cs: Optional[CScene] = None) -> float:
+             cs: Optional[CScene] = None, time: float = 0.0) -> float:
     cs = cs or CScene(scene)
     o = np.ascontiguousarray(o, np.float64)
     d = np.ascontiguousarray(d, np.float64)
-    return float(lib().ora_integral(cs.ref(), int(i), _ptr(o), _ptr(d), float(t0), float(t1), int(form)))
+    return float(lib().ora_integral(cs.ref(time), int(i), _ptr(o), _ptr(d), float(t0), float(t1), int(form)))
 
 
-def color(scene, i: int, d, cs: Optional[CScene] = None, eye=(0.0, 0.0, 0.0)) -> np.ndarray:
+def color(scene, i: int, d, cs: Optional[CScene] = None, eye=(0.0, 0.0, 0.0), time: float = 0.0) -> np.ndarray:
     """Colour of primitive i seen from a camera at `eye` along the unit pixel ray d."""
     cs = cs or CScene(scene)
     d = np.ascontiguousarray(d, np.float64)
     o = np.ascontiguousarray(eye, np.float64)
     out = np.zeros(3, np.float64)
-    lib().ora_color(cs.ref(), int(i), _ptr(o), _ptr(d), _ptr(out))
+    lib().ora_color(cs.ref(time), int(i), _ptr(o), _ptr(d), _ptr(out))
     return out
 
 

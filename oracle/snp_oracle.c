@@ -23,10 +23,13 @@
  *   - Sec. 3.1 / 3.3 (Primitives): view-dependent colour in four bands of real
  *     spherical harmonics (48 coefficients), evaluated along the direction from
  *     the camera to the primitive centre: c = max(0, 1/2 + sum_i Y_i(d) k_i).
+ *   - App. Applications (volumetric dynamic scenes): time-conditioned density,
+ *     the cosine argument gains xi_t W_t; the degree-0 SH coefficient follows a
+ *     polynomial plus Fourier series in xi_t.
  *
  * Readings where the paper is silent (camera model, depth key, near plane, early
- * termination, tile keys) follow the conventions documented in the design doc of this
- * repository; each one is restated at its point of use below.
+ * termination, tile keys) are the library's documented conventions; each one is
+ * restated at its point of use below.
  *
  * The FP32 "key specification" (key_* functions) defines which primitives are
  * visible, their pixel rectangle and their depth key.  It is evaluated in IEEE
@@ -60,6 +63,12 @@ typedef struct {
     const double *rgb;                          /* [n,3] */
     const double *feat, *Wc1, *bc1, *Wc2, *bc2, *Wc3, *bc3; /* [n,8] [n,Nc,11] [n,Nc] [n,Nc,Nc] [n,Nc] [n,3,Nc] [n,3] */
     const double *sh;                           /* [n,16,3] spherical-harmonic coefficients */
+    /* Time-conditioned scenes (App. Applications, volumetric dynamic scenes); NULL
+     * for static ones.  time = xi_t of the view being rendered (ora_render takes it
+     * from the camera). */
+    double time;
+    const double *wt;                           /* [n,Ns] phase weights W_t */
+    const double *sh_t;                         /* [n,12,3] degree-0 series a_1..4, b_1..4, c_1..4 */
 } ora_scene;
 
 /* Geometry for the FP32 key specification (the float32 inputs as given). */
@@ -73,6 +82,7 @@ typedef struct {
     float eye[3];
     float fx, fy, cx, cy, z_near;
     int32_t width, height;
+    float time; /* xi_t of this view (dynamic scenes) */
 } ora_camera;
 
 /* =========================================================================
@@ -299,8 +309,16 @@ static double sinc(double x)
     return sin(x) / x;
 }
 
+/* Phase offset of hidden unit k that is constant along every ray: xi_t W_t,k for a
+ * time-conditioned scene (App. Applications: the density's cosine argument gains
+ * xi_t W_t outside the w0 factor), else 0. */
+static double time_phase(const ora_scene *S, int64_t i, int k)
+{
+    return S->wt ? S->time * S->wt[(size_t)i * S->n_sigma + k] : 0.0;
+}
+
 /* Integral of sigma along o + t d over [tm - half, tm + half], stable form:
- * phi_k = w0 (W1_k . u_mid + b1_k), theta_k = w0 (W1_k . d) half / m,
+ * phi_k = w0 (W1_k . u_mid + b1_k) (+ xi_t W_t,k), theta_k = w0 (W1_k . d) half / m,
  * alpha_hat = 2 half [b2 + sum_k w2_k cos(phi_k) sinc(theta_k)]. */
 static double integral_stable(const ora_scene *S, int64_t i, const prim64 *P, const double o[3],
                               const double d[3], double tm, double half)
@@ -313,7 +331,7 @@ static double integral_stable(const ora_scene *S, int64_t i, const prim64 *P, co
     double acc = S->b2[i];
     for (int k = 0; k < Ns; ++k) {
         const double *w = W1 + 3 * k;
-        double phi = w0 * (w[0] * u[0] + w[1] * u[1] + w[2] * u[2] + b1[k]);
+        double phi = w0 * (w[0] * u[0] + w[1] * u[1] + w[2] * u[2] + b1[k]) + time_phase(S, i, k);
         double th = w0 * (w[0] * d[0] + w[1] * d[1] + w[2] * d[2]) * half * P->inv_m;
         acc += w2[k] * cos(phi) * sinc(th);
     }
@@ -321,7 +339,7 @@ static double integral_stable(const ora_scene *S, int64_t i, const prim64 *P, co
 }
 
 /* Eq. 8 literally: S(t) = sum_k w2_k / a_k sin(a_k t + psi_k) + b2 t with
- * a_k = w0 W1_k . d / m, psi_k = w0 (W1_k . (o - c) / m + b1_k); returns S(t1) - S(t0).
+ * a_k = w0 W1_k . d / m, psi_k = w0 (W1_k . (o - c) / m + b1_k) (+ xi_t W_t,k); returns S(t1) - S(t0).
  * Undefined (division by zero) when some a_k == 0. */
 static double integral_naive(const ora_scene *S, int64_t i, const prim64 *P, const double o[3],
                              const double d[3], double t0, double t1)
@@ -334,7 +352,7 @@ static double integral_naive(const ora_scene *S, int64_t i, const prim64 *P, con
     for (int k = 0; k < Ns; ++k) {
         const double *w = W1 + 3 * k;
         double a = w0 * (w[0] * d[0] + w[1] * d[1] + w[2] * d[2]) * P->inv_m;
-        double psi = w0 * ((w[0] * oc[0] + w[1] * oc[1] + w[2] * oc[2]) * P->inv_m + b1[k]);
+        double psi = w0 * ((w[0] * oc[0] + w[1] * oc[1] + w[2] * oc[2]) * P->inv_m + b1[k]) + time_phase(S, i, k);
         s0 += w2[k] / a * sin(a * t0 + psi);
         s1 += w2[k] / a * sin(a * t1 + psi);
     }
@@ -379,7 +397,10 @@ static void sh_basis(const double v[3], double Y[16])
  * MLP (App. D.2 colour field in the ReLU/sigmoid form): z0 = [d, f],
  * z1 = relu(Wc1 z0 + bc1), z2 = relu(Wc2 z1 + bc2), c = sigmoid(Wc3 z2 + bc3).
  * Spherical harmonics: c = max(0, 1/2 + sum_i Y_i(v) sh_i) with v the unit
- * direction from o to the primitive centre.  Constant mode returns rgb. */
+ * direction from o to the primitive centre; for a time-conditioned scene the
+ * degree-0 coefficient is the series sh_0 + sum_{j=1..4} a_j xi^j
+ * + sum_{j=1..4} (b_j cos(j xi) + c_j sin(j xi)) (App. Applications).  Constant
+ * mode returns rgb. */
 static void color_eval(const ora_scene *S, int64_t i, const double o[3], const double d[3], double out[3])
 {
     if (S->color_mode == ORA_COLOR_CONST) {
@@ -397,6 +418,14 @@ static void color_eval(const ora_scene *S, int64_t i, const double o[3], const d
         for (int ch = 0; ch < 3; ++ch) {
             double a = 0.5;
             for (int b = 0; b < 16; ++b) a += Y[b] * K[3 * b + ch];
+            if (S->sh_t) {
+                const double *T = S->sh_t + (size_t)i * 36, x = S->time;
+                double dc = 0.0;
+                for (int j = 1; j <= 4; ++j)
+                    dc += T[3 * (j - 1) + ch] * pow(x, j) + T[3 * (3 + j) + ch] * cos(j * x) +
+                          T[3 * (7 + j) + ch] * sin(j * x);
+                a += Y[0] * dc;
+            }
             out[ch] = relu(a);
         }
         return;
@@ -455,6 +484,9 @@ int64_t ora_render(const ora_scene *S, const ora_camera *cam, const int32_t *pix
                    double t_min, const double *bg, int32_t form, double *out_rgb, double *out_tau,
                    int32_t *out_nwalk, int32_t *out_flags)
 {
+    ora_scene St = *S; /* this view's timestamp */
+    St.time = (double)cam->time;
+    S = &St;
     int64_t n = S->n;
     prim64 *P = (prim64 *)malloc(sizeof(prim64) * (size_t)(n > 0 ? n : 1));
 #pragma omp parallel for schedule(static)

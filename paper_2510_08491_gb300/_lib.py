@@ -33,16 +33,16 @@ class SnpError(RuntimeError):
 class Camera(C.Structure):
     _fields_ = [("R_wc", C.c_float * 9), ("eye", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
                 ("cx", C.c_float), ("cy", C.c_float), ("z_near", C.c_float), ("width", C.c_int32),
-                ("height", C.c_int32)]
+                ("height", C.c_int32), ("time", C.c_float)]
 
 
 class SceneDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_sigma", C.c_int32), ("color_mode", C.c_int32), ("n_c", C.c_int32),
-                ("weight_dtype", C.c_int32), ("omega0", C.c_float), ("reserved_", C.c_int32)]
+                ("weight_dtype", C.c_int32), ("omega0", C.c_float), ("dynamic", C.c_int32)]
 
 
 class NetLayout(C.Structure):
-    _fields_ = [("off", C.c_int32 * 12), ("stride", C.c_int32)]
+    _fields_ = [("off", C.c_int32 * 14), ("stride", C.c_int32)]
 
 
 class ScenePtrs(C.Structure):
@@ -114,8 +114,8 @@ def lib():
     return _lib
 
 
-def net_layout(n_sigma: int, color_mode: int, n_c: int):
-    d = SceneDesc(0, n_sigma, color_mode, n_c if color_mode == COLOR_MLP else 0, F32, 1.0, 0)
+def net_layout(n_sigma: int, color_mode: int, n_c: int, dynamic: bool = False):
+    d = SceneDesc(0, n_sigma, color_mode, n_c if color_mode == COLOR_MLP else 0, F32, 1.0, int(bool(dynamic)))
     L = NetLayout()
     st = lib().snp_get_net_layout(C.byref(d), C.byref(L))
     if st != SNP_OK:
@@ -130,6 +130,7 @@ def make_camera(cam) -> Camera:
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.z_near = float(cam.z_near)
     c.width, c.height = int(cam.width), int(cam.height)
+    c.time = float(getattr(cam, "time", 0.0))
     return c
 
 

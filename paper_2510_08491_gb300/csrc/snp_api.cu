@@ -93,7 +93,7 @@ void layout_of(const snp_scene_desc &d, snp_net_layout &L)
 {
     int off = 0;
     const int ns = d.n_sigma;
-    for (int k = 0; k < 12; ++k) L.off[k] = -1;
+    for (int k = 0; k < 14; ++k) L.off[k] = -1;
     L.off[0] = off; off += round8(3 * ns);
     L.off[1] = off; off += round8(ns);
     L.off[2] = off; off += round8(ns);
@@ -110,6 +110,12 @@ void layout_of(const snp_scene_desc &d, snp_net_layout &L)
     }
     if (d.color_mode == SNP_COLOR_SH) {
         L.off[11] = off; off += 48;
+    }
+    if (d.dynamic) {
+        L.off[12] = off; off += round8(ns);
+        if (d.color_mode == SNP_COLOR_SH) {
+            L.off[13] = off; off += round8(36);
+        }
     }
     L.stride = off;
 }
@@ -215,6 +221,9 @@ static snp_status check_desc(snp_context *ctx, const snp_scene_desc *d)
         return fail(ctx, SNP_ERR_UNSUPPORTED, "n_c must be 32 or 64, got %d", d->n_c);
     if (d->weight_dtype != SNP_F32 && d->weight_dtype != SNP_BF16)
         return fail(ctx, SNP_ERR_INVALID_ARG, "bad weight_dtype %d", d->weight_dtype);
+    if (d->dynamic != 0 && d->dynamic != 1) return fail(ctx, SNP_ERR_INVALID_ARG, "bad dynamic flag %d", d->dynamic);
+    if (d->dynamic && d->color_mode == SNP_COLOR_MLP)
+        return fail(ctx, SNP_ERR_UNSUPPORTED, "time-conditioned scenes are built for constant or SH colour");
     return SNP_OK;
 }
 
@@ -228,6 +237,7 @@ static snp_status check_cams(snp_context *ctx, const snp_camera *cams, int n_cam
             return fail(ctx, SNP_ERR_INVALID_ARG, "camera %d: bad size %dx%d", v, c.width, c.height);
         if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !(c.z_near > 0.0f))
             return fail(ctx, SNP_ERR_INVALID_ARG, "camera %d: fx, fy, z_near must be > 0", v);
+        if (!std::isfinite(c.time)) return fail(ctx, SNP_ERR_INVALID_ARG, "camera %d: time is not finite", v);
     }
     return SNP_OK;
 }
@@ -248,7 +258,7 @@ static snp_status build_views(snp_context *ctx, const snp_camera *cams, int n_ca
         V.tiles_x = (c.width + ts - 1) / ts;
         V.tiles_y = (c.height + ts - 1) / ts;
         V.tile_off = (int32_t)t;
-        V.pad_ = 0;
+        V.time = c.time;
         V.pix_off = p;
         {
             // (R_wc^T)^-1 by the adjugate, in FP64
@@ -300,6 +310,7 @@ static void fill_args(RasterArgs &a, const snp_context *ctx, const snp_scene_des
     a.off_W1 = L.off[0]; a.off_b1 = L.off[1]; a.off_w2 = L.off[2]; a.off_b2 = L.off[3];
     a.off_feat = L.off[4]; a.off_Wc1 = L.off[5]; a.off_bc1 = L.off[6]; a.off_Wc2 = L.off[7];
     a.off_bc2 = L.off[8]; a.off_Wc3 = L.off[9]; a.off_bc3 = L.off[10]; a.off_sh = L.off[11];
+    a.off_wt = L.off[12];
     a.stride = L.stride;
     a.omega0 = d->omega0;
     a.t_min = ctx->cfg.t_min;
@@ -315,7 +326,8 @@ extern "C" {
 snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out)
 {
     if (!desc || !out) return SNP_ERR_INVALID_ARG;
-    if (check_desc(nullptr, desc) != SNP_OK) return SNP_ERR_INVALID_ARG;
+    const snp_status s = check_desc(nullptr, desc);
+    if (s != SNP_OK) return s;
     layout_of(*desc, *out);
     return SNP_OK;
 }
@@ -473,7 +485,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     if (!(c.t_min >= 0.0f) || !(c.t_min < 1.0f)) return fail(ctx, SNP_ERR_INVALID_ARG, "t_min must be in [0, 1)");
     const int ts = c.tile_size;
     const int chunk =
-        c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts);
+        c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts, desc->dynamic != 0);
     if (chunk > 64 || raster_fwd_smem(desc->color_mode, desc->n_c, desc->n_sigma, chunk, ts) > 220 * 1024)
         return fail(ctx, SNP_ERR_INVALID_ARG, "chunk %d too large", chunk);
 
@@ -529,9 +541,13 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         fill_args(pa, ctx, desc, scene, nullptr);
         if ((s = launch_pack_net(pa, desc->color_mode, desc->n_c, desc->weight_dtype == SNP_BF16, st)) != SNP_OK)
             return fail(ctx, s, "network pack launch failed");
-        if (desc->color_mode == SNP_COLOR_SH)
+        if (desc->color_mode == SNP_COLOR_SH) {
+            snp_net_layout L;
+            layout_of(*desc, L);
             launch_sh_color((const float *)scene->geom, scene->net, desc->weight_dtype == SNP_BF16, n,
-                            (const View *)ctx->views.p, n_cams, pa.off_sh, pa.stride, (float *)ctx->rec.p, st);
+                            (const View *)ctx->views.p, n_cams, L.off[11], L.off[13], L.stride, (float *)ctx->rec.p,
+                            st);
+        }
     }
     STAGE_END();
     STAGE_BEGIN(SNP_STAGE_SCAN);
@@ -631,7 +647,7 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     a.g_net = grads->net;
     a.g_view = (float *)ctx->g_view.p;
     a.g_h0 = (float *)ctx->g_h0.p;
-    a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true, ctx->ts);
+    a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true, ctx->ts, desc->dynamic != 0);
     if (ctx->cfg.chunk > 0 && ctx->cfg.chunk < a.chunk) a.chunk = ctx->cfg.chunk;
     int *d_work = (int *)((char *)ctx->small.p + kSmallWork);
     a.work_counter = d_work;
@@ -648,10 +664,13 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     if (grads->geom)
         launch_project_bwd((const float *)scene->geom, n, (const View *)ctx->views.p, ctx->n_views,
                            (const float *)ctx->g_view.p, desc->color_mode == SNP_COLOR_CONST, grads->geom, st);
-    if (desc->color_mode == SNP_COLOR_SH && (grads->geom || grads->net))
+    if (desc->color_mode == SNP_COLOR_SH && (grads->geom || grads->net)) {
+        snp_net_layout L;
+        layout_of(*desc, L);
         launch_sh_bwd((const float *)scene->geom, scene->net, desc->weight_dtype == SNP_BF16, n,
-                      (const View *)ctx->views.p, ctx->n_views, a.off_sh, a.stride, (const float *)ctx->rec.p,
-                      (const float *)ctx->g_view.p, grads->net, grads->geom, st);
+                      (const View *)ctx->views.p, ctx->n_views, L.off[11], L.off[13], L.stride,
+                      (const float *)ctx->rec.p, (const float *)ctx->g_view.p, grads->net, grads->geom, st);
+    }
     if (grads->net && desc->color_mode == SNP_COLOR_MLP)
         launch_color_post(scene->net, desc->weight_dtype == SNP_BF16, n, desc->n_c, a.off_feat, a.off_Wc1,
                           a.off_bc1, a.stride, (const float *)ctx->g_h0.p, grads->net, st);
@@ -713,7 +732,7 @@ snp_status snp_autotune(snp_context *ctx, const snp_scene_desc *desc, const snp_
     const int sizes[3] = {8, 16, 32};
     for (int ti = 0; ti < 3; ++ti) {
         const int ts = sizes[ti];
-        const int dch = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts);
+        const int dch = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts, desc->dynamic != 0);
         const int chunks[2] = {dch, dch / 2 > 0 ? dch / 2 : 1};
         for (int ci = 0; ci < (chunks[1] == chunks[0] ? 1 : 2); ++ci) {
             snp_config c = b;

@@ -57,7 +57,7 @@ struct View {
     int32_t width, height;
     int32_t tiles_x, tiles_y;
     int32_t tile_off;  // first global tile id of this view
-    int32_t pad_;
+    float time;        // timestamp xi_t (time-conditioned scenes)
     int64_t pix_off;   // first pixel of this view in the concatenated image
     // Inverse of R_wc^T in FP64: the stored FP32 rotation is not exactly
     // orthonormal, so the camera-frame centre used for the ray geometry is

@@ -45,6 +45,7 @@ struct RasterArgs {
     int64_t n_tiles;
     const int32_t *lay;       // unused on device (layout passed by value below)
     int32_t off_W1, off_b1, off_w2, off_b2, off_feat, off_Wc1, off_bc1, off_Wc2, off_bc2, off_Wc3, off_bc3, off_sh;
+    int32_t off_wt;           // time-conditioned density: W_t [n_sigma] (-1: static scene)
     int32_t stride;
     float omega0;
     float t_min;
@@ -76,11 +77,12 @@ struct RasterArgs {
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
 // snp_sh.cu
+// off_sht: the degree-0 time series [12][3] of a time-conditioned scene (-1: none)
 void launch_sh_color(const float *geom, const void *net, int bf16, int64_t n, const View *views, int n_views,
-                     int off_sh, int stride, float *rec, cudaStream_t st);
+                     int off_sh, int off_sht, int stride, float *rec, cudaStream_t st);
 void launch_sh_bwd(const float *geom, const void *net, int bf16, int64_t n, const View *views, int n_views,
-                   int off_sh, int stride, const float *rec, const float *g_view, float *g_net, float *g_geom,
-                   cudaStream_t st);
+                   int off_sh, int off_sht, int stride, const float *rec, const float *g_view, float *g_net,
+                   float *g_geom, cudaStream_t st);
 
 // snp_loss.cu
 constexpr int kLossSlots = 1024;
@@ -91,8 +93,8 @@ snp_status launch_raster_bwd(const RasterArgs &a, int color_mode, int n_c, int f
 size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);
 int raster_npack_stride(int color_mode, int n_c, int n_sigma);
 snp_status launch_pack_net(const RasterArgs &a, int color_mode, int n_c, int bf16, cudaStream_t st);
-size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts);
-int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts);
+size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts, bool dyn);
+int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts, bool dyn);
 snp_status launch_fwd_ts8(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
 snp_status launch_fwd_ts16(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);
 snp_status launch_fwd_ts32(const RasterArgs &a, int nc, int form, int bf16, cudaStream_t st);

@@ -53,20 +53,53 @@ __device__ __forceinline__ void cp_async_wait_all()
 // into shared memory: the projection record and the primitive's packed network
 // block (already in the staged layout, see k_pack_net) as 16-byte asynchronous
 // copies.  All threads of the block participate; the caller synchronises.
+//
+// Without a colour network (NC = 0) an entry is only ~23 pieces, so the pieces of
+// all entries are spread over the block as one flat range.  Those kernels also
+// carry the time-conditioned scene (a.off_wt >= 0): the view's phase xi W_t,k is
+// added to the staged w0 b1_k of every hidden unit -- the time term is constant
+// along a ray, a per-(view, primitive) shift of the phase (App. Applications).
+// Each thread shifts only pieces it copied itself, which its own
+// cp.async.wait_group has completed.  (The colour-MLP kernels keep the
+// per-entry loop and never see the shift, so their register allocation is
+// unchanged.)
+template <int NC, bool BF16>
 __device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
-                                            const RasterArgs &a, int es)
+                                            const RasterArgs &a, int es, float xi)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr int kRec16 = kRecFloats / 4;
     const int per = es / 4;  // 16-byte pieces per entry: record, then the network block
-    for (int e = 0; e < cnt; ++e) {
-        const int64_t gid = s_gid[e];
-        const float *rec = a.rec + gid * kRecFloats;
-        const float *net = a.npack + (gid - vn) * a.npack_stride;
-        float *dst = sm + e * es;
-        for (int q = tid; q < per; q += nt) cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
+    if constexpr (NC == 0) {
+        const int total = cnt * per;
+        for (int idx = tid; idx < total; idx += nt) {
+            const int e = idx / per, q = idx - e * per;
+            const int64_t gid = s_gid[e];
+            const float *src = q < kRec16 ? a.rec + gid * kRecFloats + 4 * q
+                                          : a.npack + (gid - vn) * a.npack_stride + 4 * (q - kRec16);
+            cp_async16(sm + e * es + 4 * q, src);
+        }
+        cp_async_wait_all();
+        if (a.off_wt >= 0) {
+            for (int idx = tid; idx < total; idx += nt) {
+                const int e = idx / per, q = idx - e * per - kRec16;
+                if (q >= 0 && q < a.n_sigma) {
+                    float *w = sm + e * es + 4 * (q + kRec16) + 3;
+                    *w = fmaf(xi, ld_w<BF16>(a.net, (s_gid[e] - vn) * a.stride + a.off_wt + q), *w);
+                }
+            }
+        }
+    } else {
+        for (int e = 0; e < cnt; ++e) {
+            const int64_t gid = s_gid[e];
+            const float *rec = a.rec + gid * kRecFloats;
+            const float *net = a.npack + (gid - vn) * a.npack_stride;
+            float *dst = sm + e * es;
+            for (int q = tid; q < per; q += nt)
+                cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
+        }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
 }
 
 // Network block of primitive p in the staged layout (density block, then the

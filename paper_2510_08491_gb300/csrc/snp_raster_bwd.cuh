@@ -29,11 +29,11 @@ constexpr int kMaskWords = 512;
 // Elements of one primitive's network record (snp_net_layout): every field
 // 8-element aligned and padded.
 __host__ __device__ constexpr int round8i(int x) { return (x + 7) & ~7; }
-__host__ __device__ constexpr int net_stride(int ns, int nc, bool sh)
+__host__ __device__ constexpr int net_stride(int ns, int nc, bool sh, bool dyn)
 {
     return round8i(3 * ns) + 2 * round8i(ns) + 8 +
            (nc == 0 ? 0 : 8 + round8i(11 * nc) + round8i(nc) + round8i(nc * nc) + round8i(nc) + round8i(3 * nc) + 8) +
-           (sh ? 48 : 0);
+           (sh ? 48 : 0) + (dyn ? round8i(ns) + (sh ? 40 : 0) : 0);
 }
 
 // Per-entry gradient accumulator (floats):
@@ -55,12 +55,14 @@ __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, 
 }
 
 // Flush the chunk's cnt entry accumulators: permute the Wc2 blocks to row-major
-// and scale W1 / b1 by w0 in place, reduce every block into the caller's arrays
+// and scale W1 / b1 by w0 in place (for a time-conditioned scene first setting
+// dL/dW_t,k = xi dL/d(staged phase offset k), since the staged offset is
+// w0 b1_k + xi W_t,k), reduce every block into the caller's arrays
 // with bulk asynchronous adds (issued by thread 0), wait until they have read
 // shared memory, then clear the accumulators.  All threads call it.
 template <int NC, int NT>
 __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int vg, const uint32_t *s_gid, int cnt,
-                                            int64_t vn, int tid, int nt)
+                                            int64_t vn, int tid, int nt, float xi)
 {
     const int ns = a.n_sigma;
     if constexpr (NC > 0) {
@@ -93,6 +95,14 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
                 }
                 __syncthreads();
             }
+        }
+    }
+    if (NC == 0 && a.off_wt >= 0) {
+        // same (entry, unit) -> thread map as the scaling loop below: no barrier needed
+        for (int q = tid; q < cnt * (4 * ns); q += nt) {
+            const int e = q / (4 * ns), r = q - e * (4 * ns);
+            float *A = acc + e * vg;
+            if (r >= 3 * ns) A[a.off_wt + r - 3 * ns] = xi * A[a.off_b1 + r - 3 * ns];
         }
     }
     for (int q = tid; q < cnt * (4 * ns); q += nt) {
@@ -416,7 +426,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 s_cmw[i] = c0 - rg.x + e < maxwalk ? a.cmask[(int64_t)c0 * (NPIX / 32) + i] : 0u;
             }
             __syncthreads();
-            stage_chunk(sm, s_gid, cnt, vn, a, es);
+            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es, V.time);
             __syncthreads();
 
             // P1: the pixels that composited each entry, from the forward's masks (entries
@@ -531,7 +541,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            flush_chunk<NC, NT>(a, acc, vg, s_gid, cnt, vn, tid, NT);
+            flush_chunk<NC, NT>(a, acc, vg, s_gid, cnt, vn, tid, NT, V.time);
         }
         __syncthreads();
     }

@@ -15,10 +15,10 @@ size_t raster_fwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
     return fwd_smem_bytes<16>(nc, n_sigma, chunk);
 }
 
-size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
+size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts, bool dyn)
 {
     const int nc = nc_of(color_mode, n_c);
-    const int stride = net_stride(n_sigma, nc, color_mode == SNP_COLOR_SH);
+    const int stride = net_stride(n_sigma, nc, color_mode == SNP_COLOR_SH, dyn);
     if (ts == 8) return bwd_smem_bytes<8>(nc, n_sigma, chunk, stride);
     if (ts == 32) return bwd_smem_bytes<32>(nc, n_sigma, chunk, stride);
     return bwd_smem_bytes<16>(nc, n_sigma, chunk, stride);
@@ -27,14 +27,14 @@ size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts)
 // Largest chunk (<= 32 forward, <= 8 backward) within the shared-memory budget:
 // about half an SM for the forward (two CTAs per SM); for the backward half an SM
 // where it is built for two CTAs per SM, else most of one.
-int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts)
+int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts, bool dyn)
 {
     const int fmb = fwd_min_blocks(ts, nc_of(color_mode, n_c));
     const size_t fwd_budget = fmb == 4 ? 52 * 1024 : (fmb == 3 ? 70 * 1024 : 104 * 1024);
     const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2 ? 110 * 1024 : 200 * 1024;
     int ch = backward ? 8 : 32;
     if (backward) {
-        while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts) > bwd_budget) --ch;
+        while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts, dyn) > bwd_budget) --ch;
     } else {
         while (ch > 1 && raster_fwd_smem(color_mode, n_c, n_sigma, ch, ts) > fwd_budget) --ch;
     }

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                 s_na[tid] = 0;
             }
             __syncthreads();
-            stage_chunk(sm, s_gid, cnt, vn, a, es);
+            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es, V.time);
             __syncthreads();
 
             // P1: which pixels' rays enter which ellipsoids

@@ -10,6 +10,11 @@
 // through v = (c_prim - eye) / |c_prim - eye|, to the centre.
 //
 // Y_i are the real harmonics of degree l = 0..3 in tesseral form, index l^2 + l + m.
+//
+// Time-conditioned scenes (App. Applications, volumetric dynamic scenes): the
+// degree-0 coefficient of each channel is sh[0] + sum_{j=1..4} a_j xi^j
+// + sum_{j=1..4} (b_j cos(j xi) + c_j sin(j xi)), xi the view's timestamp; the
+// 12 series coefficients per channel are stored [12][3] as a_1..4, b_1..4, c_1..4.
 #include "snp_common.cuh"
 #include "snp_internal.h"
 
@@ -44,6 +49,18 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float (&Y)[16
     Y[13] = kY3c * x * (5.0f * z2 - 1.0f);
     Y[14] = kY3e * z * (x2 - y2);
     Y[15] = kY3a * x * (x2 - 3.0f * y2);
+}
+
+// The 12 basis values of the degree-0 time series at xi: xi^j, cos(j xi), sin(j xi), j = 1..4.
+__device__ __forceinline__ void time_basis(float xi, float (&B)[12])
+{
+    float p = xi;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        B[j] = p;
+        p *= xi;
+        sincosf((float)(j + 1) * xi, &B[8 + j], &B[4 + j]);
+    }
 }
 
 // Gradient of sum_i g_i Y_i(x, y, z) with respect to (x, y, z) (the harmonics as
@@ -85,7 +102,7 @@ __device__ __forceinline__ float3 sh_grad(float x, float y, float z, const float
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_sh_color(const float *__restrict__ geom, const void *__restrict__ net,
                                                   int64_t n, const View *__restrict__ views, int n_views, int off_sh,
-                                                  int stride, float *__restrict__ rec)
+                                                  int off_sht, int stride, float *__restrict__ rec)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n * n_views) return;
@@ -105,6 +122,18 @@ __global__ void __launch_bounds__(256) k_sh_color(const float *__restrict__ geom
     for (int b = 0; b < 16; ++b)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(Y[b], ld_w<BF16>(net, base + 3 * b + ch), col[ch]);
+    if (off_sht >= 0) {
+        float B[12];
+        time_basis(V.time, B);
+        const int64_t tb = i * stride + off_sht;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float dc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 12; ++j) dc = fmaf(B[j], ld_w<BF16>(net, tb + 3 * j + ch), dc);
+            col[ch] = fmaf(Y[0], dc, col[ch]);
+        }
+    }
     float *r = rec + q * kRecFloats + kRecRgb;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) r[ch] = fmaxf(col[ch], 0.0f);
@@ -113,7 +142,7 @@ __global__ void __launch_bounds__(256) k_sh_color(const float *__restrict__ geom
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_sh_bwd(const float *__restrict__ geom, const void *__restrict__ net,
                                                 int64_t n, const View *__restrict__ views, int n_views, int off_sh,
-                                                int stride, const float *__restrict__ rec,
+                                                int off_sht, int stride, const float *__restrict__ rec,
                                                 const float *__restrict__ g_view, float *__restrict__ g_net,
                                                 float *__restrict__ g_geom)
 {
@@ -129,6 +158,11 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const float *__restrict__ geom, 
             K[b][ch] = ld_w<BF16>(net, base + 3 * b + ch);
             gK[b][ch] = 0.0f;
         }
+    float gT[12][3];
+#pragma unroll
+    for (int j = 0; j < 12; ++j)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gT[j][ch] = 0.0f;
     float3 gc = make_float3(0.f, 0.f, 0.f);
     for (int v = 0; v < n_views; ++v) {
         const int64_t q = (int64_t)v * n + i;
@@ -156,6 +190,15 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const float *__restrict__ geom, 
                 gY[b] = fmaf(gch[ch], K[b][ch], gY[b]);
             }
         }
+        if (off_sht >= 0) {
+            // the series enters as Y_0 dc: dL/d(series coefficient j) = dL/dc Y_0 B_j(xi)
+            float B[12];
+            time_basis(V.time, B);
+#pragma unroll
+            for (int j = 0; j < 12; ++j)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) gT[j][ch] = fmaf(gch[ch] * kY0, B[j], gT[j][ch]);
+        }
         // v = w / |w|, w = c - eye:  dL/dw = (I - v v^T) dL/dv / |w|
         const float3 gv = sh_grad(dx, dy, dz, gY);
         const float vg = gv.x * dx + gv.y * dy + gv.z * dz;
@@ -168,6 +211,13 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const float *__restrict__ geom, 
         for (int b = 0; b < 16; ++b)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) g_net[base + 3 * b + ch] += gK[b][ch];
+        if (off_sht >= 0) {
+            const int64_t tb = i * stride + off_sht;
+#pragma unroll
+            for (int j = 0; j < 12; ++j)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) g_net[tb + 3 * j + ch] += gT[j][ch];
+        }
     }
     if (g_geom) {
         float *O = g_geom + i * SNP_GEOM_STRIDE;
@@ -180,27 +230,28 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const float *__restrict__ geom, 
 }  // namespace
 
 void launch_sh_color(const float *geom, const void *net, int bf16, int64_t n, const View *views, int n_views,
-                     int off_sh, int stride, float *rec, cudaStream_t st)
+                     int off_sh, int off_sht, int stride, float *rec, cudaStream_t st)
 {
     const int64_t total = n * n_views;
     if (total <= 0) return;
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    if (bf16) k_sh_color<true><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, stride, rec);
-    else k_sh_color<false><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, stride, rec);
+    if (bf16) k_sh_color<true><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, off_sht, stride, rec);
+    else k_sh_color<false><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, off_sht, stride, rec);
     note_launch();
 }
 
 void launch_sh_bwd(const float *geom, const void *net, int bf16, int64_t n, const View *views, int n_views,
-                   int off_sh, int stride, const float *rec, const float *g_view, float *g_net, float *g_geom,
-                   cudaStream_t st)
+                   int off_sh, int off_sht, int stride, const float *rec, const float *g_view, float *g_net,
+                   float *g_geom, cudaStream_t st)
 {
     if (n <= 0) return;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     if (bf16)
-        k_sh_bwd<true><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, stride, rec, g_view, g_net, g_geom);
+        k_sh_bwd<true><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, off_sht, stride, rec, g_view,
+                                               g_net, g_geom);
     else
-        k_sh_bwd<false><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, stride, rec, g_view, g_net,
-                                                g_geom);
+        k_sh_bwd<false><<<blocks, 256, 0, st>>>(geom, net, n, views, n_views, off_sh, off_sht, stride, rec, g_view,
+                                                g_net, g_geom);
     note_launch();
 }
 

@@ -16,7 +16,7 @@ import torch
 
 from . import _lib as L
 
-NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")
+NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh", "wt", "sh_t")
 
 
 @dataclass
@@ -42,7 +42,8 @@ def pack_scene(scene, device="cuda", weight_dtype: Optional[str] = None) -> Pack
     wd = weight_dtype or scene.weight_dtype
     mlp = scene.color == "mlp"
     cm = {"const": L.COLOR_CONST, "mlp": L.COLOR_MLP, "sh": L.COLOR_SH}[scene.color]
-    offs, stride = L.net_layout(scene.n_sigma, cm, scene.n_c)
+    dyn = bool(getattr(scene, "dynamic", False))
+    offs, stride = L.net_layout(scene.n_sigma, cm, scene.n_c, dyn)
     n = scene.n
     geom = np.zeros((n, L.GEOM_STRIDE), np.float32)
     geom[:, 0:3] = scene.centers
@@ -57,7 +58,7 @@ def pack_scene(scene, device="cuda", weight_dtype: Optional[str] = None) -> Pack
         a = a.reshape(n, int(np.prod(a.shape[1:])) if a.ndim > 1 else 1)
         net[:, offs[k]:offs[k] + a.shape[1]] = a
     desc = L.SceneDesc(n, scene.n_sigma, cm, scene.n_c if mlp else 0, L.BF16 if wd == "bf16" else L.F32,
-                       float(scene.omega0), 0)
+                       float(scene.omega0), int(dyn))
     g = torch.from_numpy(geom).to(device)
     t = torch.from_numpy(net).to(device)
     if wd == "bf16":

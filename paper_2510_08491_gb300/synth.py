@@ -45,6 +45,7 @@ class Camera:
     width: int
     height: int
     z_near: np.float32 = np.float32(0.2)
+    time: np.float32 = np.float32(0.0)  # timestamp in [0, 1] (dynamic scenes only)
 
     @property
     def n_pixels(self) -> int:
@@ -81,10 +82,15 @@ class Scene:
     Wc3: Optional[np.ndarray] = None  # (n, 3, Nc)
     bc3: Optional[np.ndarray] = None  # (n, 3)
     sh: Optional[np.ndarray] = None  # (n, 16, 3) spherical-harmonic colour coefficients
+    # time-conditioned scenes: phase weights W_t per hidden unit and, with SH colour,
+    # the degree-0 time series a_1..a_4, b_1..b_4, c_1..c_4 per channel
+    dynamic: bool = False
+    wt: Optional[np.ndarray] = None  # (n, Ns)
+    sh_t: Optional[np.ndarray] = None  # (n, 12, 3)
     weight_dtype: str = "f32"
     extra: dict = field(default_factory=dict)
 
-    NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh")
+    NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh", "wt", "sh_t")
     GEOM_FIELDS = ("centers", "log_scales", "quats", "rgb")
 
     def fields(self):
@@ -93,6 +99,8 @@ class Scene:
             names += ["feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"]
         if self.color == "sh":
             names += ["sh"]
+        if self.dynamic:
+            names += ["wt"] + (["sh_t"] if self.color == "sh" else [])
         return names
 
     def subset(self, idx) -> "Scene":
@@ -178,13 +186,15 @@ def fibonacci_cameras(n: int, radius: float, resolutions: Sequence) -> List[Came
 def make_scene(n: int, seed: int = 0, *, center_half: float = 1.0, n_sigma: int = 8,
                omega0: float = 5.0, color: str = "const", n_c: int = 32,
                log_scale_mean: float = -2.0, log_scale_std: float = 0.3,
-               thin_ratio_max: Optional[float] = None, rng=None) -> Scene:
+               thin_ratio_max: Optional[float] = None, dynamic: bool = False, rng=None) -> Scene:
     """Draw a scene with the distributions of the benchmark workloads.
 
     centres ~ U[-h, h]^3, log-scales ~ N(-2, 0.3) per axis, quaternions ~ N(0, I4),
     W1 ~ N(0, 1), b1 ~ U(-pi, pi), w2 ~ N(0, 0.5), b2 = 0.5, rgb ~ U(0, 1);
     colour MLP: feat ~ N(0, 1), Wc_l ~ N(0, 1/sqrt(fan_in)), biases 0.
     spherical harmonics ("sh"): degree-0 coefficients ~ N(0, 0.6), degrees 1..3 ~ N(0, 0.2).
+    dynamic: W_t ~ N(0, 2) (phase shift per unit time); with SH colour the degree-0
+    time series coefficients ~ N(0, 0.1).  Drawn last, after everything above.
     thin_ratio_max: if set, axis 0 is the major axis ~ N(-2, 0.3) and the other two
     are major - ln r with r ~ logU[1, thin_ratio_max] (independently per axis).
     """
@@ -219,6 +229,11 @@ def make_scene(n: int, seed: int = 0, *, center_half: float = 1.0, n_sigma: int 
         sh = g.normal(0.0, 0.2, size=(n, 16, 3))
         sh[:, 0, :] = g.normal(0.0, 0.6, size=(n, 3))
         sc.sh = sh.astype(f32)
+    if dynamic:
+        sc.dynamic = True
+        sc.wt = g.normal(0.0, 2.0, size=(n, n_sigma)).astype(f32)
+        if color == "sh":
+            sc.sh_t = g.normal(0.0, 0.1, size=(n, 12, 3)).astype(f32)
     return sc
 
 
@@ -318,15 +333,18 @@ def workload(name: str, seed: int = 0) -> Workload:
         g = np.random.Generator(np.random.PCG64(seed + 7))
         res = [RESOLUTIONS[i] for i in g.integers(0, 4, size=16)]
         return Workload(name, sc.to_bf16(), fibonacci_cameras(16, 10.0, res), 16)
-    if name == "fps100k_800px_sh":
+    if name in ("fps100k_800px_sh", "dyn100k_800px_8t"):
         # The speed protocol of App. A (Integration Cost): 100k random primitives in a
         # volume, the primitive of Sec. 3.3 (Implementation Details: N_sigma = 8, w0 = 30,
         # four SH bands) with its initialisation of the density weights,
         # W1 ~ U(-1/3, 1/3) and w2 ~ U(-sqrt(6/N_sigma)/w0, +), seen by square 800 x 800
-        # views at a 39.6 degree field of view on a radius-4 ring (the camera set-up of
-        # the synthetic scenes).
+        # views at a 39.6 degree field of view on a radius-4 ring at 30 degrees elevation
+        # (the camera set-up of the synthetic scenes).  The dynamic variant (the
+        # volumetric dynamic scenes of App. Applications) adds the time-conditioned
+        # density and degree-0 colour series and gives view k the timestamp k / 7.
+        dyn = name.startswith("dyn")
         sc = make_scene(100_000, seed, center_half=1.5, n_sigma=8, omega0=30.0, color="sh",
-                        log_scale_mean=-3.0)
+                        log_scale_mean=-3.0, dynamic=dyn)
         g = np.random.Generator(np.random.PCG64(seed + 3))
         sc.W1 = g.uniform(-1.0 / 3.0, 1.0 / 3.0, size=sc.W1.shape).astype(np.float32)
         lim = math.sqrt(6.0 / sc.n_sigma) / sc.omega0
@@ -336,10 +354,13 @@ def workload(name: str, seed: int = 0) -> Workload:
             t = 2.0 * math.pi * k / 8
             eye = (4.0 * math.sin(t) * math.cos(math.radians(30.0)), 4.0 * math.sin(math.radians(30.0)),
                    4.0 * math.cos(t) * math.cos(math.radians(30.0)))
-            cams.append(look_at_camera(eye, (0, 0, 0), 800, 800, fov_y_deg=39.6))
+            cam = look_at_camera(eye, (0, 0, 0), 800, 800, fov_y_deg=39.6)
+            if dyn:
+                cam.time = np.float32(k / 7.0)
+            cams.append(cam)
         return Workload(name, sc, cams, 16)
     raise KeyError(name)
 
 
 WORKLOADS = ("tiny64_128px", "fwd100k_1080p_4view", "diff300k_720p", "thin50k_1080p",
-             "batch500k_16view", "fps100k_800px_sh")
+             "batch500k_16view", "fps100k_800px_sh", "dyn100k_800px_8t")

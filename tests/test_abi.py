@@ -3,6 +3,8 @@
 No compute call is made (no GPU needed)."""
 import ctypes
 
+import pytest
+
 from paper_2510_08491_gb300 import _lib as L
 
 
@@ -32,7 +34,15 @@ def test_net_layout_is_aligned_and_complete():
         assert o1 + s1 <= o2
     assert spans[-1][0] + spans[-1][1] <= stride
     offs_c, stride_c = L.net_layout(8, L.COLOR_CONST, 0)
-    assert offs_c[4:] == [-1] * 8 and stride_c == 24 + 8 + 8 + 8
+    assert offs_c[4:] == [-1] * 10 and stride_c == 24 + 8 + 8 + 8
     # spherical harmonics: the density fields, then sh [16][3]
     offs_s, stride_s = L.net_layout(8, L.COLOR_SH, 0)
     assert offs_s[4:11] == [-1] * 7 and offs_s[11] == 48 and stride_s == 48 + 48
+    assert offs_s[12:] == [-1, -1]
+    # time-conditioned: W_t [N_sigma] after everything, then the SH series [12][3]
+    offs_d, stride_d = L.net_layout(8, L.COLOR_SH, 0, dynamic=True)
+    assert offs_d[:12] == offs_s[:12] and offs_d[12] == 96 and offs_d[13] == 104 and stride_d == 144
+    offs_dc, stride_dc = L.net_layout(8, L.COLOR_CONST, 0, dynamic=True)
+    assert offs_dc[12] == 48 and offs_dc[13] == -1 and stride_dc == 56
+    with pytest.raises(L.SnpError):
+        L.net_layout(8, L.COLOR_MLP, 32, dynamic=True)

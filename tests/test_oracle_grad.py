@@ -22,8 +22,14 @@ from paper_2510_08491_gb300 import synth
 
 
 def _setup(O, n=2000, color="mlp", seed=0, res=64):
-    sc = synth.make_scene(n, seed=seed, center_half=3.0, n_sigma=16, omega0=5.0, color=color, n_c=32)
+    """color "<mode>+t": a time-conditioned scene seen at time 0.6."""
+    dyn = color.endswith("+t")
+    color = color.split("+")[0]
+    sc = synth.make_scene(n, seed=seed, center_half=3.0, n_sigma=16, omega0=5.0, color=color, n_c=32,
+                          dynamic=dyn)
     cam = synth.ring_cameras(1, 8.0, res, res)[0]
+    if dyn:
+        cam.time = np.float32(0.6)
     ts = 16
     tl = O.tile_keys(sc, [cam], ts)
     pix = np.arange(cam.n_pixels, dtype=np.int32)
@@ -63,7 +69,7 @@ def _loss(O, sc, cam, pix, gtile, off, lp, dL, cs=None):
     return float((out.rgb * dL).sum()), out.n_comp
 
 
-@pytest.mark.parametrize("color", ["const", "mlp", "sh"])
+@pytest.mark.parametrize("color", ["const", "mlp", "sh", "sh+t"])
 def test_torch_forward_equals_c_forward(oracle_lib, color):
     O = oracle_lib
     from oracle import grad as G
@@ -123,7 +129,7 @@ def _fd_group_directions(O, G, color, n_dirs, seed):
     return checked, skipped, worst
 
 
-@pytest.mark.parametrize("color", ["const", "mlp", "sh"])
+@pytest.mark.parametrize("color", ["const", "mlp", "sh", "const+t", "sh+t"])
 def test_gradient_matches_fd_directional(oracle_lib, color):
     O = oracle_lib
     from oracle import grad as G
