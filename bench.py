@@ -169,6 +169,79 @@ def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True
 
 
 # ----------------------------------------------------------------------------- GPU leg
+class TrainState:
+    """The rest of a training step after the backward pass: the anisotropy
+    regulariser, the population-control statistic and one Adam step (learning
+    rates of the paper's App. hyperparameters), plus isolated timings of each."""
+
+    def __init__(self, r, ps, sc):
+        import torch
+        from paper_2510_08491_gb300 import _lib as L
+        self.r, self.ps, self.n = r, ps, ps.n
+        self.m_geom, self.v_geom = torch.zeros_like(ps.geom), torch.zeros_like(ps.geom)
+        self.m_net = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
+        self.v_net = torch.zeros_like(self.m_net)
+        self.master = ps.net.float().clone() if ps.net.dtype != torch.float32 else None
+        self.ssum = torch.zeros(self.n, dtype=torch.float32, device="cuda")
+        self.scnt = torch.zeros(self.n, dtype=torch.int32, device="cuda")
+        c = L.AdamConfig()
+        c.lr_geom[:] = [1.6e-4, 5e-3, 1e-3, 2.5e-3]
+        c.lr_net[:] = [1e-3] * 11 + [2.5e-3, 1e-3, 2.5e-3]
+        c.beta1, c.beta2, c.eps, c.step = 0.9, 0.999, 1e-15, 0
+        self.cfg = c
+        ns, nc = sc.n_sigma, sc.n_c if sc.color == "mlp" else 0
+        sizes = [3 * ns, ns, ns, 1, 8, nc * 11, nc, nc * nc, nc, 3 * nc, 3, 48, ns, 36]
+        self.net_cols = sum(4 * ((sizes[k] + 3) // 4) for k, o in enumerate(ps.offsets) if o >= 0)
+        self.reg_weight = 1e-3
+
+    def step(self, g_geom, g_net):
+        self.r.geom_reg(self.ps, self.reg_weight, g_geom)
+        self.r.popctl_accumulate(self.ps, g_net, self.ssum, self.scnt)
+        self.cfg.step += 1
+        self.r.adam_step(self.ps, g_geom, g_net, self.m_geom, self.v_geom, self.m_net, self.v_net, self.cfg,
+                         net_master=self.master)
+
+    def _time(self, fn, k):
+        import torch
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    def measure(self, g_geom, g_net, hbm_gbs):
+        import torch
+        from paper_2510_08491_gb300 import _lib as L
+
+        def adam():
+            self.cfg.step += 1
+            self.r.adam_step(self.ps, g_geom, g_net, self.m_geom, self.v_geom, self.m_net, self.v_net, self.cfg,
+                             net_master=self.master)
+        t_adam = self._time(adam, 20)
+        # algorithmic bytes: per updated element p, g, m, v read and p, m, v written (28 B;
+        # BF16 weights: FP32 master plus the 2-byte rounded copy, 30 B)
+        b_el = 30 if self.master is not None else 28
+        bytes_adam = self.n * (13 * 28 + self.net_cols * b_el)
+        t_reg = self._time(lambda: self.r.geom_reg(self.ps, self.reg_weight, g_geom), 20)
+        t_stat = self._time(lambda: self.r.popctl_accumulate(self.ps, g_net, self.ssum, self.scnt), 20)
+        pc = L.PopctlConfig(1e-5, 1e-6, 1e-2, 0.5, 4.0, 0)
+        noise = torch.randn((self.n, 2, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+
+        def densify():
+            a, o, n_out = self.r.popctl_plan(self.ps, self.ssum, self.scnt, pc)
+            self.r.popctl_apply(self.ps, a, o, n_out, noise)
+        t_pop = self._time(densify, 5)
+        gbs = bytes_adam / (t_adam * 1e-3) / 1e9
+        return {"adam_ms": round(t_adam, 4), "adam_bytes": int(bytes_adam), "adam_gbs": round(gbs, 1),
+                "adam_hbm_frac": round(gbs / hbm_gbs, 4), "regulariser_ms": round(t_reg, 4),
+                "statistic_ms": round(t_stat, 4), "plan_apply_ms": round(t_pop, 4),
+                "peak_note": "HBM copy bandwidth of measured peaks"}
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -187,7 +260,7 @@ def run_ours(args, rank, world):
     ps = pack_scene(sc)
     P = sum(c.n_pixels for c in cams)
     batched = args.workload in BATCHED
-    use_graph = args.graph or batched
+    use_graph = (args.graph or batched) and not args.train
     cfg = L.make_config(tile_size=args.tile, t_min=wl.t_min, timing=not use_graph)
     if args.autotune or batched:
         cfg = r.autotune(ps, cams, cfg, backward=True)
@@ -205,6 +278,7 @@ def run_ours(args, rank, world):
     g_geom = torch.zeros_like(ps.geom)
     g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    train_state = TrainState(r, ps, sc) if args.train else None
 
     def step():
         g_geom.zero_()
@@ -213,6 +287,8 @@ def run_ours(args, rank, world):
         if target is not None:
             r.mse_loss(img, target, dL, loss)
         r.backward(ps, dL, g_geom, g_net)
+        if train_state is not None:
+            train_state.step(g_geom, g_net)
 
     def fwd_only():
         r.forward(ps, cams, cfg, out=img)
@@ -378,6 +454,9 @@ def run_ours(args, rank, world):
     }
     if loss is not None:
         res["loss"] = float(h_loss.item())
+    if train_state is not None:
+        res["config"]["step"] += "+regulariser+statistic+adam"
+        res["train"] = train_state.measure(g_geom, g_net, float(peaks.get("hbm_gbs", 6800.0)))
     if rank == 0 and not args.no_cpu_baseline and (args.workload == WORKLOAD or args.cpu_baseline):
         npx, secs, cores = oracle_sample(wl, args.cpu_tiles)
         res["cpu_baseline"] = {"value": round(npx / secs / 1e6, 6), "unit": "Mpixel/s", "cores": cores,
@@ -424,6 +503,9 @@ def main():
     ap.add_argument("--graph", action="store_true", help="time replays of a captured CUDA graph of the step")
     ap.add_argument("--autotune", action="store_true", help="pick tile size and chunk with snp_autotune first")
     ap.add_argument("--tile", type=int, default=16, choices=(8, 16, 32), help="tile size (without --autotune)")
+    ap.add_argument("--train", action="store_true",
+                    help="add the regulariser, the population-control statistic and an Adam step to every step "
+                         "(eager, no graph) and time each of them alone")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -293,6 +293,115 @@ int64_t snp_kernel_launches(void);
 snp_status snp_mse_loss(snp_context *ctx, const float *image, const float *target, int64_t n, float *dL_dimage,
                         float *loss, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Training-step services around the renderer (Sec. 3.3 Training and
+ * Population Control, Sec. 5.3, App. hyperparameters).  All take device
+ * pointers owned by the caller and run asynchronously on `stream` unless stated.
+ * ------------------------------------------------------------------------ */
+
+/* Population-control statistic (Sec. 3.3, Population Control): the paper densifies
+ * on the gradient magnitude of each primitive's network weights instead of the
+ * screen-space position gradient of 3D Gaussian splatting.  Per primitive i, with
+ * g the network-gradient record of one step (snp_render_backward's grads->net):
+ *   m_i = || (dL/dW1, dL/db1, dL/dw2, dL/db2 [, dL/dW_t]) ||_2   (the density network)
+ * and, where m_i > 0 (the primitive received gradient in this step),
+ *   stat_sum[i] += m_i,  stat_count[i] += 1.
+ *   g_net       device float32 [n][stride], read
+ *   stat_sum    device float32 [n], stat_count device int32 [n]: accumulated into
+ *               (zero both to start a densification window)
+ * No allocation, no host synchronisation (capturable).  SNP_ERR_INVALID_ARG for a
+ * null pointer with n > 0. */
+snp_status snp_popctl_accumulate(snp_context *ctx, const snp_scene_desc *desc, const float *g_net, float *stat_sum,
+                                 int32_t *stat_count, void *stream);
+
+/* Thresholds of the population-control decision.  The paper's values (App.
+ * hyperparameters): grad_threshold 1e-4 (real scenes) or 1e-5 (synthetic scenes),
+ * prune_threshold 2e-6 or 1e-6, grow_scale 1e-2, prune_scale 0.5. */
+typedef struct {
+    float grad_threshold;  /* densify where stat_sum >= grad_threshold * stat_count (count > 0) */
+    float prune_threshold; /* prune where stat_sum < prune_threshold * stat_count, or count == 0 */
+    float grow_scale;      /* densified primitives with max(s) <= grow_scale * extent are cloned, others split */
+    float prune_scale;     /* primitives with max(s) > prune_scale * extent are pruned */
+    float extent;          /* scene extent in world units (> 0) */
+    int32_t reserved_;
+} snp_popctl_config;
+
+enum { SNP_POP_PRUNE = 0, SNP_POP_KEEP = 1, SNP_POP_CLONE = 2, SNP_POP_SPLIT = 3 };
+
+/* Decide per primitive, first rule that applies (l = max of the three log-scales):
+ *   l > ln(prune_scale * extent)                      -> SNP_POP_PRUNE
+ *   count > 0 and sum >= grad_threshold * count       -> SNP_POP_CLONE if l <= ln(grow_scale * extent),
+ *                                                        else SNP_POP_SPLIT
+ *   count == 0 or sum < prune_threshold * count       -> SNP_POP_PRUNE
+ *   otherwise                                         -> SNP_POP_KEEP
+ * Comparisons and the two products in float32; the two logarithms are evaluated in
+ * double on the host and rounded to float32.  Outputs (device, caller-owned):
+ *   action      int32 [n]
+ *   out_offset  uint32 [n]: first output row of primitive i, the exclusive scan of
+ *               its output count (PRUNE 0, KEEP 1, CLONE 2, SPLIT 2)
+ *   n_out       host int64: number of output rows (the call synchronises `stream`)
+ * Errors: SNP_ERR_INVALID_ARG for null pointers or extent <= 0. */
+snp_status snp_popctl_plan(snp_context *ctx, const snp_scene_desc *desc, const float *geom, const float *stat_sum,
+                           const int32_t *stat_count, const snp_popctl_config *cfg, int32_t *action,
+                           uint32_t *out_offset, int64_t *n_out, void *stream);
+
+/* Write the new scene of a plan: rows out_offset[i].. of geom_out / net_out receive
+ * primitive i's outputs, so survivors keep their order.
+ *   KEEP   one copy;  CLONE  two copies (3D Gaussian splatting's clone: the optimiser
+ *          moves them apart);
+ *   SPLIT  two children j = 0, 1 centred at c + R(q) diag(s) eps_j with log-scales
+ *          log s - fl(ln 1.6) per axis (float32 subtraction), all else copied;
+ *   PRUNE  nothing.
+ *   noise     device float32 [n][2][3]: standard normal eps_0, eps_1 per primitive
+ *             (the library draws no random numbers)
+ *   geom_out  device float32 [n_out][16], net_out device [n_out][stride] of the
+ *             scene's weight_dtype; must not overlap the inputs.
+ * Network rows are copied bit for bit.  The caller resets its optimiser moments and
+ * statistics for the new rows.  Asynchronous, no allocation. */
+snp_status snp_popctl_apply(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
+                            const int32_t *action, const uint32_t *out_offset, const float *noise, float *geom_out,
+                            void *net_out, void *stream);
+
+/* Geometry regulariser (Sec. 3.3 Training; Sec. 5.3): penalises anisotropic
+ * primitives through the standard deviation of the components of each scale vector
+ * s = exp(log s):
+ *   L_reg = weight * (1/n) sum_i std(s_i),  std(s) = sqrt((1/3) sum_a (s_a - mean(s))^2),
+ * and adds dL_reg/dlog s_a = (weight / n) s_a (s_a - mean(s)) / (3 std(s)) (0 where
+ * std(s) = 0) into the log-scale columns of g_geom [n][16].
+ *   loss  device float32, overwritten (FP64 block sums added in a fixed order)
+ * Shares the context's reduction slots with snp_mse_loss: do not run the two at once
+ * on different streams.  No allocation (capturable).  n = 0 writes loss = 0. */
+snp_status snp_geom_reg(snp_context *ctx, const snp_scene_desc *desc, const float *geom, float weight,
+                        float *g_geom, float *loss, void *stream);
+
+/* One Adam step (Kingma and Ba, Algorithm 1; the paper trains with Adam and gives
+ * per-group learning rates, App. hyperparameters), per element:
+ *   m = beta1 m + (1 - beta1) g,   v = beta2 v + (1 - beta2) g^2,
+ *   p = p - lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ *   lr_geom  per geometry column group: centres (0-2), log-scales (3-5),
+ *            quaternions (6-9), constant rgb (10-12); columns 13-15 untouched
+ *   lr_net   per snp_net_layout field (index as off[]); padding elements are updated
+ *            with their field's rate and, with zero gradient and moments, stay put
+ *   step     t >= 1; the bias corrections 1 / (1 - beta^t) are evaluated in double on
+ *            the host and rounded to float32 */
+typedef struct {
+    float lr_geom[4];
+    float lr_net[14];
+    float beta1, beta2, eps;
+    int32_t step;
+} snp_adam_config;
+
+/*   geom, m_geom, v_geom        device float32 [n][16] (updated); grads->geom read
+ *   net                         device [n][stride] of weight_dtype (updated)
+ *   net_master                  float32 [n][stride] master weights: required with
+ *                               SNP_BF16 (updated, then rounded to nearest even into
+ *                               net), NULL with SNP_F32 (net updated in place)
+ *   m_net, v_net                device float32 [n][stride] (updated); grads->net read
+ * A group whose gradient pointer is NULL is skipped.  Asynchronous, no allocation. */
+snp_status snp_adam_step(snp_context *ctx, const snp_scene_desc *desc, float *geom, void *net, float *net_master,
+                         const snp_grad_ptrs *grads, float *m_geom, float *v_geom, float *m_net, float *v_net,
+                         const snp_adam_config *cfg, void *stream);
+
 /* Allocation-free sort (the paper has no counterpart: this is a library
  * service).  Sorts n (key, value) pairs in place by the low key_bits bits of the
  * key, stably (equal keys keep their input order) -- the same LSD radix sort

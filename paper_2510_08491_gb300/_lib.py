@@ -63,6 +63,18 @@ class Stats(C.Structure):
                 ("n_candidates", C.c_int64), ("n_hits", C.c_int64), ("n_composited", C.c_int64)]
 
 
+class PopctlConfig(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("prune_threshold", C.c_float), ("grow_scale", C.c_float),
+                ("prune_scale", C.c_float), ("extent", C.c_float), ("reserved_", C.c_int32)]
+
+
+class AdamConfig(C.Structure):
+    _fields_ = [("lr_geom", C.c_float * 4), ("lr_net", C.c_float * 14), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("step", C.c_int32)]
+
+
+POP_PRUNE, POP_KEEP, POP_CLONE, POP_SPLIT = 0, 1, 2, 3
+
 _lib = None
 
 _SIGS = {
@@ -82,6 +94,14 @@ _SIGS = {
     "snp_autotune": [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(ScenePtrs), C.POINTER(Camera), C.c_int32,
                      C.POINTER(Config), C.c_int32, C.POINTER(Config), C.POINTER(C.c_float), C.c_void_p],
     "snp_mse_loss": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "snp_popctl_accumulate": [C.c_void_p, C.POINTER(SceneDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "snp_popctl_plan": [C.c_void_p, C.POINTER(SceneDesc), C.c_void_p, C.c_void_p, C.c_void_p,
+                        C.POINTER(PopctlConfig), C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p],
+    "snp_popctl_apply": [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(ScenePtrs), C.c_void_p, C.c_void_p,
+                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "snp_geom_reg": [C.c_void_p, C.POINTER(SceneDesc), C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p],
+    "snp_adam_step": [C.c_void_p, C.POINTER(SceneDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GradPtrs),
+                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdamConfig), C.c_void_p],
 }
 FLAG_STAGE_TIMING = 1
 FLAG_LENGTH_QUEUE = 2

@@ -140,6 +140,8 @@ struct snp_context {
         cmask;
     // loss reduction: kLossSlots FP64 block sums, then the completion counter
     Buf loss_part;
+    // population-control plan: per-primitive output counts, scan scratch, total
+    Buf pop_cnt, pop_tmp, pop_total;
     // pinned host staging
     View *h_views = nullptr;
     uint32_t *h_small = nullptr;
@@ -363,7 +365,7 @@ void snp_destroy(snp_context *ctx)
                    &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
                    &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0,
                    &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan,
-                   &ctx->npack, &ctx->cmask, &ctx->loss_part};
+                   &ctx->npack, &ctx->cmask, &ctx->loss_part, &ctx->pop_cnt, &ctx->pop_tmp, &ctx->pop_total};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_views) cudaFreeHost(ctx->h_views);
@@ -851,3 +853,181 @@ snp_status snp_debug_keys(snp_context *ctx, int64_t token, uint64_t *keys_host, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ training-step services
+
+// Growth of the population-control scratch: an offline call, allowed on a
+// reserved context too (it synchronises anyway).
+static snp_status ensure_offline(snp_context *ctx, Buf &b, size_t bytes, const char *name)
+{
+    const bool r = ctx->reserved;
+    ctx->reserved = false;
+    const snp_status s = ensure(ctx, b, bytes, name);
+    ctx->reserved = r;
+    return s;
+}
+
+snp_status snp_popctl_accumulate(snp_context *ctx, const snp_scene_desc *desc, const float *g_net, float *stat_sum,
+                                 int32_t *stat_count, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    const int64_t n = desc->n;
+    if (n > 0 && (!g_net || !stat_sum || !stat_count)) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    CK(cudaSetDevice(ctx->device));
+    snp_net_layout L;
+    layout_of(*desc, L);
+    PopFields f{};
+    const int ns = desc->n_sigma;
+    const int sizes[5] = {3 * ns, ns, ns, 1, ns};
+    const int idx[5] = {0, 1, 2, 3, 12};
+    for (int k = 0; k < 5; ++k)
+        if (L.off[idx[k]] >= 0) {
+            f.off[f.count] = L.off[idx[k]];
+            f.size[f.count] = sizes[k];
+            ++f.count;
+        }
+    f.stride = L.stride;
+    if ((s = launch_popctl_stat(g_net, n, f, stat_sum, stat_count, (cudaStream_t)stream)) != SNP_OK)
+        return fail(ctx, s, "statistic launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return SNP_OK;
+}
+
+snp_status snp_popctl_plan(snp_context *ctx, const snp_scene_desc *desc, const float *geom, const float *stat_sum,
+                           const int32_t *stat_count, const snp_popctl_config *cfg, int32_t *action,
+                           uint32_t *out_offset, int64_t *n_out, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    const int64_t n = desc->n;
+    if (!cfg || !n_out || (n > 0 && (!geom || !stat_sum || !stat_count || !action || !out_offset)))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    if (!(cfg->extent > 0.0f) || !(cfg->grow_scale > 0.0f) || !(cfg->prune_scale > 0.0f))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "extent, grow_scale and prune_scale must be > 0");
+    *n_out = 0;
+    if (n == 0) return SNP_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = ensure_offline(ctx, ctx->pop_cnt, (size_t)n * 4, "pop_cnt")) != SNP_OK) return s;
+    if ((s = ensure_offline(ctx, ctx->pop_tmp, (size_t)scan_temp_words(n) * 4, "pop_tmp")) != SNP_OK) return s;
+    if ((s = ensure_offline(ctx, ctx->pop_total, 16, "pop_total")) != SNP_OK) return s;
+    PopThresholds t;
+    t.grad = cfg->grad_threshold;
+    t.prune = cfg->prune_threshold;
+    t.log_grow = (float)log((double)cfg->grow_scale * (double)cfg->extent);
+    t.log_prune = (float)log((double)cfg->prune_scale * (double)cfg->extent);
+    if ((s = launch_popctl_plan(geom, n, stat_sum, stat_count, t, action, (uint32_t *)ctx->pop_cnt.p, st)) != SNP_OK)
+        return fail(ctx, s, "plan launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    scan_u32((const uint32_t *)ctx->pop_cnt.p, out_offset, n, (uint32_t *)ctx->pop_total.p,
+             (uint32_t *)ctx->pop_tmp.p, st);
+    CK(cudaGetLastError());
+    uint32_t total = 0;
+    CK(cudaMemcpyAsync(&total, ctx->pop_total.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *n_out = total;
+    return SNP_OK;
+}
+
+snp_status snp_popctl_apply(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
+                            const int32_t *action, const uint32_t *out_offset, const float *noise, float *geom_out,
+                            void *net_out, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    const int64_t n = desc->n;
+    if (n == 0) return SNP_OK;
+    if (!scene || !scene->geom || !scene->net || !action || !out_offset || !noise || !geom_out || !net_out)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    if ((((uintptr_t)scene->net) | ((uintptr_t)net_out)) & 15u)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "network arrays must be 16-byte aligned");
+    CK(cudaSetDevice(ctx->device));
+    snp_net_layout L;
+    layout_of(*desc, L);
+    const int row_bytes = L.stride * (desc->weight_dtype == SNP_BF16 ? 2 : 4);
+    if ((s = launch_popctl_apply(scene->geom, scene->net, n, row_bytes, action, out_offset, noise,
+                                 (float)log(1.6), geom_out, net_out, (cudaStream_t)stream)) != SNP_OK)
+        return fail(ctx, s, "apply launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return SNP_OK;
+}
+
+snp_status snp_geom_reg(snp_context *ctx, const snp_scene_desc *desc, const float *geom, float weight,
+                        float *g_geom, float *loss, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    const int64_t n = desc->n;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!loss || (n > 0 && !geom)) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    CK(cudaSetDevice(ctx->device));
+    if (n == 0) {
+        CK(cudaMemsetAsync(loss, 0, sizeof(float), st));
+        return SNP_OK;
+    }
+    double *part = (double *)ctx->loss_part.p;
+    unsigned *counter = (unsigned *)(part + kLossSlots);
+    if ((s = launch_geom_reg(geom, n, (float)((double)weight / (double)n), g_geom, loss, part, counter, kLossSlots,
+                             st)) != SNP_OK)
+        return fail(ctx, s, "regulariser launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return SNP_OK;
+}
+
+snp_status snp_adam_step(snp_context *ctx, const snp_scene_desc *desc, float *geom, void *net, float *net_master,
+                         const snp_grad_ptrs *grads, float *m_geom, float *v_geom, float *m_net, float *v_net,
+                         const snp_adam_config *cfg, void *stream)
+{
+    if (!ctx) return SNP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    snp_status s;
+    if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
+    if (!cfg || !grads) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    if (cfg->step < 1) return fail(ctx, SNP_ERR_INVALID_ARG, "step must be >= 1, got %d", cfg->step);
+    if (!(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) ||
+        !(cfg->eps > 0.0f))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "need 0 <= beta < 1 and eps > 0");
+    const int64_t n = desc->n;
+    if (n == 0) return SNP_OK;
+    const bool bf16 = desc->weight_dtype == SNP_BF16;
+    if (grads->geom && (!geom || !m_geom || !v_geom)) return fail(ctx, SNP_ERR_INVALID_ARG, "null geometry array");
+    if (grads->net && (!net || !m_net || !v_net || (bf16 && !net_master)))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "null network array (BF16 weights need the FP32 master copy)");
+    if (grads->net && ((((uintptr_t)net) | ((uintptr_t)grads->net) | ((uintptr_t)m_net) | ((uintptr_t)v_net) |
+                        ((uintptr_t)(bf16 ? (void *)net_master : net))) & 15u))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "network arrays must be 16-byte aligned");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    AdamConsts c;
+    c.beta1 = cfg->beta1;
+    c.beta2 = cfg->beta2;
+    c.one_m_beta1 = (float)(1.0 - (double)cfg->beta1);
+    c.one_m_beta2 = (float)(1.0 - (double)cfg->beta2);
+    c.corr1 = (float)(1.0 / (1.0 - pow((double)cfg->beta1, (double)cfg->step)));
+    c.corr2 = (float)(1.0 / (1.0 - pow((double)cfg->beta2, (double)cfg->step)));
+    c.eps = cfg->eps;
+    if (grads->geom && (s = launch_adam_geom(geom, grads->geom, m_geom, v_geom, n, cfg->lr_geom, c, st)) != SNP_OK)
+        return fail(ctx, s, "Adam launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (grads->net) {
+        snp_net_layout L;
+        layout_of(*desc, L);
+        const int ns = desc->n_sigma, nc = desc->n_c;
+        const int sizes[14] = {3 * ns, ns, ns, 1, kFeat, nc * (3 + kFeat), nc, nc * nc, nc, 3 * nc, 3, 48, ns, 36};
+        AdamNetFields f;
+        for (int k = 0; k < 14; ++k) {
+            f.off[k] = L.off[k];
+            f.end[k] = L.off[k] >= 0 ? L.off[k] + sizes[k] : -1;
+            f.lr[k] = cfg->lr_net[k];
+        }
+        f.stride = L.stride;
+        float *P = bf16 ? net_master : (float *)net;
+        if ((s = launch_adam_net(P, bf16 ? net : nullptr, grads->net, m_net, v_net, n, f, c, st)) != SNP_OK)
+            return fail(ctx, s, "Adam launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    return SNP_OK;
+}

@@ -84,6 +84,36 @@ void launch_sh_bwd(const float *geom, const void *net, int bf16, int64_t n, cons
                    int off_sh, int off_sht, int stride, const float *rec, const float *g_view, float *g_net,
                    float *g_geom, cudaStream_t st);
 
+// snp_train.cu
+struct PopFields {       // density-network fields of the gradient record
+    int32_t off[5], size[5];
+    int32_t count, stride;
+};
+struct PopThresholds {   // float32 forms of the population-control thresholds
+    float grad, prune, log_grow, log_prune;
+};
+struct AdamConsts {
+    float beta1, beta2, one_m_beta1, one_m_beta2, corr1, corr2, eps;
+};
+struct AdamNetFields {   // [off, end) and rate per snp_net_layout field (off < 0: absent)
+    int32_t off[14], end[14];
+    float lr[14];
+    int32_t stride;
+};
+snp_status launch_popctl_stat(const float *g_net, int64_t n, const PopFields &f, float *sum, int32_t *count,
+                              cudaStream_t st);
+snp_status launch_popctl_plan(const float *geom, int64_t n, const float *sum, const int32_t *count,
+                              const PopThresholds &t, int32_t *action, uint32_t *outs, cudaStream_t st);
+snp_status launch_popctl_apply(const float *geom, const void *net, int64_t n, int row_bytes, const int32_t *action,
+                               const uint32_t *off, const float *noise, float log_shrink, float *geom_out,
+                               void *net_out, cudaStream_t st);
+snp_status launch_geom_reg(const float *geom, int64_t n, float scale, float *g_geom, float *loss, double *part,
+                           unsigned *counter, int max_blocks, cudaStream_t st);
+snp_status launch_adam_geom(float *p, const float *g, float *m, float *v, int64_t n, const float lr[4],
+                            const AdamConsts &c, cudaStream_t st);
+snp_status launch_adam_net(float *p, void *pb, const float *g, float *m, float *v, int64_t n,
+                           const AdamNetFields &f, const AdamConsts &c, cudaStream_t st);
+
 // snp_loss.cu
 constexpr int kLossSlots = 1024;
 snp_status launch_mse_loss(const float *img, const float *tgt, int64_t n, float *dL, float *loss, double *part,

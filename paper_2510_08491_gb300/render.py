@@ -140,6 +140,64 @@ class Renderer:
                                             C.c_void_p(st)))
         return loss, dL
 
+    # ------------------------------------------------------------ training-step services
+
+    def _st(self, stream=None) -> C.c_void_p:
+        return C.c_void_p((stream or torch.cuda.current_stream(self.device)).cuda_stream)
+
+    def popctl_accumulate(self, ps: PackedScene, g_net: torch.Tensor, stat_sum: torch.Tensor,
+                          stat_count: torch.Tensor, stream=None):
+        """Add this step's density-network gradient norm per primitive (snp_popctl_accumulate)."""
+        self.ctx.check(L.lib().snp_popctl_accumulate(self.ctx.handle, C.byref(ps.desc), C.c_void_p(g_net.data_ptr()),
+                                                     C.c_void_p(stat_sum.data_ptr()),
+                                                     C.c_void_p(stat_count.data_ptr()), self._st(stream)))
+
+    def popctl_plan(self, ps: PackedScene, stat_sum: torch.Tensor, stat_count: torch.Tensor, cfg: L.PopctlConfig,
+                    stream=None):
+        """Per-primitive actions and output offsets (snp_popctl_plan); returns (action, offset, n_out)."""
+        n = ps.n
+        action = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        offset = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)  # uint32 bits
+        n_out = C.c_int64(0)
+        self.ctx.check(L.lib().snp_popctl_plan(self.ctx.handle, C.byref(ps.desc), C.c_void_p(ps.geom.data_ptr()),
+                                               C.c_void_p(stat_sum.data_ptr()), C.c_void_p(stat_count.data_ptr()),
+                                               C.byref(cfg), C.c_void_p(action.data_ptr()),
+                                               C.c_void_p(offset.data_ptr()), C.byref(n_out), self._st(stream)))
+        return action[:n], offset[:n], int(n_out.value)
+
+    def popctl_apply(self, ps: PackedScene, action: torch.Tensor, offset: torch.Tensor, n_out: int,
+                     noise: torch.Tensor, stream=None) -> PackedScene:
+        """The new scene of a plan (snp_popctl_apply); noise is float32 [n, 2, 3] standard normal."""
+        geom = torch.empty((max(n_out, 1), L.GEOM_STRIDE), dtype=torch.float32, device=self.device)
+        net = torch.empty((max(n_out, 1), ps.stride), dtype=ps.net.dtype, device=self.device)
+        self.ctx.check(L.lib().snp_popctl_apply(self.ctx.handle, C.byref(ps.desc), C.byref(ps.ptrs()),
+                                                C.c_void_p(action.data_ptr()), C.c_void_p(offset.data_ptr()),
+                                                C.c_void_p(noise.data_ptr()), C.c_void_p(geom.data_ptr()),
+                                                C.c_void_p(net.data_ptr()), self._st(stream)))
+        d = L.SceneDesc(n_out, ps.desc.n_sigma, ps.desc.color_mode, ps.desc.n_c, ps.desc.weight_dtype,
+                        ps.desc.omega0, ps.desc.dynamic)
+        return PackedScene(d, geom[:n_out], net[:n_out], ps.offsets, ps.stride)
+
+    def geom_reg(self, ps: PackedScene, weight: float, g_geom: Optional[torch.Tensor],
+                 loss: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Anisotropy regulariser (snp_geom_reg): returns the loss [1]; adds its gradient into g_geom."""
+        loss = torch.empty(1, dtype=torch.float32, device=self.device) if loss is None else loss
+        self.ctx.check(L.lib().snp_geom_reg(self.ctx.handle, C.byref(ps.desc), C.c_void_p(ps.geom.data_ptr()),
+                                            float(weight), C.c_void_p(g_geom.data_ptr() if g_geom is not None else None),
+                                            C.c_void_p(loss.data_ptr()), self._st(stream)))
+        return loss
+
+    def adam_step(self, ps: PackedScene, g_geom, g_net, m_geom, v_geom, m_net, v_net, cfg: L.AdamConfig,
+                  net_master: Optional[torch.Tensor] = None, stream=None):
+        """One fused Adam step over the geometry and network arrays (snp_adam_step)."""
+        def ptr(t):
+            return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p()
+        g = L.GradPtrs(g_geom.data_ptr() if g_geom is not None else None,
+                       g_net.data_ptr() if g_net is not None else None)
+        self.ctx.check(L.lib().snp_adam_step(self.ctx.handle, C.byref(ps.desc), ptr(ps.geom), ptr(ps.net),
+                                             ptr(net_master), C.byref(g), ptr(m_geom), ptr(v_geom), ptr(m_net),
+                                             ptr(v_net), C.byref(cfg), self._st(stream)))
+
     def stats(self, token: Optional[int] = None) -> L.Stats:
         s = L.Stats()
         st = torch.cuda.current_stream(self.device).cuda_stream
