@@ -261,10 +261,10 @@ def run_ours(args, rank, world):
     P = sum(c.n_pixels for c in cams)
     batched = args.workload in BATCHED
     use_graph = (args.graph or batched) and not args.train
-    cfg = L.make_config(tile_size=args.tile, t_min=wl.t_min, timing=not use_graph)
+    cfg = L.make_config(tile_size=args.tile, t_min=wl.t_min, timing=not use_graph, replay_color=args.replay_color)
     if args.autotune or batched:
         cfg = r.autotune(ps, cams, cfg, backward=True)
-        cfg.flags = L.FLAG_STAGE_TIMING if not use_graph else 0
+        cfg.flags = (L.FLAG_STAGE_TIMING if not use_graph else 0) | (L.FLAG_REPLAY_COLOR if args.replay_color else 0)
     img = torch.empty((P, 3), device="cuda", dtype=torch.float32)
     target = None
     if wl.target_scene is not None:
@@ -337,7 +337,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         launches = L.kernel_launches() - l0
         # per-kernel device times from eager steps with stage timing (same kernels, same config)
-        cfg.flags = L.FLAG_STAGE_TIMING
+        cfg.flags = L.FLAG_STAGE_TIMING | (L.FLAG_REPLAY_COLOR if args.replay_color else 0)
         r.ctx.stage_times(reset=True)
         for _ in range(max(min(args.steps, 5), 2)):
             step()
@@ -435,6 +435,7 @@ def run_ours(args, rank, world):
                    "tile": int(cfg.tile_size), "chunk": int(cfg.chunk),
                    "step": "forward+loss+backward" if target is not None else "forward+backward",
                    "graph": graph is not None, "autotuned": bool(args.autotune or batched),
+                   "colour_store": sc.color == "mlp" and not args.replay_color,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (network weights %.2f GB)" % (h_net.numel() * h_net.element_size()
                                                                               / 1e9)},
@@ -503,6 +504,8 @@ def main():
     ap.add_argument("--graph", action="store_true", help="time replays of a captured CUDA graph of the step")
     ap.add_argument("--autotune", action="store_true", help="pick tile size and chunk with snp_autotune first")
     ap.add_argument("--tile", type=int, default=16, choices=(8, 16, 32), help="tile size (without --autotune)")
+    ap.add_argument("--replay-color", action="store_true",
+                    help="keep no colour store: the backward evaluates the colour network again")
     ap.add_argument("--train", action="store_true",
                     help="add the regulariser, the population-control statistic and an Adam step to every step "
                          "(eager, no graph) and time each of them alone")

@@ -173,6 +173,13 @@ typedef struct {
  * decreasing list length instead of row-major order (trades L2 reuse of
  * primitive records between neighbouring tiles for a shorter tail). */
 #define SNP_FLAG_LENGTH_QUEUE 2
+/* snp_config.flags: keep no colour store.  By default a forward of a colour-MLP
+ * scene saves the colour and alpha_hat of every composited pair (16 bytes per pair,
+ * in a context buffer sized from the previous forward's count) so that the backward
+ * does not evaluate the colour network again; with this flag the backward
+ * recomputes them (less device memory, slower backward).  Pairs that do not fit the
+ * buffer are recomputed either way. */
+#define SNP_FLAG_REPLAY_COLOR 4
 
 /* Stages reported by snp_stage_times. */
 enum {

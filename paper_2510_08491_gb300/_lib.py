@@ -105,6 +105,7 @@ _SIGS = {
 }
 FLAG_STAGE_TIMING = 1
 FLAG_LENGTH_QUEUE = 2
+FLAG_REPLAY_COLOR = 4
 STAGES = ("project", "scan", "emit", "sort", "ranges", "raster_fwd", "raster_bwd", "post_bwd")
 
 
@@ -162,10 +163,11 @@ def make_cameras(cams):
 
 
 def make_config(tile_size=16, chunk=0, form=FORM_STABLE, t_min=1e-4, bg=(0.0, 0.0, 0.0), timing=False,
-                length_queue=False) -> Config:
+                length_queue=False, replay_color=False) -> Config:
     cfg = Config()
     cfg.tile_size, cfg.chunk, cfg.integral_form = int(tile_size), int(chunk), int(form)
-    cfg.flags = (FLAG_STAGE_TIMING if timing else 0) | (FLAG_LENGTH_QUEUE if length_queue else 0)
+    cfg.flags = (FLAG_STAGE_TIMING if timing else 0) | (FLAG_LENGTH_QUEUE if length_queue else 0) | \
+        (FLAG_REPLAY_COLOR if replay_color else 0)
     cfg.t_min = float(t_min)
     cfg.bg[:] = [float(b) for b in bg]
     return cfg

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -142,6 +143,11 @@ struct snp_context {
     Buf loss_part;
     // population-control plan: per-primitive output counts, scan scratch, total
     Buf pop_cnt, pop_tmp, pop_total;
+    // colour store of the latest forward (colour-MLP scenes) and its per-key offsets
+    Buf colstore, key_off;
+    bool col_on = false;       // the latest forward wrote the store
+    int64_t last_comp = 0;     // composited pairs of the previous forward (sizes the store)
+    bool fwd_done = false;     // the stats buffer holds a finished forward's counters
     // pinned host staging
     View *h_views = nullptr;
     uint32_t *h_small = nullptr;
@@ -166,7 +172,7 @@ struct snp_context {
 
 // Offsets inside the small device buffer.
 constexpr size_t kSmallTotal = 0, kSmallFlags = 16, kSmallTiles = 32, kSmallWork = 48, kSmallNsort = 64,
-                 kSmallBytes = 256;
+                 kSmallColCount = 128, kSmallBytes = 256;
 
 #define STAGE_BEGIN(k) \
     if (ctx->timing) ctx->timer.begin((k), st)
@@ -365,7 +371,8 @@ void snp_destroy(snp_context *ctx)
                    &ctx->vals, &ctx->keys_alt, &ctx->vals_alt, &ctx->hist, &ctx->hist_scan, &ctx->ranges,
                    &ctx->px_state, &ctx->px_nwalk, &ctx->stats, &ctx->small, &ctx->g_view, &ctx->g_h0,
                    &ctx->qkeys, &ctx->qvals, &ctx->qkeys_alt, &ctx->qvals_alt, &ctx->qhist, &ctx->qhist_scan,
-                   &ctx->npack, &ctx->cmask, &ctx->loss_part, &ctx->pop_cnt, &ctx->pop_tmp, &ctx->pop_total};
+                   &ctx->npack, &ctx->cmask, &ctx->loss_part, &ctx->pop_cnt, &ctx->pop_tmp, &ctx->pop_total,
+                   &ctx->colstore, &ctx->key_off};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_views) cudaFreeHost(ctx->h_views);
@@ -381,6 +388,7 @@ static snp_status ensure_keys(snp_context *ctx, int64_t K, int ts)
 {
     ENS(keys, (size_t)K * 8);
     ENS(cmask, (size_t)K * (ts * ts / 32) * 4);
+    ENS(key_off, (size_t)K * 4);
     ENS(keys_alt, (size_t)K * 8);
     ENS(vals, (size_t)K * 4);
     ENS(vals_alt, (size_t)K * 4);
@@ -412,6 +420,18 @@ static snp_status ensure_frame(snp_context *ctx, int64_t n, int n_views, int64_t
     ENS(qhist_scan, (size_t)sort_hist_words(tiles) * 4);
     ENS(npack, (size_t)n * raster_npack_stride(d->color_mode, d->n_c, d->n_sigma) * 4);
     return SNP_OK;
+}
+
+// Colour-store capacity (pairs) for K keys: the previous forward's composited count
+// plus a quarter, else 16 per key, plus the partly used blocks of the forward CTAs;
+// at most every (key, pixel) pair and 2^32 - 2.
+static int64_t col_pairs_wanted(const snp_context *ctx, int64_t K, int ts)
+{
+    int64_t want = ctx->last_comp > 0 ? ctx->last_comp + ctx->last_comp / 4 : K * 16;
+    want += (int64_t)4 * 152 * kColBlock;
+    want = std::max<int64_t>(want, (int64_t)1 << 16);
+    want = std::min<int64_t>(want, std::max<int64_t>(K, 1) * ts * ts);
+    return std::min<int64_t>(want, (int64_t)0xfffffffe);
 }
 
 static snp_status ensure_scan_tmp(snp_context *ctx, int64_t vn, int64_t key_bound, int64_t tiles)
@@ -455,6 +475,8 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
         ENS(g_view, (size_t)desc->n * n_cams * kGvFloats * 4);
         ENS(g_h0, (size_t)desc->n * nc * 4);
     }
+    if (desc->color_mode == SNP_COLOR_MLP && !(cfg && (cfg->flags & SNP_FLAG_REPLAY_COLOR)))
+        ENS(colstore, (size_t)col_pairs_wanted(ctx, max_keys, ts) * 16);
     ctx->key_cap = max_keys;
     ctx->reserved = true;
     return SNP_OK;
@@ -558,7 +580,14 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     STAGE_END();
     if (!ctx->reserved) {
         CK(cudaMemcpyAsync(ctx->h_small, d_total, 4, cudaMemcpyDeviceToHost, st));
+        if (ctx->fwd_done)  // the previous forward's composited count sizes the colour store
+            CK(cudaMemcpyAsync(ctx->h_small + 8, (char *)ctx->stats.p + 16, 8, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (ctx->fwd_done) {
+            uint64_t comp;
+            memcpy(&comp, ctx->h_small + 8, 8);
+            ctx->last_comp = (int64_t)comp;
+        }
         key_bound = ctx->h_small[0];
         if ((s = ensure_keys(ctx, key_bound, ts)) != SNP_OK) return s;
         if ((s = ensure_scan_tmp(ctx, vn, key_bound, tiles)) != SNP_OK) return s;
@@ -608,9 +637,27 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
                   ? (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p)
                   : nullptr;
     CK(cudaMemsetAsync(d_work, 0, 4, st));
+    ctx->col_on = desc->color_mode == SNP_COLOR_MLP && !(c.flags & SNP_FLAG_REPLAY_COLOR);
+    if (ctx->col_on && !ctx->reserved &&
+        ensure(ctx, ctx->colstore, (size_t)col_pairs_wanted(ctx, key_bound, ts) * 16, "colstore") != SNP_OK) {
+        // no room for the store: the backward recomputes the colours instead
+        cudaGetLastError();
+        ctx->err[0] = 0;
+        ctx->col_on = false;
+    }
+    if (ctx->col_on) ctx->col_on = ctx->colstore.bytes >= 16;
+    if (ctx->col_on) {
+        unsigned long long *d_col = (unsigned long long *)((char *)ctx->small.p + kSmallColCount);
+        CK(cudaMemsetAsync(d_col, 0, 8, st));
+        a.colstore = (float4 *)ctx->colstore.p;
+        a.key_off = (uint32_t *)ctx->key_off.p;
+        a.col_count = d_col;
+        a.col_cap = (uint32_t)std::min<size_t>(ctx->colstore.bytes / 16, (size_t)0xfffffffe);
+    }
     STAGE_BEGIN(SNP_STAGE_RASTER_FWD);
     s = launch_raster_fwd(a, desc->color_mode, desc->n_c, c.integral_form, desc->weight_dtype == SNP_BF16, ts, st);
     STAGE_END();
+    ctx->fwd_done = true;
     if (s != SNP_OK) return fail(ctx, s, "raster forward launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     CK(cudaGetLastError());
     if (token) *token = ctx->token;
@@ -643,6 +690,10 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     const uint32_t *svals = (const uint32_t *)(ctx->keys_in_alt ? ctx->vals_alt.p : ctx->vals.p);
     RasterArgs a;
     fill_args(a, ctx, desc, scene, svals);
+    if (ctx->col_on) {
+        a.colstore = (float4 *)ctx->colstore.p;
+        a.key_off = (uint32_t *)ctx->key_off.p;
+    }
     a.px_state = (float4 *)ctx->px_state.p;
     a.px_nwalk = (uint32_t *)ctx->px_nwalk.p;
     a.dL_dimage = dL_dimages;

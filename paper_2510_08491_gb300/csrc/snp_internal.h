@@ -71,7 +71,19 @@ struct RasterArgs {
     // per-primitive network blocks in the staged shared-memory layout (k_pack_net)
     float *npack;             // [n][npack_stride]
     int32_t npack_stride;     // floats per primitive
+    // colour store (colour-MLP scenes): the forward writes (colour, alpha_hat) of every
+    // composited pair, per key in the order of its composited-mask bits, so that the
+    // backward reads them instead of evaluating the colour network again.  NULL: off.
+    float4 *colstore;         // [col_cap]
+    uint32_t *key_off;        // [K] first colstore index of each key's pairs (kNoStore: not stored)
+    unsigned long long *col_count;  // bump allocator of the forward (zeroed before it)
+    uint32_t col_cap;         // capacity in pairs
 };
+
+constexpr uint32_t kNoStore = 0xffffffffu;
+// Pairs a forward CTA takes from the colour store at a time (it hands out slices of
+// the block to its chunks, so that the global allocator is touched once per block).
+constexpr uint32_t kColBlock = 8192;
 
 // snp_raster_*.cu
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,

@@ -483,10 +483,10 @@ __device__ __forceinline__ int acc_unit(int m, int t) { return 8 * (m >> 1) + 2 
 
 // Colour of the composited pairs at positions r0 .. r0+15 of an entry's list
 // (n entries; list holds pixel slots).  Channel c of the pair at slot q goes to
-// out[c * plane + q].
+// out[q * qs + c * plane].
 template <int NC, bool BF16>
 __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s_ray, const uint16_t *list, int r0,
-                                                int n, float *out, int plane)
+                                                int n, float *out, int qs, int plane)
 {
     const int lane = threadIdx.x & 31, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
@@ -530,7 +530,7 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
     }
     const bool v = t == 0 ? pr.v0 : pr.v1;
     if (t < 2 && v) {
-        const int q = t == 0 ? pr.pix0 : pr.pix1, o = 3 * t;
+        const int q = (t == 0 ? pr.pix0 : pr.pix1) * qs, o = 3 * t;
         out[q] = sigmoidf_fast(c[o + 0] + B3.x);
         out[plane + q] = sigmoidf_fast(c[o + 1] + B3.y);
         out[2 * plane + q] = sigmoidf_fast(c[o + 2] + B3.z);
@@ -539,8 +539,8 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 
 // Backward of the colour MLP for the composited pairs at positions r0 .. r0+15 of
 // an entry's list.  Per pair: dL/dc = w dL (w: compositing weight at w_e[slot],
-// dL: dl[c * npix + slot]) and dL/da3 = dL/dc c (1 - c) (c at col_e[c * plane +
-// slot]).  Accumulates, with shared-memory atomics, in the network record layout:
+// dL: dl[c * npix + slot]) and dL/da3 = dL/dc c (1 - c) (c at col_e[slot * qs +
+// c * plane]).  Accumulates, with shared-memory atomics, in the network record layout:
 //   WC1 [NC][11]  dL/dWc1 for the direction columns 0..2;   H0 [NC] dL/dh0;
 //   AW2 [NC * NC] dL/dWc2 in mma fragment order (element i of lane l of output
 //                 tile (mn, nk), i.e. row 16 mn + l/4 + 8 (i >> 1), column
@@ -552,7 +552,7 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 template <int NC, bool BF16>
 __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float4 *s_ray, const uint16_t *list,
                                                     int r0, int n, const float *w_e, const float *dl, int npix,
-                                                    const float *col_e, int plane, float *WC1, float *H0,
+                                                    const float *col_e, int qs, int plane, float *WC1, float *H0,
                                                     float *AW2, float *W3, float *BC2, float *AB3)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -566,7 +566,7 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
     auto ga3 = [&](bool v, int q) {
         if (!v) return make_float3(0.f, 0.f, 0.f);
         const float w = w_e[q];
-        const float cx = col_e[q], cy = col_e[plane + q], cz = col_e[2 * plane + q];
+        const float cx = col_e[q * qs], cy = col_e[plane + q * qs], cz = col_e[2 * plane + q * qs];
         return make_float3(w * dl[q] * cx * (1.0f - cx), w * dl[npix + q] * cy * (1.0f - cy),
                            w * dl[2 * npix + q] * cz * (1.0f - cz));
     };
@@ -681,6 +681,16 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
                 if (d4[i] != 0.0f) atomicAdd(dst + 32 * i, d4[i]);
         }
     }
+}
+
+// Rank of pixel slot `slot` among the set bits of a tile's composited mask
+// (words[NPIX / 32]): the number of composited pixels with a smaller slot.
+template <int NPIX>
+__device__ __forceinline__ uint32_t mask_rank(const uint32_t *words, int slot)
+{
+    uint32_t r = __popc(words[slot >> 5] & ((1u << (slot & 31)) - 1u));
+    for (int w = 0; w < (slot >> 5); ++w) r += __popc(words[w]);
+    return r;
 }
 
 // Warp-aggregated append of `val` to list[] for the lanes with pred set.

@@ -3,7 +3,10 @@
 // Persistent CTAs take tiles as in the forward and walk each tile's list in
 // staged chunks.  Per chunk: the pixels that composited each entry come from the
 // forward's composited masks (P1); alpha_hat and the colour of every composited
-// pair are recomputed (P2 / P4); each pixel replays its weights and the gradient
+// pair are read back from the forward's colour store, by the rank of the pixel
+// among the entry's composited pixels, or -- where the store was full or is off,
+// and always without a colour network -- recomputed (P2 / P4); each pixel replays
+// its weights and the gradient
 // of its colour with respect to alpha_hat in list order (P3 / P5); then the
 // per-pair gradients run as work items (P6).  With the forward's final colour C
 // (no background) and optical depth tau_f:
@@ -343,12 +346,15 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     float *s_dl = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [3][NPIX] dL/dC of the tile's pixels
     float *sm = s_dl + 3 * NPIX;                           // [CH][es] staged entries
     float *acc = sm + CH * es;                             // [CH][vg] per-entry gradient sums
-    float *s_ah = acc + CH * vg;                           // [CH][NPIX] alpha_hat, then dL/dalpha_hat
-    float *s_w = s_ah + CH * NPIX;                         // [CH][NPIX] weights of the composited pairs
-    float *s_col = s_w + CH * NPIX;                        // [3][CH][NPIX] colours
-    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + 3 * CH * NPIX);  // [CH][NPIX]
+    // [CH][NPIX] per composited pair: colour (x, y, z) and alpha_hat (w), which P3/P5
+    // replace by dL/dalpha_hat (the layout of a colour-store record)
+    float4 *s_cs = reinterpret_cast<float4 *>(acc + CH * vg);
+    float *s_w = reinterpret_cast<float *>(s_cs + CH * NPIX);  // [CH][NPIX] weights of the composited pairs
+    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_w + CH * NPIX);  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
     __shared__ uint32_t s_gid[kMaxChunk];
+    __shared__ uint32_t s_koff[64];         // colour-store offsets of the chunk's keys
+    __shared__ bool s_stored;               // every composited pair of the chunk is in the store
     __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
@@ -419,6 +425,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 s_gid[tid] = a.vals[c0 + tid];
                 s_nh[tid] = 0;
                 s_na[tid] = 0;
+                if constexpr (NC > 0) s_koff[tid] = a.colstore ? a.key_off[c0 + tid] : kNoStore;
             }
             // composited masks of the chunk's entries (none past the tile's walk length)
             for (int i = tid; i < cnt * (NPIX / 32); i += NT) {
@@ -442,21 +449,39 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     const bool act = (word >> lane) & 1u;
                     cm[k] |= (uint32_t)act << e;
                     list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
+                    if constexpr (NC > 0) {
+                        // the pair's (colour, alpha_hat) from the forward's store, copied
+                        // asynchronously while the lists are built
+                        const uint32_t o = s_koff[e];
+                        if (act && o != kNoStore)
+                            cp_async16(s_cs + e * NPIX + slot,
+                                       a.colstore + o + mask_rank<NPIX>(s_cmw + e * (NPIX / 32), slot));
+                    }
                 }
             }
+            if constexpr (NC > 0) cp_async_wait_all();
             __syncthreads();
             if (tid < 32) {
                 warp_prefix64(s_na, cnt, s_pa);
                 warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
                 warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
+                if constexpr (NC > 0) {
+                    const bool miss = (int)lane < cnt && s_na[lane] > 0 && s_koff[lane] == kNoStore;
+                    const bool miss2 = (int)lane + 32 < cnt && s_na[lane + 32] > 0 && s_koff[lane + 32] == kNoStore;
+                    const bool any = __any_sync(0xffffffffu, miss || miss2);
+                    if (lane == 0) s_stored = !any;
+                }
             }
             __syncthreads();
+            bool stored = false;
+            if constexpr (NC > 0) stored = s_stored;
             // P2: alpha_hat of every composited pair (per thread), then P4: their colours
-            // (per warp, 16 pairs of one entry); independent, so one phase
+            // (per warp, 16 pairs of one entry); independent, so one phase.  With the
+            // colour store both come from the forward (one 16-byte load per pair).
             {
                 const int na = s_pa[cnt];
                 int e = 0;
-                for (int q = tid; q < na; q += NT) {
+                for (int q = tid; q < (NC > 0 && stored ? 0 : na); q += NT) {
                     while (q >= s_pa[e + 1]) ++e;
                     const int pix = s_al[e * NPIX + (q - s_pa[e])];
                     const float *R = sm + e * es;
@@ -464,21 +489,20 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     Hit h;
                     float ah = 0.0f;
                     if (intersect(R, ck, r, h)) ah = integral<FORM>(R, R + kRecFloats, ns, ck, r, h);
-                    s_ah[e * NPIX + pix] = ah;
-                    if constexpr (NC == 0) {
-                        s_col[(0 * CH + e) * NPIX + pix] = R[kRecRgb + 0];
-                        s_col[(1 * CH + e) * NPIX + pix] = R[kRecRgb + 1];
-                        s_col[(2 * CH + e) * NPIX + pix] = R[kRecRgb + 2];
-                    }
+                    if constexpr (NC == 0) s_cs[e * NPIX + pix] = make_float4(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2], ah);
+                    else s_cs[e * NPIX + pix].w = ah;
                 }
             }
             if constexpr (NC > 0) {
-                const int np = s_pp[cnt];
-                int e = 0;
-                for (int q = wid; q < np; q += NT / 32) {
-                    while (q >= s_pp[e + 1]) ++e;
-                    warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
-                                              (q - s_pp[e]) * 16, s_na[e], s_col + e * NPIX, CH * NPIX);
+                if (!stored) {
+                    const int np = s_pp[cnt];
+                    int e = 0;
+                    for (int q = wid; q < np; q += NT / 32) {
+                        while (q >= s_pp[e + 1]) ++e;
+                        warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray,
+                                                  s_al + e * NPIX, (q - s_pp[e]) * 16, s_na[e],
+                                                  reinterpret_cast<float *>(s_cs + e * NPIX), 4, 1);
+                    }
                 }
             }
             __syncthreads();
@@ -490,19 +514,19 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 const int slot = k * NT + tid;
                 for (uint32_t m = cm[k]; m != 0u; m &= m - 1u) {
                     const int e = __ffs(m) - 1;
-                    const float ah = s_ah[e * NPIX + slot];
+                    const float4 cs = s_cs[e * NPIX + slot];
+                    const float ah = cs.w;
                     const float w = __expf(-tau[k]) * (1.0f - __expf(-ah));
                     tau[k] += ah;
                     const float Tn = __expf(-tau[k]);
                     s_w[e * NPIX + slot] = w;
-                    const float3 col = make_float3(s_col[(0 * CH + e) * NPIX + slot], s_col[(1 * CH + e) * NPIX + slot],
-                                                   s_col[(2 * CH + e) * NPIX + slot]);
+                    const float3 col = make_float3(cs.x, cs.y, cs.z);
                     pref[k].x = fmaf(w, col.x, pref[k].x);
                     pref[k].y = fmaf(w, col.y, pref[k].y);
                     pref[k].z = fmaf(w, col.z, pref[k].z);
-                    s_ah[e * NPIX + slot] = dL[k].x * (Tn * col.x - (Cf[k].x - pref[k].x)) +
-                                            dL[k].y * (Tn * col.y - (Cf[k].y - pref[k].y)) +
-                                            dL[k].z * (Tn * col.z - (Cf[k].z - pref[k].z)) - bgdot[k];
+                    s_cs[e * NPIX + slot].w = dL[k].x * (Tn * col.x - (Cf[k].x - pref[k].x)) +
+                                              dL[k].y * (Tn * col.y - (Cf[k].y - pref[k].y)) +
+                                              dL[k].z * (Tn * col.z - (Cf[k].z - pref[k].z)) - bgdot[k];
                 }
             }
             __syncthreads();
@@ -526,7 +550,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                             const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
                             g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
                         }
-                        pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_ah[e * NPIX + pix], g_c,
+                        pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_cs[e * NPIX + pix].w, g_c,
                                                 acc + e * vg);
                     } else if constexpr (NC > 0) {
                         const int q = it - nb;
@@ -534,7 +558,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         float *A = acc + ec * vg;
                         warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
                                                       s_al + ec * NPIX, (q - s_pp[ec]) * 16, s_na[ec],
-                                                      s_w + ec * NPIX, s_dl, NPIX, s_col + ec * NPIX, CH * NPIX,
+                                                      s_w + ec * NPIX, s_dl, NPIX,
+                                                      reinterpret_cast<const float *>(s_cs + ec * NPIX), 4, 1,
                                                       A + a.off_Wc1, A + a.stride + kGvFloats, A + a.off_Wc2,
                                                       A + a.off_Wc3, A + a.off_bc2, A + a.off_bc3);
                     }

@@ -14,7 +14,10 @@
 //                   before any colour is evaluated; composited pairs are listed;
 //   P4 (per warp)   colour MLP of the composited pairs in passes of 16 pairs of
 //                   one list entry (tensor cores for the hidden layer);
-//   P5 (per pixel)  C += w * colour in list order.
+//   P5 (per pixel)  C += w * colour in list order; with the colour store on, each
+//                   composited pair's (colour, alpha_hat) is written to the key's
+//                   slice of the store at the rank of its pixel among the key's
+//                   composited pixels (the backward reads it back by the same rank).
 // The result is the sequential front-to-back composite.  The per-pixel composited
 // colour, optical depth, number of list entries walked and, per (tile, entry), the
 // mask of pixels that composited it are saved for the backward pass.
@@ -29,7 +32,8 @@ __host__ __device__ inline size_t fwd_smem_bytes(int nc, int ns, int chunk)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
     const size_t per_entry = (size_t)entry_stride(ns, nc) * 4 + NPIX * 4 /* alpha_hat */ + NPIX * 2 /* hit list */ +
-                             (nc > 0 ? NPIX * (4 + 12 + 2) /* weight, colour, list */ : 0);
+                             (nc > 0 ? NPIX * (4 + 12 + 2) /* weight, colour, list */ +
+                                           (NPIX / 32 + 1) * 4 /* mask words, store offset */ : 0);
     return NPIX * 32 /* rays */ + (size_t)chunk * per_entry;
 }
 
@@ -50,12 +54,17 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
     float *s_col = s_w + (NC > 0 ? CH * NPIX : 0);              // [3][CH][NPIX] colours (MLP)
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + (NC > 0 ? 3 * CH * NPIX : 0));  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                          // [CH][NPIX] (MLP)
+    uint32_t *s_cw = reinterpret_cast<uint32_t *>(s_al + (NC > 0 ? CH * NPIX : 0));  // [CH][NPIX/32] masks (MLP)
+    uint32_t *s_koff = s_cw + (NC > 0 ? CH * (NPIX / 32) : 0);  // [CH] colour-store offsets (MLP)
     __shared__ uint32_t s_gid[kMaxChunk];
+    __shared__ int s_pc[65];
+    __shared__ unsigned long long s_cbase, s_blk_next, s_blk_end;  // colour store: chunk base, CTA block
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_nb[65], s_pb[65];
     __shared__ int s_view, s_item;
 
     const int tid = threadIdx.x;
     uint32_t n_cand = 0, n_hit = 0, n_comp = 0;
+    if (tid == 0) s_blk_next = s_blk_end = 0;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.work_counter, 1);
@@ -171,6 +180,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                     if (lane_id() == 0 && a.cmask)
                         a.cmask[(int64_t)(c0 + e) * (NPIX / 32) + (slot >> 5)] = word;
                     if constexpr (NC > 0) {
+                        if (lane_id() == 0) s_cw[e * (NPIX / 32) + (slot >> 5)] = word;
+                    }
+                    if constexpr (NC > 0) {
                         s_w[e * NPIX + slot] = act ? w : -1.0f;
                         list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
                     }
@@ -179,7 +191,37 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
 
             if constexpr (NC > 0) {
                 __syncthreads();
-                if (tid < 32) warp_batch_prefix(s_na, cnt, 4, s_nb, s_pb);
+                if (tid < 32) {
+                    warp_batch_prefix(s_na, cnt, 4, s_nb, s_pb);
+                    if (a.colstore) {
+                        // one slice of the colour store per chunk, split by entry
+                        warp_prefix64(s_na, cnt, s_pc);
+                        __syncwarp();
+                        if (tid == 0) {
+                            const unsigned long long tot = (unsigned long long)s_pc[cnt];
+                            if (s_blk_next + tot > s_blk_end) {
+                                // a new block of the store for this CTA (the rest of the old one is left unused)
+                                const unsigned long long want = tot > kColBlock ? tot : kColBlock;
+                                const unsigned long long b = atomicAdd(a.col_count, want);
+                                const bool fits = b + want <= (unsigned long long)a.col_cap;
+                                s_blk_next = fits ? b : 0ull;
+                                s_blk_end = fits ? b + want : 0ull;
+                            }
+                            if (s_blk_next + tot <= s_blk_end) {
+                                s_cbase = s_blk_next;
+                                s_blk_next += tot;
+                            } else {
+                                s_cbase = ~0ull;  // store full: the backward recomputes this chunk
+                            }
+                        }
+                        __syncwarp();
+                        for (int e = tid; e < cnt; e += 32) {
+                            const uint32_t o = s_cbase == ~0ull ? kNoStore : (uint32_t)(s_cbase + s_pc[e]);
+                            s_koff[e] = o;
+                            a.key_off[c0 + e] = o;
+                        }
+                    }
+                }
                 __syncthreads();
                 // P4: colour of every composited pair, one warp per pass of 16 pairs of one entry
                 const int np = s_pb[cnt];
@@ -187,7 +229,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                 for (int q = tid >> 5; q < np; q += NT / 32) {
                     while (q >= s_pb[e + 1]) ++e;
                     warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
-                                              (q - s_pb[e]) * 16, s_na[e], s_col + e * NPIX, CH * NPIX);
+                                              (q - s_pb[e]) * 16, s_na[e], s_col + e * NPIX, 1, CH * NPIX);
                 }
                 __syncthreads();
                 // P5: accumulate in list order
@@ -197,9 +239,17 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                         const int slot = k * NT + tid;
                         const float w = s_w[e2 * NPIX + slot];
                         if (w >= 0.0f) {
-                            C[k].x = fmaf(w, s_col[(0 * CH + e2) * NPIX + slot], C[k].x);
-                            C[k].y = fmaf(w, s_col[(1 * CH + e2) * NPIX + slot], C[k].y);
-                            C[k].z = fmaf(w, s_col[(2 * CH + e2) * NPIX + slot], C[k].z);
+                            const float cx = s_col[(0 * CH + e2) * NPIX + slot], cy = s_col[(1 * CH + e2) * NPIX + slot],
+                                        cz = s_col[(2 * CH + e2) * NPIX + slot];
+                            C[k].x = fmaf(w, cx, C[k].x);
+                            C[k].y = fmaf(w, cy, C[k].y);
+                            C[k].z = fmaf(w, cz, C[k].z);
+                            if (a.colstore) {
+                                const uint32_t o = s_koff[e2];
+                                if (o != kNoStore)
+                                    a.colstore[o + mask_rank<NPIX>(s_cw + e2 * (NPIX / 32), slot)] =
+                                        make_float4(cx, cy, cz, s_ah[e2 * NPIX + slot]);
+                            }
                         }
                     }
                 }

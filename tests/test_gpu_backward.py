@@ -158,3 +158,21 @@ def test_mlp64_ns32_bf16(R, oracle_lib):
     g = _gpu_grads(R, sc, cams, np.concatenate(dLv))
     gref = _oracle_grads(O, sc, cams, dLv)
     _check(g, gref, sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
+
+
+@pytest.mark.parametrize("replay", [False, True])
+def test_mlp_colour_store_and_replay(R, oracle_lib, replay):
+    """The backward with the forward's colour store (default) and with the colours
+    recomputed (SNP_FLAG_REPLAY_COLOR) both match the oracle, and each other."""
+    O = oracle_lib
+    sc = synth.make_scene(1500, seed=12, center_half=1.5, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
+    cams = [synth.look_at_camera((0.0, 0.5, 6.0), (0, 0, 0), 80, 64),
+            synth.look_at_camera((5.0, 1.0, 3.0), (0, 0, 0), 48, 72)]
+    dLv = _dl(O, sc, cams, 5)
+    fields = sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"]
+    g = _gpu_grads_cfg(R, sc, cams, np.concatenate(dLv), replay_color=replay)
+    _check(g, _oracle_grads(O, sc, cams, dLv), fields)
+    g_other = _gpu_grads_cfg(R, sc, cams, np.concatenate(dLv), replay_color=not replay)
+    for k in fields:
+        scale = np.abs(g[k]).max() + 1e-30
+        assert np.abs(g[k] - g_other[k]).max() <= 1e-5 * scale, k
