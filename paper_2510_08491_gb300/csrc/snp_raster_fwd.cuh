@@ -191,8 +191,19 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
 
             if constexpr (NC > 0) {
                 __syncthreads();
+                if (tid < 32) warp_batch_prefix(s_na, cnt, 4, s_nb, s_pb);
+                __syncthreads();
+                // P4: colour of every composited pair, one warp per pass of 16 pairs of one entry
+                const int np = s_pb[cnt];
+                int e = 0;
+                for (int q = tid >> 5; q < np; q += NT / 32) {
+                    while (q >= s_pb[e + 1]) ++e;
+                    warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
+                                              (q - s_pb[e]) * 16, s_na[e], s_col + e * NPIX, 1, CH * NPIX);
+                }
                 if (tid < 32) {
-                    warp_batch_prefix(s_na, cnt, 4, s_nb, s_pb);
+                    // colour-store slice of the chunk (needed from P5 on; here it overlaps
+                    // the other warps' colour passes)
                     if (a.colstore) {
                         // one slice of the colour store per chunk, split by entry
                         warp_prefix64(s_na, cnt, s_pc);
@@ -215,21 +226,12 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                             }
                         }
                         __syncwarp();
-                        for (int e = tid; e < cnt; e += 32) {
-                            const uint32_t o = s_cbase == ~0ull ? kNoStore : (uint32_t)(s_cbase + s_pc[e]);
-                            s_koff[e] = o;
-                            a.key_off[c0 + e] = o;
+                        for (int ei = tid; ei < cnt; ei += 32) {
+                            const uint32_t o = s_cbase == ~0ull ? kNoStore : (uint32_t)(s_cbase + s_pc[ei]);
+                            s_koff[ei] = o;
+                            a.key_off[c0 + ei] = o;
                         }
                     }
-                }
-                __syncthreads();
-                // P4: colour of every composited pair, one warp per pass of 16 pairs of one entry
-                const int np = s_pb[cnt];
-                int e = 0;
-                for (int q = tid >> 5; q < np; q += NT / 32) {
-                    while (q >= s_pb[e + 1]) ++e;
-                    warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray, s_al + e * NPIX,
-                                              (q - s_pb[e]) * 16, s_na[e], s_col + e * NPIX, 1, CH * NPIX);
                 }
                 __syncthreads();
                 // P5: accumulate in list order
