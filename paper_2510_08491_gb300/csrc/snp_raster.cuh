@@ -44,6 +44,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
 }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -63,6 +68,23 @@ __device__ __forceinline__ void cp_async_wait_all()
 // cp.async.wait_group has completed.  (The colour-MLP kernels keep the
 // per-entry loop and never see the shift, so their register allocation is
 // unchanged.)
+// The copies of stage_chunk for a colour-network kernel, without the wait: the
+// caller issues more copies (the colour store's) and waits once for all.
+__device__ __forceinline__ void stage_chunk_issue(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
+                                                  const RasterArgs &a, int es)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr int kRec16 = kRecFloats / 4;
+    const int per = es / 4;
+    for (int e = 0; e < cnt; ++e) {
+        const int64_t gid = s_gid[e];
+        const float *rec = a.rec + gid * kRecFloats;
+        const float *net = a.npack + (gid - vn) * a.npack_stride;
+        float *dst = sm + e * es;
+        for (int q = tid; q < per; q += nt) cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
+    }
+}
+
 template <int NC, bool BF16>
 __device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
                                             const RasterArgs &a, int es, float xi)

@@ -25,8 +25,9 @@
 
 namespace snp {
 
-// Shared words for the composited masks of one backward chunk (chunk x tile
-// pixels / 32; the backward chunk is at most 8 entries).
+// Shared words for the composited masks of two backward chunks, the current one
+// and the next one being copied in (chunk x tile pixels / 32 each; the backward
+// chunk is at most 8 entries).
 constexpr int kMaskWords = 512;
 
 // Elements of one primitive's network record (snp_net_layout): every field
@@ -353,9 +354,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_w + CH * NPIX);  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
     __shared__ uint32_t s_gid[kMaxChunk];
-    __shared__ uint32_t s_koff[64];         // colour-store offsets of the chunk's keys
+    __shared__ uint32_t s_koff[64];         // colour-store offsets of the chunk's keys (two halves)
     __shared__ bool s_stored;               // every composited pair of the chunk is in the store
-    __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk
+    __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk (two halves)
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
     __shared__ uint32_t s_maxwalk;
@@ -418,23 +419,43 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
         __syncthreads();
         const uint32_t maxwalk = s_maxwalk;
 
-        for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += CH) {
+        // Per chunk: its keys' record ids, colour-store offsets and composited masks, in
+        // one of two halves of s_gid / s_koff / s_cmw; the next chunk's are copied into
+        // the other half (4-byte cp.async) while this chunk runs P6.
+        bool pre = false;
+        int ci = 0;
+        for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += CH, ++ci) {
             const int cnt = min((int)(rg.y - c0), CH);
+            uint32_t *const cg = s_gid + (ci & 1) * (kMaxChunk / 2);
+            uint32_t *const cko = s_koff + (ci & 1) * 32;
+            uint32_t *const cmw = s_cmw + (ci & 1) * (kMaskWords / 2);
             __syncthreads();
+            if (pre) {
+                cp_async_wait_all();
+            } else {
+                if (tid < cnt) {
+                    cg[tid] = a.vals[c0 + tid];
+                    if constexpr (NC > 0) cko[tid] = a.colstore ? a.key_off[c0 + tid] : kNoStore;
+                }
+                // composited masks of the chunk's entries (none past the tile's walk length)
+                for (int i = tid; i < cnt * (NPIX / 32); i += NT) {
+                    const int e = i / (NPIX / 32);
+                    cmw[i] = c0 - rg.x + e < maxwalk ? a.cmask[(int64_t)c0 * (NPIX / 32) + i] : 0u;
+                }
+            }
             if (tid < cnt) {
-                s_gid[tid] = a.vals[c0 + tid];
                 s_nh[tid] = 0;
                 s_na[tid] = 0;
-                if constexpr (NC > 0) s_koff[tid] = a.colstore ? a.key_off[c0 + tid] : kNoStore;
-            }
-            // composited masks of the chunk's entries (none past the tile's walk length)
-            for (int i = tid; i < cnt * (NPIX / 32); i += NT) {
-                const int e = i / (NPIX / 32);
-                s_cmw[i] = c0 - rg.x + e < maxwalk ? a.cmask[(int64_t)c0 * (NPIX / 32) + i] : 0u;
             }
             __syncthreads();
-            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es, V.time);
-            __syncthreads();
+            if constexpr (NC > 0) {
+                // staging copies in flight through P1, which needs only the masks; one
+                // wait below covers them and P1's colour-store copies
+                stage_chunk_issue(sm, cg, cnt, vn, a, es);
+            } else {
+                stage_chunk<NC, BF16>(sm, cg, cnt, vn, a, es, V.time);
+                __syncthreads();
+            }
 
             // P1: the pixels that composited each entry, from the forward's masks (entries
             // at or past the tile's walk length were composited by no pixel)
@@ -445,17 +466,17 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     const int slot = k * NT + tid;
-                    const unsigned word = s_cmw[e * (NPIX / 32) + (slot >> 5)];
+                    const unsigned word = cmw[e * (NPIX / 32) + (slot >> 5)];
                     const bool act = (word >> lane) & 1u;
                     cm[k] |= (uint32_t)act << e;
                     list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
                     if constexpr (NC > 0) {
                         // the pair's (colour, alpha_hat) from the forward's store, copied
                         // asynchronously while the lists are built
-                        const uint32_t o = s_koff[e];
+                        const uint32_t o = cko[e];
                         if (act && o != kNoStore)
                             cp_async16(s_cs + e * NPIX + slot,
-                                       a.colstore + o + mask_rank<NPIX>(s_cmw + e * (NPIX / 32), slot));
+                                       a.colstore + o + mask_rank<NPIX>(cmw + e * (NPIX / 32), slot));
                     }
                 }
             }
@@ -466,8 +487,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
                 warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
                 if constexpr (NC > 0) {
-                    const bool miss = (int)lane < cnt && s_na[lane] > 0 && s_koff[lane] == kNoStore;
-                    const bool miss2 = (int)lane + 32 < cnt && s_na[lane + 32] > 0 && s_koff[lane + 32] == kNoStore;
+                    const bool miss = (int)lane < cnt && s_na[lane] > 0 && cko[lane] == kNoStore;
+                    const bool miss2 = (int)lane + 32 < cnt && s_na[lane + 32] > 0 && cko[lane + 32] == kNoStore;
                     const bool any = __any_sync(0xffffffffu, miss || miss2);
                     if (lane == 0) s_stored = !any;
                 }
@@ -530,6 +551,30 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
+            // the next chunk's ids, store offsets and masks, in flight through P6
+            {
+                const uint32_t c0n = c0 + CH;
+                pre = c0n < rg.y && c0n - rg.x < maxwalk;
+                if (pre) {
+                    const int cntn = min((int)(rg.y - c0n), CH);
+                    uint32_t *const ng = s_gid + ((ci + 1) & 1) * (kMaxChunk / 2);
+                    uint32_t *const nko = s_koff + ((ci + 1) & 1) * 32;
+                    uint32_t *const nmw = s_cmw + ((ci + 1) & 1) * (kMaskWords / 2);
+                    if (tid < cntn) {
+                        cp_async4(ng + tid, a.vals + c0n + tid);
+                        if constexpr (NC > 0) {
+                            if (a.colstore) cp_async4(nko + tid, a.key_off + c0n + tid);
+                            else nko[tid] = kNoStore;
+                        }
+                    }
+                    for (int i = tid; i < cntn * (NPIX / 32); i += NT) {
+                        const int e = i / (NPIX / 32);
+                        if (c0n - rg.x + e < maxwalk) cp_async4(nmw + i, a.cmask + (int64_t)c0n * (NPIX / 32) + i);
+                        else nmw[i] = 0u;
+                    }
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                }
+            }
             // P6: per-pair gradients.  Work items: density / geometry batches of 32 pairs
             // of one entry (per-lane chain, warp reductions), then colour-MLP passes of
             // 16 pairs of one entry (tensor cores); any warp takes any item.
@@ -566,7 +611,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            flush_chunk<NC, NT>(a, acc, vg, s_gid, cnt, vn, tid, NT, V.time);
+            flush_chunk<NC, NT>(a, acc, vg, cg, cnt, vn, tid, NT, V.time);
         }
         __syncthreads();
     }

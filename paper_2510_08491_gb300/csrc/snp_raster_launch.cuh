@@ -60,7 +60,7 @@ template <int TS, int NC, int FORM, bool BF16>
 static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
 {
     const size_t smem = bwd_smem_bytes<TS>(NC, a.n_sigma, a.chunk, a.stride);
-    if (smem > kSmemMax || a.chunk < 1 || a.chunk > 64 || a.chunk * (TS * TS / 32) > kMaskWords ||
+    if (smem > kSmemMax || a.chunk < 1 || a.chunk > 32 || a.chunk * (TS * TS / 32) > kMaskWords / 2 ||
         a.stride != net_stride(a.n_sigma, NC, a.off_sh >= 0, a.off_wt >= 0))
         return SNP_ERR_INVALID_ARG;
     if (a.n_tiles <= 0) return SNP_OK;
