@@ -103,16 +103,22 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
         const uint2 rg = a.ranges[tile];
         const int64_t vn = (int64_t)v * a.n;
 
-        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += CH) {
+        // The chunk's record ids live in one half of s_gid; with a colour network the
+        // next chunk's are copied into the other half (4-byte cp.async) from P2 on.
+        bool pre = false;
+        int ci = 0;
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += CH, ++ci) {
             const int cnt = min((int)(rg.y - c0), CH);
+            uint32_t *const cg = s_gid + (NC > 0 ? (ci & 1) * (kMaxChunk / 2) : 0);
             __syncthreads();
             if (tid < cnt) {
-                s_gid[tid] = a.vals[c0 + tid];
+                if (!pre) cg[tid] = a.vals[c0 + tid];
                 s_nh[tid] = 0;
                 s_na[tid] = 0;
             }
+            if (pre) cp_async_wait_all();
             __syncthreads();
-            stage_chunk<NC, BF16>(sm, s_gid, cnt, vn, a, es, V.time);
+            stage_chunk<NC, BF16>(sm, cg, cnt, vn, a, es, V.time);
             __syncthreads();
 
             // P1: which pixels' rays enter which ellipsoids
@@ -131,6 +137,16 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
             __syncthreads();
             if (tid < 32) warp_prefix64(s_nh, cnt, s_ph);
             __syncthreads();
+
+            if constexpr (NC > 0) {  // (without a colour network the phases are too short to cover it)
+                const uint32_t c0n = c0 + CH;
+                pre = c0n < rg.y;
+                if (pre) {
+                    if ((int)tid < min((int)(rg.y - c0n), CH))
+                        cp_async4(s_gid + ((ci + 1) & 1) * (kMaxChunk / 2) + tid, a.vals + c0n + tid);
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                }
+            }
 
             // P2: alpha_hat of every hit
             {
@@ -261,6 +277,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
             for (int k = 0; k < PPT; ++k) any_alive |= alive[k];
             if (__syncthreads_and(!any_alive)) break;
         }
+        if constexpr (NC > 0) cp_async_wait_all();  // a copy for a chunk the early exit skipped must land first
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             if (!inside[k]) continue;

@@ -46,7 +46,7 @@ template <int TS, int NC, int FORM, bool BF16>
 static snp_status run_fwd(const RasterArgs &a, cudaStream_t st)
 {
     const size_t smem = fwd_smem_bytes<TS>(NC, a.n_sigma, a.chunk);
-    if (smem > kSmemMax || a.chunk < 1 || a.chunk > 64) return SNP_ERR_INVALID_ARG;
+    if (smem > kSmemMax || a.chunk < 1 || a.chunk > 64 || a.chunk > kMaxChunk / 2) return SNP_ERR_INVALID_ARG;
     if (a.n_tiles <= 0) return SNP_OK;
     auto kern = k_raster_fwd<TS, NC, FORM, BF16>;
     allow_smem(kern);
