@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk (two halves)
     __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
+    __shared__ int s_item6;  // P6 item counter (items past the first one of each warp)
     __shared__ uint32_t s_maxwalk;
 
     const int tid = threadIdx.x;
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 s_nh[tid] = 0;
                 s_na[tid] = 0;
             }
+            if (tid == 0) s_item6 = 0;
             __syncthreads();
             if constexpr (NC > 0) {
                 // staging copies in flight through P1, which needs only the masks; one
@@ -575,16 +577,31 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     asm volatile("cp.async.commit_group;\n" ::: "memory");
                 }
             }
-            // P6: per-pair gradients.  Work items: density / geometry batches of 32 pairs
-            // of one entry (per-lane chain, warp reductions), then colour-MLP passes of
-            // 16 pairs of one entry (tensor cores); any warp takes any item.
+            // P6: per-pair gradients.  Work items: colour-MLP passes of 16 pairs of one
+            // entry (tensor cores), then density / geometry batches of 32 pairs of one
+            // entry (per-lane chain, warp reductions).  The costlier colour passes go
+            // first and warps take the next item from a shared counter as they finish,
+            // so the phase ends on short items.
             {
                 const int nb = s_pb[cnt], np = NC > 0 ? s_pp[cnt] : 0;
                 int e = 0, ec = 0;
-                for (int it = wid; it < nb + np; it += NT / 32) {
-                    if (it < nb) {
-                        while (it >= s_pb[e + 1]) ++e;
-                        const int kk = (it - s_pb[e]) * 32 + (int)lane;
+                int it = wid;
+                while (it < nb + np) {
+                    if (NC > 0 && it < np) {
+                        if constexpr (NC > 0) {
+                            while (it >= s_pp[ec + 1]) ++ec;
+                            float *A = acc + ec * vg;
+                            warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
+                                                          s_al + ec * NPIX, (it - s_pp[ec]) * 16, s_na[ec],
+                                                          s_w + ec * NPIX, s_dl, NPIX,
+                                                          reinterpret_cast<const float *>(s_cs + ec * NPIX), 4, 1,
+                                                          A + a.off_Wc1, A + a.stride + kGvFloats, A + a.off_Wc2,
+                                                          A + a.off_Wc3, A + a.off_bc2, A + a.off_bc3);
+                        }
+                    } else {
+                        const int q = it - np;
+                        while (q >= s_pb[e + 1]) ++e;
+                        const int kk = (q - s_pb[e]) * 32 + (int)lane;
                         const bool valid = kk < s_na[e];
                         const int pix = valid ? s_al[e * NPIX + kk] : 0;
                         const PixRay r = load_ray(s_ray, pix);
@@ -597,17 +614,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         }
                         pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_cs[e * NPIX + pix].w, g_c,
                                                 acc + e * vg);
-                    } else if constexpr (NC > 0) {
-                        const int q = it - nb;
-                        while (q >= s_pp[ec + 1]) ++ec;
-                        float *A = acc + ec * vg;
-                        warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
-                                                      s_al + ec * NPIX, (q - s_pp[ec]) * 16, s_na[ec],
-                                                      s_w + ec * NPIX, s_dl, NPIX,
-                                                      reinterpret_cast<const float *>(s_cs + ec * NPIX), 4, 1,
-                                                      A + a.off_Wc1, A + a.stride + kGvFloats, A + a.off_Wc2,
-                                                      A + a.off_Wc3, A + a.off_bc2, A + a.off_bc3);
                     }
+                    int nx = 0;
+                    if (lane == 0) nx = atomicAdd(&s_item6, 1) + NT / 32;
+                    it = __shfl_sync(0xffffffffu, nx, 0);
                 }
             }
             __syncthreads();
