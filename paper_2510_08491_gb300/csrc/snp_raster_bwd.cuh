@@ -464,6 +464,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             uint32_t cm[PPT];  // per pixel: entries of this chunk it composited
 #pragma unroll
             for (int k = 0; k < PPT; ++k) cm[k] = 0u;
+            // Each entry's pair list is its composited pixels in slot order: a pixel's
+            // position is its rank among the set bits of the entry's mask (no atomics).
             for (int e = 0; e < cnt; ++e) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
@@ -471,16 +473,22 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     const unsigned word = cmw[e * (NPIX / 32) + (slot >> 5)];
                     const bool act = (word >> lane) & 1u;
                     cm[k] |= (uint32_t)act << e;
-                    list_append(act, (uint16_t)slot, &s_na[e], s_al + e * NPIX);
-                    if constexpr (NC > 0) {
-                        // the pair's (colour, alpha_hat) from the forward's store, copied
-                        // asynchronously while the lists are built
-                        const uint32_t o = cko[e];
-                        if (act && o != kNoStore)
-                            cp_async16(s_cs + e * NPIX + slot,
-                                       a.colstore + o + mask_rank<NPIX>(cmw + e * (NPIX / 32), slot));
+                    if (act) {
+                        const uint32_t rank = mask_rank<NPIX>(cmw + e * (NPIX / 32), slot);
+                        s_al[e * NPIX + rank] = (uint16_t)slot;
+                        if constexpr (NC > 0) {
+                            // the pair's (colour, alpha_hat) from the forward's store, copied
+                            // asynchronously while the lists are built
+                            const uint32_t o = cko[e];
+                            if (o != kNoStore) cp_async16(s_cs + e * NPIX + slot, a.colstore + o + rank);
+                        }
                     }
                 }
+            }
+            if (tid < cnt) {
+                int c = 0;
+                for (int w = 0; w < NPIX / 32; ++w) c += __popc(cmw[tid * (NPIX / 32) + w]);
+                s_na[tid] = c;
             }
             if constexpr (NC > 0) cp_async_wait_all();
             __syncthreads();
