@@ -61,9 +61,10 @@ __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, 
 // Flush the chunk's cnt entry accumulators: permute the Wc2 blocks to row-major
 // and scale W1 / b1 by w0 in place (for a time-conditioned scene first setting
 // dL/dW_t,k = xi dL/d(staged phase offset k), since the staged offset is
-// w0 b1_k + xi W_t,k), reduce every block into the caller's arrays
-// with bulk asynchronous adds (issued by thread 0), wait until they have read
-// shared memory, then clear the accumulators.  All threads call it.
+// w0 b1_k + xi W_t,k), then reduce every block into the caller's arrays with bulk
+// asynchronous adds issued by thread 0.  All threads call it.  The reads of the
+// bulk adds complete in the background: the kernel waits for them (thread 0) and
+// clears the accumulators only in the next chunk, before its first accumulation.
 template <int NC, int NT>
 __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int vg, const uint32_t *s_gid, int cnt,
                                             int64_t vn, int tid, int nt, float xi)
@@ -125,11 +126,8 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
             bulk_reduce_add(a.g_view + gid * kGvFloats, A + a.stride, kGvFloats * 4u);
             if constexpr (NC > 0) bulk_reduce_add(a.g_h0 + prim * NC, A + a.stride + kGvFloats, NC * 4u);
         }
-        asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
     }
-    __syncthreads();
-    float4 *A4 = reinterpret_cast<float4 *>(acc);
-    for (int q = tid; q < cnt * vg / 4; q += nt) A4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Density and geometry gradient of one (pixel, primitive) pair, reduced across
@@ -366,6 +364,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const unsigned lane = lane_id();
     const int wid = tid >> 5;
     for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
+    int clear_n = 0;  // float4s of accumulators the next chunk clears (after the bulk reads)
 
     for (;;) {
         if (tid == 0) {
@@ -491,7 +490,13 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 s_na[tid] = c;
             }
             if constexpr (NC > 0) cp_async_wait_all();
+            // the previous chunk's bulk adds have read its accumulators by now
+            if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
             __syncthreads();
+            {
+                float4 *A4 = reinterpret_cast<float4 *>(acc);
+                for (int q = tid; q < clear_n; q += NT) A4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             if (tid < 32) {
                 warp_prefix64(s_na, cnt, s_pa);
                 warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
@@ -630,6 +635,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             }
             __syncthreads();
             flush_chunk<NC, NT>(a, acc, vg, cg, cnt, vn, tid, NT, V.time);
+            clear_n = cnt * vg / 4;
         }
         __syncthreads();
     }
