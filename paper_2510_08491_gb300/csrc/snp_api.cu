@@ -7,6 +7,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -174,10 +176,21 @@ struct snp_context {
 constexpr size_t kSmallTotal = 0, kSmallFlags = 16, kSmallTiles = 32, kSmallWork = 48, kSmallNsort = 64,
                  kSmallColCount = 128, kSmallBytes = 256;
 
-#define STAGE_BEGIN(k) \
-    if (ctx->timing) ctx->timer.begin((k), st)
-#define STAGE_END() \
-    if (ctx->timing) ctx->timer.end(st)
+// Host-side NVTX range per stage (visible to Nsight tools and to ncu's
+// --nvtx-include filters), plus CUDA events when stage timing is on.
+static const char *const kStageNames[SNP_N_STAGES] = {"snp:project", "snp:scan",       "snp:emit",
+                                                      "snp:sort",    "snp:ranges",     "snp:raster_fwd",
+                                                      "snp:raster_bwd", "snp:post_bwd"};
+#define STAGE_BEGIN(k)                        \
+    do {                                      \
+        nvtxRangePushA(kStageNames[(k)]);     \
+        if (ctx->timing) ctx->timer.begin((k), st); \
+    } while (0)
+#define STAGE_END()                           \
+    do {                                      \
+        if (ctx->timing) ctx->timer.end(st);  \
+        nvtxRangePop();                       \
+    } while (0)
 
 static snp_status fail(snp_context *c, snp_status s, const char *fmt, ...)
 {
@@ -563,8 +576,10 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     {
         RasterArgs pa;
         fill_args(pa, ctx, desc, scene, nullptr);
-        if ((s = launch_pack_net(pa, desc->color_mode, desc->n_c, desc->weight_dtype == SNP_BF16, st)) != SNP_OK)
+        if ((s = launch_pack_net(pa, desc->color_mode, desc->n_c, desc->weight_dtype == SNP_BF16, st)) != SNP_OK) {
+            STAGE_END();
             return fail(ctx, s, "network pack launch failed");
+        }
         if (desc->color_mode == SNP_COLOR_SH) {
             snp_net_layout L;
             layout_of(*desc, L);

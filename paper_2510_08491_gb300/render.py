@@ -84,6 +84,40 @@ def unpack_geom_grad(g_geom: torch.Tensor) -> dict:
     return {"centers": g[:, 0:3], "log_scales": g[:, 3:6], "quats": g[:, 6:10], "rgb": g[:, 10:13]}
 
 
+_DESC_FIELDS = ("n", "n_sigma", "color_mode", "n_c", "weight_dtype", "omega0", "dynamic")
+
+
+def save_checkpoint(path: str, ps: PackedScene, state: Optional[dict] = None, step: int = 0) -> None:
+    """Write the packed scene (geometry and network arrays in the library's layout),
+    optional optimiser state (name -> tensor, e.g. Adam moments and an FP32 master
+    copy) and the step count to one .npz file.  BF16 networks keep their exact bits."""
+    arrays = {"geom": ps.geom.detach().cpu().numpy()}
+    if ps.net.dtype == torch.bfloat16:
+        arrays["net_bf16_bits"] = ps.net.detach().cpu().view(torch.int16).numpy()
+    else:
+        arrays["net"] = ps.net.detach().cpu().numpy()
+    for k, t in (state or {}).items():
+        arrays["state_" + k] = t.detach().cpu().numpy()
+    desc = np.asarray([float(getattr(ps.desc, f)) for f in _DESC_FIELDS], np.float64)
+    np.savez(path, desc=desc, offsets=np.asarray(ps.offsets, np.int32), stride=np.int32(ps.stride),
+             step=np.int64(step), **arrays)
+
+
+def load_checkpoint(path: str, device="cuda"):
+    """Read a file written by save_checkpoint: returns (PackedScene, state dict, step)."""
+    z = np.load(path)
+    d = z["desc"]
+    desc = L.SceneDesc(int(d[0]), int(d[1]), int(d[2]), int(d[3]), int(d[4]), float(d[5]), int(d[6]))
+    geom = torch.from_numpy(z["geom"]).to(device)
+    if "net_bf16_bits" in z:
+        net = torch.from_numpy(z["net_bf16_bits"]).view(torch.bfloat16).to(device)
+    else:
+        net = torch.from_numpy(z["net"]).to(device)
+    state = {k[len("state_"):]: torch.from_numpy(z[k]).to(device) for k in z.files if k.startswith("state_")}
+    ps = PackedScene(desc, geom.contiguous(), net.contiguous(), [int(x) for x in z["offsets"]], int(z["stride"]))
+    return ps, state, int(z["step"])
+
+
 class Renderer:
     """One libsnp context plus the stream-level calls."""
 

@@ -136,6 +136,48 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     return out
 
 
+# ----------------------------------------------------------------------------- scene files
+
+_HEADER_KEYS = ("n", "n_sigma", "omega0", "color", "n_c", "weight_dtype", "dynamic")
+_CAMERA_KEYS = ("R_wc", "eye", "fx", "fy", "cx", "cy", "width", "height", "z_near", "time")
+
+
+def save_scene(scene: Scene, path: str, cameras: Optional[Sequence[Camera]] = None) -> None:
+    """Write a scene (and optionally its cameras) as one .npz file: the structure-of-
+    arrays fields in float32 plus a JSON header with the sizes and modes."""
+    import json
+    header = {k: getattr(scene, k) for k in _HEADER_KEYS}
+    header["fields"] = list(scene.fields())
+    arrays = {f: np.ascontiguousarray(getattr(scene, f), dtype=np.float32) for f in scene.fields()}
+    if cameras is not None:
+        header["cameras"] = [{k: np.asarray(getattr(c, k)).tolist() for k in _CAMERA_KEYS} for c in cameras]
+    np.savez(path, __header__=np.frombuffer(json.dumps(header).encode(), dtype=np.uint8), **arrays)
+
+
+def load_scene(path: str):
+    """Read a file written by save_scene: returns (scene, cameras or None)."""
+    import json
+    z = np.load(path)
+    header = json.loads(bytes(z["__header__"]).decode())
+    kw = {k: header[k] for k in _HEADER_KEYS}
+    arrays = {f: np.ascontiguousarray(z[f], dtype=np.float32) for f in header["fields"]}
+    base = {f: arrays.get(f) for f in ("centers", "log_scales", "quats", "W1", "b1", "w2", "b2", "rgb")}
+    sc = Scene(n=int(kw["n"]), n_sigma=int(kw["n_sigma"]), omega0=float(kw["omega0"]), color=kw["color"],
+               n_c=int(kw["n_c"]), weight_dtype=kw["weight_dtype"], dynamic=bool(kw["dynamic"]), **base)
+    for f, a in arrays.items():
+        if f not in base:
+            setattr(sc, f, a)
+    cams = None
+    if "cameras" in header:
+        cams = []
+        for c in header["cameras"]:
+            cams.append(Camera(R_wc=np.asarray(c["R_wc"], np.float32), eye=np.asarray(c["eye"], np.float32),
+                               fx=np.float32(c["fx"]), fy=np.float32(c["fy"]), cx=np.float32(c["cx"]),
+                               cy=np.float32(c["cy"]), width=int(c["width"]), height=int(c["height"]),
+                               z_near=np.float32(c["z_near"]), time=np.float32(c["time"])))
+    return sc, cams
+
+
 # ----------------------------------------------------------------------------- cameras
 
 
