@@ -12,6 +12,11 @@
  *   alpha = 1 - exp(-max(0, alpha_hat)) (Eq. 9); primitives are depth-sorted
  *   per screen tile and alpha-blended front to back (Eq. 4) with their colour.
  *
+ * Around the renderer, the calls of a training step: the population-control
+ * statistic, decision and scene rewrite (Sec. 3.3), the anisotropy regulariser
+ * (Sec. 3.3, Sec. 5.3) and a fused Adam step; and time-conditioned (dynamic)
+ * scenes (App. Applications) through snp_scene_desc.dynamic.
+ *
  * Conventions fixed by this library where the paper is silent (camera model,
  * depth key, near plane, early termination, colour network) are stated at
  * each declaration below.
