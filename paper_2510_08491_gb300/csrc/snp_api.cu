@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <nvtx3/nvToolsExt.h>
@@ -668,6 +669,12 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         a.key_off = (uint32_t *)ctx->key_off.p;
         a.col_count = d_col;
         a.col_cap = (uint32_t)std::min<size_t>(ctx->colstore.bytes / 16, (size_t)0xfffffffe);
+        // test hook: SNP_TEST_COLSTORE_PAIRS caps the store, so that tests can drive the
+        // backward's per-chunk recomputation of the pairs that did not fit
+        if (const char *cap_env = getenv("SNP_TEST_COLSTORE_PAIRS")) {
+            const long long v = atoll(cap_env);
+            if (v >= 0 && (unsigned long long)v < a.col_cap) a.col_cap = (uint32_t)v;
+        }
     }
     STAGE_BEGIN(SNP_STAGE_RASTER_FWD);
     s = launch_raster_fwd(a, desc->color_mode, desc->n_c, c.integral_form, desc->weight_dtype == SNP_BF16, ts, st);
