@@ -306,12 +306,17 @@ class GraphStep:
     current contents of ps.geom / ps.net and dL and writes image / grads."""
 
     def __init__(self, renderer: Renderer, ps: PackedScene, cams, cfg: L.Config, max_keys: int,
-                 dL: Optional[torch.Tensor] = None, backward: bool = True, target: Optional[torch.Tensor] = None):
+                 dL: Optional[torch.Tensor] = None, backward: bool = True, target: Optional[torch.Tensor] = None,
+                 reserve: bool = True):
         """dL: fixed image gradient for the backward; or target: the step computes the
         squared-error loss against it (snp_mse_loss) and back-propagates its gradient
-        (self.loss holds the loss after each replay)."""
+        (self.loss holds the loss after each replay).  reserve=False captures on the
+        context's current reservation (same cameras, configuration and scene shape):
+        several graphs over different scene and output buffers then share one set of
+        workspace buffers, and must be replayed one after another on one stream."""
         self.r, self.ps, self.cams, self.cfg = renderer, ps, cams, cfg
-        renderer.reserve(ps, cams, cfg, max_keys)
+        if reserve:
+            renderer.reserve(ps, cams, cfg, max_keys)
         P = renderer.image_size(cams)
         self.image = torch.empty((P, 3), dtype=torch.float32, device=renderer.device)
         self.target = target

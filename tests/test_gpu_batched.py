@@ -106,6 +106,40 @@ def test_graph_capture_matches_eager(R):
     assert r.stats().n_keys == K
 
 
+def test_two_graphs_share_a_reservation(R):
+    """Two captured steps over different scenes and outputs on one reservation,
+    replayed alternately, each reproduce their eager result."""
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import GraphStep, Renderer, pack_scene
+    sc = synth.make_scene(2500, seed=52, center_half=2.0, n_sigma=16, color="mlp", n_c=32)
+    sc2 = synth.perturb(sc, seed=53, std=0.02)
+    cams = _uneven_views(3, 7.0, seed=4)
+    r = Renderer(0)
+    cfg = L.make_config()
+    P = r.image_size(cams)
+    dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(6))
+    eager, pss = [], []
+    for s_ in (sc, sc2):
+        ps = pack_scene(s_)
+        img = r.forward(ps, cams, cfg).clone()
+        gg = torch.zeros_like(ps.geom)
+        gn = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
+        r.backward(ps, dL, gg, gn)
+        eager.append((img, gg, gn))
+        pss.append(ps)
+    torch.cuda.synchronize()
+    K = max(r.stats().n_keys, 1)
+    steps = [GraphStep(r, pss[0], cams, cfg, max_keys=2 * K + 4096, dL=dL),
+             GraphStep(r, pss[1], cams, cfg, max_keys=0, dL=dL, reserve=False)]
+    for _ in range(2):
+        for st, (img, gg, gn) in zip(steps, eager):
+            st.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(st.image, img)
+            for a, b in ((st.g_geom, gg), (st.g_net, gn)):
+                assert (a - b).abs().max().item() <= 1e-5 * (b.abs().max().item() + 1e-12)
+
+
 def test_capacity_overflow_is_reported(R):
     from paper_2510_08491_gb300 import _lib as L
     from paper_2510_08491_gb300.render import Renderer, pack_scene
