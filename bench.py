@@ -169,6 +169,17 @@ def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True
 
 
 # ----------------------------------------------------------------------------- GPU leg
+# Training hyperparameters of the paper (App. hyperparameters): Adam learning
+# rates per group -- geometry (centres, log-scales, quaternions, constant rgb; the
+# paper gives no rate for a constant colour, so it takes the SH rate) and per
+# network field (snp_net_layout order: the density and colour MLPs at the MLP
+# rate, SH coefficients and their time series at the SH rate, W_t at the MLP
+# rate) -- and the synthetic-scene population-control thresholds.
+PAPER_LR_GEOM = [1.6e-4, 5e-3, 1e-3, 2.5e-3]
+PAPER_LR_NET = [1e-3] * 11 + [2.5e-3, 1e-3, 2.5e-3]
+PAPER_POPCTL_SYNTHETIC = (1e-5, 1e-6, 1e-2, 0.5)  # densify, prune, grow scale, prune scale
+
+
 class TrainState:
     """The rest of a training step after the backward pass: the anisotropy
     regulariser, the population-control statistic and one Adam step (learning
@@ -185,8 +196,8 @@ class TrainState:
         self.ssum = torch.zeros(self.n, dtype=torch.float32, device="cuda")
         self.scnt = torch.zeros(self.n, dtype=torch.int32, device="cuda")
         c = L.AdamConfig()
-        c.lr_geom[:] = [1.6e-4, 5e-3, 1e-3, 2.5e-3]
-        c.lr_net[:] = [1e-3] * 11 + [2.5e-3, 1e-3, 2.5e-3]
+        c.lr_geom[:] = PAPER_LR_GEOM
+        c.lr_net[:] = PAPER_LR_NET
         c.beta1, c.beta2, c.eps, c.step = 0.9, 0.999, 1e-15, 0
         self.cfg = c
         ns, nc = sc.n_sigma, sc.n_c if sc.color == "mlp" else 0
@@ -228,7 +239,7 @@ class TrainState:
         bytes_adam = self.n * (13 * 28 + self.net_cols * b_el)
         t_reg = self._time(lambda: self.r.geom_reg(self.ps, self.reg_weight, g_geom), 20)
         t_stat = self._time(lambda: self.r.popctl_accumulate(self.ps, g_net, self.ssum, self.scnt), 20)
-        pc = L.PopctlConfig(1e-5, 1e-6, 1e-2, 0.5, 4.0, 0)
+        pc = L.PopctlConfig(*PAPER_POPCTL_SYNTHETIC, 4.0, 0)
         noise = torch.randn((self.n, 2, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
 
         def densify():

@@ -185,3 +185,32 @@ def test_adam_matches_torch():
     assert np.abs(mine - ref).max() < 1e-14
     assert np.array_equal(mine[:, 6], p0[:, 6])   # zero rate: untouched
     del p
+
+
+def _golden(name):
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (x.strip() for x in line.split("="))
+            vals[k] = float(v)
+    return vals
+
+
+def test_bench_uses_the_papers_hyperparameters():
+    """The training-step benchmark's Adam rates and population-control thresholds
+    are the paper's (App. hyperparameters), field by field; the dynamic series has
+    the printed number of terms."""
+    import bench
+    g = _golden("paper_hyperparameters.txt")
+    assert bench.PAPER_LR_GEOM[:3] == [g["lr_means"], g["lr_scales"], g["lr_quats"]]
+    net = bench.PAPER_LR_NET
+    assert net[0:4] == [g["lr_mlp"]] * 4           # W1, b1, w2, b2
+    assert net[4:11] == [g["lr_mlp"]] * 7          # colour MLP fields
+    assert net[11] == g["lr_sh"] and net[13] == g["lr_sh"]  # sh, degree-0 series
+    assert bench.PAPER_POPCTL_SYNTHETIC == (g["densify_synthetic"], g["prune_synthetic"], g["grow_scale"],
+                                           g["prune_scale"])
+    from oracle import grad as Gd
+    # the degree-0 series: xi^j (j = 1..n) and cos(j xi), sin(j xi) (j = 1..l)
+    assert len(Gd._time_series(0.3)) == g["series_poly_terms"] + 2 * g["series_fourier_terms"]
