@@ -326,7 +326,7 @@ template <int TS>
 __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk, int stride)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
-    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(stride, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2 * 2);
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(stride, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2);
     return NPIX * (32 + 12) + (size_t)chunk * per_entry;
 }
 
@@ -349,13 +349,12 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     // replace by dL/dalpha_hat (the layout of a colour-store record)
     float4 *s_cs = reinterpret_cast<float4 *>(acc + CH * vg);
     float *s_w = reinterpret_cast<float *>(s_cs + CH * NPIX);  // [CH][NPIX] weights of the composited pairs
-    uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_w + CH * NPIX);  // [CH][NPIX]
-    uint16_t *s_al = s_hl + CH * NPIX;                     // [CH][NPIX]
+    uint16_t *s_al = reinterpret_cast<uint16_t *>(s_w + CH * NPIX);  // [CH][NPIX] pair lists
     __shared__ uint32_t s_gid[kMaxChunk];
     __shared__ uint32_t s_koff[64];         // colour-store offsets of the chunk's keys (two halves)
     __shared__ bool s_stored;               // every composited pair of the chunk is in the store
     __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk (two halves)
-    __shared__ int s_nh[65], s_na[65], s_ph[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
+    __shared__ int s_na[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
     __shared__ int s_item6;  // P6 item counter (items past the first one of each warp)
     __shared__ uint32_t s_maxwalk;
@@ -444,7 +443,6 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             if (tid < cnt) {
-                s_nh[tid] = 0;
                 s_na[tid] = 0;
             }
             if (tid == 0) s_item6 = 0;
