@@ -183,7 +183,9 @@ typedef struct {
  * in a context buffer sized from the previous forward's count) so that the backward
  * does not evaluate the colour network again; with this flag the backward
  * recomputes them (less device memory, slower backward).  Pairs that do not fit the
- * buffer are recomputed either way. */
+ * buffer are recomputed either way.  Test hook: a non-negative integer in the
+ * environment variable SNP_TEST_COLSTORE_PAIRS caps the store at that many pairs
+ * (read at every forward), so tests can drive the recomputation path. */
 #define SNP_FLAG_REPLAY_COLOR 4
 
 /* Stages reported by snp_stage_times. */
