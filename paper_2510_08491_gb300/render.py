@@ -373,6 +373,11 @@ class _RenderFn(torch.autograd.Function):
         return g_geom, g_net, None, None, None, None
 
 
+# The differentiable render under its public name: images as a function of the
+# packed geometry and network tensors (snp_render_forward / snp_render_backward).
+SplatNetRender = _RenderFn
+
+
 def render(renderer: Renderer, ps: PackedScene, cams, cfg: Optional[L.Config] = None) -> torch.Tensor:
     """Differentiable render: images [sum H*W, 3] (views concatenated, HWC) as a function of
     ps.geom and ps.net (set requires_grad on them to get gradients)."""
