@@ -1,15 +1,20 @@
 // snp_raster_bwd.cuh -- backward per-tile rasterizer.
 //
 // Persistent CTAs take tiles as in the forward and walk each tile's list in
-// staged chunks.  Per chunk: the pixels that composited each entry come from the
-// forward's composited masks (P1); alpha_hat and the colour of every composited
-// pair are read back from the forward's colour store, by the rank of the pixel
-// among the entry's composited pixels, or -- where the store was full or is off,
-// and always without a colour network -- recomputed (P2 / P4); each pixel replays
-// its weights and the gradient
-// of its colour with respect to alpha_hat in list order (P3 / P5); then the
-// per-pair gradients run as work items (P6).  With the forward's final colour C
-// (no background) and optical depth tau_f:
+// staged chunks.  Per chunk:
+//   P1     each entry's pair list is its composited pixels in slot order, read
+//          from the forward's composited masks (a pixel's position is its rank
+//          among the mask's set bits);
+//   P2/P4  alpha_hat and the colour of every composited pair are copied back from
+//          the forward's colour store at that rank, or -- where the store was
+//          full or is off, and always without a colour network -- recomputed;
+//   P3/P5  each pixel replays its weights and the gradient of its colour with
+//          respect to alpha_hat in list order;
+//   P6     the per-pair gradients run as work items (colour passes first).
+// The next chunk's record ids, store offsets and masks are copied in during P6,
+// and the flush's bulk reductions read the accumulators while the next chunk
+// starts.  With the forward's final colour C (no background) and optical depth
+// tau_f:
 //   C = sum_i c_i alpha_i T_i + T_f bg,  T_i = exp(-sum_{j<i} alpha_hat_j),
 //   dC/dc_i = alpha_i T_i,
 //   dC/dalpha_hat_i = T_{i+1} c_i - R_i - T_f bg,  R_i = sum_{j>i} c_j alpha_j T_j = C - prefix_i,
