@@ -227,7 +227,9 @@ const char *snp_last_error(const snp_context *ctx);
  * shapes allocates device memory; a forward that would exceed max_keys returns
  * SNP_ERR_CAPACITY instead of growing (required before stream capture).  While
  * reserved, every forward must use the reserved tile size (SNP_ERR_INVALID_ARG
- * otherwise); a later reserve replaces the reservation. */
+ * otherwise); a later reserve replaces the reservation.  max_keys 0 means
+ * min(4 n n_cams + 1024, 2^32 - 1); above 2^32 - 1 the call returns
+ * SNP_ERR_UNSUPPORTED (key offsets are 32-bit). */
 snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_camera *cams, int32_t n_cams,
                        const snp_config *cfg, int64_t max_keys);
 
@@ -239,7 +241,14 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
  * Stages: projection/bounding -> tile-key emission -> stable radix sort by
  * (tile, depth) -> tile ranges -> per-tile rasterization.  Outside of a
  * reservation the call synchronises once on `stream` to read back the key
- * count. */
+ * count.
+ * Limits: n * n_cams <= 2^32 - 1 (the key value is the instance v * n + i),
+ * else SNP_ERR_UNSUPPORTED before any work.  The key offsets are scanned in
+ * 32 bits: a total of 2^32 or more tile keys (one per tile that a primitive's
+ * rectangle covers, per view) wraps, and the instance whose keys straddle 2^32
+ * then ends past the key count, so the emission flags it like a capacity
+ * overflow (snp_get_stats returns SNP_ERR_CAPACITY; the image is not valid).
+ * Every write stays inside the buffers either way. */
 snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, const snp_scene_ptrs *scene,
                               const snp_camera *cams, int32_t n_cams, const snp_config *cfg, float *images,
                               int64_t *token, void *stream);

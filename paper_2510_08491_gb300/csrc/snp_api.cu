@@ -264,6 +264,16 @@ static snp_status check_cams(snp_context *ctx, const snp_camera *cams, int n_cam
     return SNP_OK;
 }
 
+// A tile key's value is the (view, primitive) instance v * n + i and the key offsets
+// are scanned in 32 bits, so both must fit in uint32.
+static snp_status check_instances(snp_context *ctx, int64_t n, int n_cams)
+{
+    if (n * (int64_t)n_cams > (int64_t)0xffffffff)
+        return fail(ctx, SNP_ERR_UNSUPPORTED, "n x views = %lld exceeds the 32-bit instance index",
+                    (long long)(n * (int64_t)n_cams));
+    return SNP_OK;
+}
+
 // Fill the pinned view table for these cameras; returns tiles and pixels.
 static snp_status build_views(snp_context *ctx, const snp_camera *cams, int n_cams, int ts, int64_t *tiles,
                               int64_t *pixels)
@@ -468,12 +478,15 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
     snp_status s;
     if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
     if ((s = check_cams(ctx, cams, n_cams)) != SNP_OK) return s;
+    if ((s = check_instances(ctx, desc->n, n_cams)) != SNP_OK) return s;
     const int ts = cfg && cfg->tile_size ? cfg->tile_size : 16;
     if (ts != 8 && ts != 16 && ts != 32) return fail(ctx, SNP_ERR_UNSUPPORTED, "tile_size %d not built", ts);
+    if (max_keys <= 0) max_keys = std::min<int64_t>(4 * desc->n * n_cams + 1024, (int64_t)0xffffffff);
+    if (max_keys > (int64_t)0xffffffff)
+        return fail(ctx, SNP_ERR_UNSUPPORTED, "max_keys %lld exceeds 2^32 - 1", (long long)max_keys);
     int64_t tiles, pixels;
     ctx->reserved = false;
     if ((s = build_views(ctx, cams, n_cams, ts, &tiles, &pixels)) != SNP_OK) return s;
-    if (max_keys <= 0) max_keys = 4 * desc->n * n_cams + 1024;
     if ((s = ensure_frame(ctx, desc->n, n_cams, tiles, pixels, desc)) != SNP_OK) return s;
     if ((s = ensure_keys(ctx, max_keys, ts)) != SNP_OK) return s;
     if ((s = ensure_scan_tmp(ctx, desc->n * n_cams, max_keys, tiles)) != SNP_OK) return s;
@@ -507,6 +520,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     snp_status s;
     if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
     if ((s = check_cams(ctx, cams, n_cams)) != SNP_OK) return s;
+    if ((s = check_instances(ctx, desc->n, n_cams)) != SNP_OK) return s;
     if (!scene || !images || (desc->n > 0 && (!scene->geom || !scene->net)))
         return fail(ctx, SNP_ERR_INVALID_ARG, "null scene or image pointer");
     if (((uintptr_t)scene->geom & 15) || ((uintptr_t)scene->net & 15))

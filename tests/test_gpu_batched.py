@@ -186,3 +186,29 @@ def test_reserved_context_rejects_another_tile_size(R):
     assert ei.value.status == L.SNP_ERR_INVALID_ARG
     img = r.forward(ps, cams, L.make_config(tile_size=16))
     assert torch.isfinite(img).all()
+
+
+def test_reserve_rejects_32bit_index_overflow(R):
+    """The key value v * n + i and the key offsets are 32-bit: a reservation for more
+    than 2^32 - 1 instances or keys is refused before any allocation or launch, and
+    leaves the context usable."""
+    import copy
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import Renderer, pack_scene
+    sc = synth.make_scene(300, seed=91, center_half=1.5, n_sigma=8)
+    r = Renderer(0)
+    ps = pack_scene(sc)
+    big = copy.copy(ps)
+    big.desc = L.SceneDesc.from_buffer_copy(ps.desc)
+    big.desc.n = 1 << 27
+    cams33 = synth.ring_cameras(33, 6.0, 16, 16)   # 33 * 2^27 > 2^32 - 1
+    with pytest.raises(L.SnpError) as ei:
+        r.reserve(big, cams33, L.make_config())
+    assert ei.value.status == L.SNP_ERR_UNSUPPORTED
+    cams = synth.ring_cameras(1, 6.0, 96, 64)
+    with pytest.raises(L.SnpError) as ei:
+        r.reserve(ps, cams, L.make_config(), max_keys=1 << 32)
+    assert ei.value.status == L.SNP_ERR_UNSUPPORTED
+    img = r.forward(ps, cams, L.make_config())
+    ref = R.forward(ps, cams, L.make_config())
+    assert torch.equal(img, ref)
