@@ -261,7 +261,8 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
  * (final optical depth, colour, number of entries walked); gradients flow to
  * centres, log-scales, quaternions (through the normalisation), constant
  * colours and every density and colour-MLP weight.  SNP_ERR_INVALID_ARG if a
- * later forward replaced the saved state. */
+ * later forward replaced the saved state, if desc differs from the forward's,
+ * or if grads->net is not 16-byte aligned (it receives bulk reductions). */
 snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_desc *desc,
                                const snp_scene_ptrs *scene, const float *dL_dimages, const snp_grad_ptrs *grads,
                                void *stream);

@@ -714,9 +714,15 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     snp_status s;
     if ((s = check_desc(ctx, desc)) != SNP_OK) return s;
     if (desc->n != ctx->desc.n || desc->n_sigma != ctx->desc.n_sigma || desc->color_mode != ctx->desc.color_mode ||
-        desc->n_c != ctx->desc.n_c || desc->weight_dtype != ctx->desc.weight_dtype)
+        desc->n_c != ctx->desc.n_c || desc->weight_dtype != ctx->desc.weight_dtype ||
+        desc->dynamic != ctx->desc.dynamic || desc->omega0 != ctx->desc.omega0)
         return fail(ctx, SNP_ERR_INVALID_ARG, "scene description differs from the forward's");
-    if (!scene || !dL_dimages || !grads) return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    if (!scene || !dL_dimages || !grads || (desc->n > 0 && (!scene->geom || !scene->net)))
+        return fail(ctx, SNP_ERR_INVALID_ARG, "null pointer");
+    if ((((uintptr_t)scene->geom) | ((uintptr_t)scene->net) | ((uintptr_t)grads->net)) & 15u)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "scene arrays and the network gradient must be 16-byte aligned");
+    if ((((uintptr_t)grads->geom) | ((uintptr_t)dL_dimages)) & 3u)
+        return fail(ctx, SNP_ERR_INVALID_ARG, "the geometry gradient and dL/dimages must be 4-byte aligned");
     const int64_t n = desc->n, vn = n * ctx->n_views;
     const int nc = desc->color_mode == SNP_COLOR_MLP ? desc->n_c : 1;
     ENS(g_view, (size_t)vn * kGvFloats * 4);

@@ -212,3 +212,28 @@ def test_reserve_rejects_32bit_index_overflow(R):
     img = r.forward(ps, cams, L.make_config())
     ref = R.forward(ps, cams, L.make_config())
     assert torch.equal(img, ref)
+
+
+def test_backward_refuses_a_description_other_than_the_forwards(R):
+    """The backward replays the forward's lists with the forward's layout: a scene
+    description that differs from the forward's (here only in omega0, which changes
+    no array size) is refused before any launch."""
+    import copy
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import Renderer, pack_scene
+    sc = synth.make_scene(300, seed=93, center_half=1.5, n_sigma=8)
+    cams = synth.ring_cameras(1, 6.0, 96, 64)
+    r = Renderer(0)
+    ps = pack_scene(sc)
+    img = r.forward(ps, cams, L.make_config())
+    other = copy.copy(ps)
+    other.desc = L.SceneDesc.from_buffer_copy(ps.desc)
+    other.desc.omega0 = float(ps.desc.omega0) * 2.0
+    g_geom = torch.zeros_like(ps.geom)
+    with pytest.raises(L.SnpError) as ei:
+        r.backward(other, torch.ones_like(img), g_geom, None)
+    assert ei.value.status == L.SNP_ERR_INVALID_ARG
+    assert not torch.any(g_geom)
+    r.backward(ps, torch.ones_like(img), g_geom, None)
+    torch.cuda.synchronize()
+    assert torch.isfinite(g_geom).all() and torch.any(g_geom)
