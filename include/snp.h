@@ -222,14 +222,15 @@ void snp_destroy(snp_context *ctx);
 const char *snp_last_error(const snp_context *ctx);
 
 /* Pre-allocate every workspace buffer for scenes of this description, these
- * cameras and configuration, with room for max_keys tile keys (0 = estimate:
- * grow on demand).  After a successful reserve no render call on the same
- * shapes allocates device memory; a forward that would exceed max_keys returns
- * SNP_ERR_CAPACITY instead of growing (required before stream capture).  While
- * reserved, every forward must use the reserved tile size (SNP_ERR_INVALID_ARG
- * otherwise); a later reserve replaces the reservation.  max_keys 0 means
+ * cameras and configuration, with room for max_keys tile keys (0: the estimate
  * min(4 n n_cams + 1024, 2^32 - 1); above 2^32 - 1 the call returns
- * SNP_ERR_UNSUPPORTED (key offsets are 32-bit). */
+ * SNP_ERR_UNSUPPORTED, since key offsets are 32-bit).  After a successful
+ * reserve no render call on the same shapes allocates device memory or
+ * synchronises, which stream capture requires.  A reserved forward whose keys
+ * exceed max_keys drops the excess and flags it; the next snp_get_stats or
+ * snp_debug_keys on it returns SNP_ERR_CAPACITY, and its image is not valid.
+ * While reserved, every forward must use the reserved tile size
+ * (SNP_ERR_INVALID_ARG otherwise); a later reserve replaces the reservation. */
 snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_camera *cams, int32_t n_cams,
                        const snp_config *cfg, int64_t max_keys);
 
