@@ -6,6 +6,11 @@ the colour against its definition.
   for these polynomials (Gauss-Legendre in cos(theta) x uniform in phi).
 * Addition theorem, per band l: sum_m Y_lm(u) Y_lm(w) = (2l + 1) / (4 pi) P_l(u . w),
   which fixes every constant and sign inside a band up to a common orthogonal map.
+* Against scipy's complex harmonics: the real (tesseral) form
+  Y_lm = sqrt(2) (-1)^m Re Y_l^m (m > 0), Y_l0, sqrt(2) (-1)^m Im Y_l^|m| (m < 0),
+  at index l^2 + l + m; the (-1)^m cancels scipy's Condon-Shortley phase, so every
+  constant is positive.  This fixes the order and sign of each function inside a band,
+  which the two properties above leave open.
 * The C and torch (gradient) oracles evaluate the same basis.
 """
 import math
@@ -49,6 +54,27 @@ def test_addition_theorem_per_band(oracle_lib):
             lhs = float(Yu[band] @ Yw[band])
             rhs = (2 * l + 1) / (4 * math.pi) * P[l](float(u @ w))
             assert abs(lhs - rhs) < 1e-13
+
+
+def test_basis_is_the_real_form_of_scipys_harmonics(oracle_lib):
+    from scipy.special import sph_harm_y
+    O = oracle_lib
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        theta, phi = math.acos(v[2]), math.atan2(v[1], v[0])
+        Y = O.sh_basis(v)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                c = complex(sph_harm_y(l, abs(m), theta, phi))
+                if m > 0:
+                    ref = math.sqrt(2) * (-1) ** m * c.real
+                elif m < 0:
+                    ref = math.sqrt(2) * (-1) ** m * c.imag
+                else:
+                    ref = c.real
+                assert abs(Y[l * l + l + m] - ref) < 1e-13, (l, m)
 
 
 def test_torch_basis_equals_c_basis(oracle_lib):
