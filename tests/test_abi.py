@@ -46,3 +46,56 @@ def test_net_layout_is_aligned_and_complete():
     assert offs_dc[12] == 48 and offs_dc[13] == -1 and stride_dc == 56
     with pytest.raises(L.SnpError):
         L.net_layout(8, L.COLOR_MLP, 32, dynamic=True)
+
+
+def test_argument_errors_are_reported_before_any_device_work():
+    """Calls with a null context, a bad description or bad sizes fail with the
+    documented status before they touch the CUDA runtime (so they run here too)."""
+    from paper_2510_08491_gb300 import build
+    build.build()
+    lib = L.lib()
+    bad = L.SNP_ERR_INVALID_ARG
+    null = None
+    assert lib.snp_reserve(null, null, null, 1, null, 0) == bad
+    assert lib.snp_render_forward(null, null, null, null, 1, null, null, null, null) == bad
+    assert lib.snp_render_backward(null, 1, null, null, null, null, null) == bad
+    assert lib.snp_get_stats(null, 1, null, null) == bad
+    assert lib.snp_debug_keys(null, 1, null, null, 0, null, null) == bad
+    assert lib.snp_stage_times(null, null, null, 0) == bad
+    assert lib.snp_autotune(null, null, null, null, 1, null, 0, null, null, null) == bad
+    assert lib.snp_mse_loss(null, null, null, 0, null, null, null) == bad
+    assert lib.snp_popctl_accumulate(null, null, null, null, null, null) == bad
+    assert lib.snp_popctl_plan(null, null, null, null, null, null, null, null, null, null) == bad
+    assert lib.snp_popctl_apply(null, null, null, null, null, null, null, null, null) == bad
+    assert lib.snp_geom_reg(null, null, null, 1.0, null, null, null) == bad
+    assert lib.snp_adam_step(null, null, null, null, null, null, null, null, null, null, null, null) == bad
+    assert lib.snp_create(0, null) == bad
+    lib.snp_destroy(null)
+    assert lib.snp_last_error(null) == b"null context"
+
+    # scene descriptions: the layout query runs the same checks as every call
+    def desc(**kw):
+        d = L.SceneDesc()
+        d.n, d.n_sigma, d.color_mode, d.n_c, d.weight_dtype, d.omega0, d.dynamic = 10, 8, L.COLOR_CONST, 0, 0, 30.0, 0
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+    out = L.NetLayout()
+    assert lib.snp_get_net_layout(ctypes.byref(desc()), ctypes.byref(out)) == L.SNP_OK
+    assert lib.snp_get_net_layout(null, ctypes.byref(out)) == bad
+    for kw in ({"n": -1}, {"n": (1 << 28) + 1}, {"n_sigma": 0}, {"n_sigma": 65}, {"color_mode": 7},
+               {"weight_dtype": 5}, {"dynamic": 2}):
+        assert lib.snp_get_net_layout(ctypes.byref(desc(**kw)), ctypes.byref(out)) == bad, kw
+    for kw in ({"color_mode": L.COLOR_MLP, "n_c": 48}, {"color_mode": L.COLOR_MLP, "n_c": 32, "dynamic": 1}):
+        assert lib.snp_get_net_layout(ctypes.byref(desc(**kw)), ctypes.byref(out)) == L.SNP_ERR_UNSUPPORTED, kw
+
+    # the allocation-free sort validates sizes before it looks for a device
+    raw = ctypes.CDLL(build.LIB)
+    f = raw.snp_sort_pairs_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]
+    f.restype = ctypes.c_int32
+    assert f(null, null, -1, 32, null) == bad
+    assert f(null, null, 4, 0, null) == bad
+    assert f(null, null, 4, 65, null) == bad
+    assert f(null, null, (1 << 20) + 1, 32, null) == L.SNP_ERR_CAPACITY
+    assert f(null, null, 4, 32, null) == bad
