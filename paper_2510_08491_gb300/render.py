@@ -19,6 +19,31 @@ from . import _lib as L
 NET_FIELDS = ("W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3", "sh", "wt", "sh_t")
 
 
+def _need(t: Optional[torch.Tensor], rows: int, cols: int, dtypes, name: str, device: bool = True) -> None:
+    """Check an array handed to the library: on the GPU, contiguous, of one of
+    `dtypes`, at least `rows` rows of `cols` elements (a 2-D tensor must have exactly
+    `cols` columns).  The C ABI takes plain pointers and cannot see sizes, so a
+    mismatch would otherwise become out-of-bounds device accesses.  None passes."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected one of {tuple(dtypes)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.dim() == 2 and t.shape[1] != cols:
+        raise ValueError(f"{name}: {t.shape[1]} columns, expected {cols}")
+    if t.numel() < rows * cols:
+        raise ValueError(f"{name}: {t.numel()} elements, expected at least {rows} x {cols}")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+
+
+_F32 = (torch.float32,)
+_I32 = (torch.int32,)
+
+
 @dataclass
 class PackedScene:
     """Device arrays in the library's layout plus their description."""
@@ -35,6 +60,19 @@ class PackedScene:
 
     def ptrs(self) -> L.ScenePtrs:
         return L.ScenePtrs(self.geom.data_ptr() if self.n else None, self.net.data_ptr() if self.n else None)
+
+    def validate(self) -> None:
+        """Raise ValueError unless the arrays match the description: geometry float32
+        [n, 16], network [n, stride] in the description's weight type and layout."""
+        d = self.desc
+        offs, stride = L.net_layout(int(d.n_sigma), int(d.color_mode), int(d.n_c), bool(d.dynamic))
+        if stride != self.stride or list(offs) != list(self.offsets):
+            raise ValueError("network layout differs from the scene description's")
+        _need(self.geom, self.n, L.GEOM_STRIDE, _F32, "geom", device=False)
+        _need(self.net, self.n, stride, (torch.bfloat16,) if d.weight_dtype == L.BF16 else _F32, "net", device=False)
+        for t, name in ((self.geom, "geom"), (self.net, "net")):
+            if not t.is_cuda:
+                raise ValueError(f"{name}: expected a CUDA tensor")
 
 
 def pack_scene(scene, device="cuda", weight_dtype: Optional[str] = None) -> PackedScene:
@@ -134,10 +172,12 @@ class Renderer:
     def forward(self, ps: PackedScene, cams, cfg: Optional[L.Config] = None, out: Optional[torch.Tensor] = None,
                 stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
         cfg = cfg or L.make_config()
+        ps.validate()
         carr = L.make_cameras(cams)
         P = self.image_size(cams)
         if out is None:
             out = torch.empty((P, 3), dtype=torch.float32, device=self.device)
+        _need(out, P, 3, _F32, "out")
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         tok = C.c_int64()
         sp = ps.ptrs()
@@ -145,17 +185,23 @@ class Renderer:
                                                   C.byref(cfg), C.c_void_p(out.data_ptr()), C.byref(tok),
                                                   C.c_void_p(st)))
         self.token = tok.value
+        self._pixels = P
         return out
 
     def backward(self, ps: PackedScene, dL: torch.Tensor, g_geom: Optional[torch.Tensor],
                  g_net: Optional[torch.Tensor], token: Optional[int] = None,
                  stream: Optional[torch.cuda.Stream] = None):
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        ps.validate()
+        dL = dL.contiguous()
+        _need(dL, getattr(self, "_pixels", 0), 3, _F32, "dL")
+        _need(g_geom, ps.n, L.GEOM_STRIDE, _F32, "g_geom")
+        _need(g_net, ps.n, ps.stride, _F32, "g_net")
         gp = L.GradPtrs(g_geom.data_ptr() if g_geom is not None else None,
                         g_net.data_ptr() if g_net is not None else None)
         sp = ps.ptrs()
         self.ctx.check(L.lib().snp_render_backward(self.ctx.handle, int(token or self.token), C.byref(ps.desc),
-                                                   C.byref(sp), C.c_void_p(dL.contiguous().data_ptr()),
+                                                   C.byref(sp), C.c_void_p(dL.data_ptr()),
                                                    C.byref(gp), C.c_void_p(st)))
 
     def mse_loss(self, image: torch.Tensor, target: torch.Tensor, dL: Optional[torch.Tensor] = None,
@@ -182,6 +228,10 @@ class Renderer:
     def popctl_accumulate(self, ps: PackedScene, g_net: torch.Tensor, stat_sum: torch.Tensor,
                           stat_count: torch.Tensor, stream=None):
         """Add this step's density-network gradient norm per primitive (snp_popctl_accumulate)."""
+        ps.validate()
+        _need(g_net, ps.n, ps.stride, _F32, "g_net")
+        _need(stat_sum, ps.n, 1, _F32, "stat_sum")
+        _need(stat_count, ps.n, 1, _I32, "stat_count")
         self.ctx.check(L.lib().snp_popctl_accumulate(self.ctx.handle, C.byref(ps.desc), C.c_void_p(g_net.data_ptr()),
                                                      C.c_void_p(stat_sum.data_ptr()),
                                                      C.c_void_p(stat_count.data_ptr()), self._st(stream)))
@@ -190,6 +240,9 @@ class Renderer:
                     stream=None):
         """Per-primitive actions and output offsets (snp_popctl_plan); returns (action, offset, n_out)."""
         n = ps.n
+        ps.validate()
+        _need(stat_sum, n, 1, _F32, "stat_sum")
+        _need(stat_count, n, 1, _I32, "stat_count")
         action = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
         offset = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)  # uint32 bits
         n_out = C.c_int64(0)
@@ -202,6 +255,10 @@ class Renderer:
     def popctl_apply(self, ps: PackedScene, action: torch.Tensor, offset: torch.Tensor, n_out: int,
                      noise: torch.Tensor, stream=None) -> PackedScene:
         """The new scene of a plan (snp_popctl_apply); noise is float32 [n, 2, 3] standard normal."""
+        ps.validate()
+        _need(action, ps.n, 1, _I32, "action")
+        _need(offset, ps.n, 1, _I32, "offset")
+        _need(noise, ps.n, 6, _F32, "noise")
         geom = torch.empty((max(n_out, 1), L.GEOM_STRIDE), dtype=torch.float32, device=self.device)
         net = torch.empty((max(n_out, 1), ps.stride), dtype=ps.net.dtype, device=self.device)
         self.ctx.check(L.lib().snp_popctl_apply(self.ctx.handle, C.byref(ps.desc), C.byref(ps.ptrs()),
@@ -216,6 +273,9 @@ class Renderer:
                  loss: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """Anisotropy regulariser (snp_geom_reg): returns the loss [1]; adds its gradient into g_geom."""
         loss = torch.empty(1, dtype=torch.float32, device=self.device) if loss is None else loss
+        _need(ps.geom, ps.n, L.GEOM_STRIDE, _F32, "geom")
+        _need(g_geom, ps.n, L.GEOM_STRIDE, _F32, "g_geom")
+        _need(loss, 1, 1, _F32, "loss")
         self.ctx.check(L.lib().snp_geom_reg(self.ctx.handle, C.byref(ps.desc), C.c_void_p(ps.geom.data_ptr()),
                                             float(weight), C.c_void_p(g_geom.data_ptr() if g_geom is not None else None),
                                             C.c_void_p(loss.data_ptr()), self._st(stream)))
@@ -226,6 +286,11 @@ class Renderer:
         """One fused Adam step over the geometry and network arrays (snp_adam_step)."""
         def ptr(t):
             return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p()
+        ps.validate()
+        for t, name in ((g_geom, "g_geom"), (m_geom, "m_geom"), (v_geom, "v_geom")):
+            _need(t, ps.n, L.GEOM_STRIDE, _F32, name)
+        for t, name in ((g_net, "g_net"), (m_net, "m_net"), (v_net, "v_net"), (net_master, "net_master")):
+            _need(t, ps.n, ps.stride, _F32, name)
         g = L.GradPtrs(g_geom.data_ptr() if g_geom is not None else None,
                        g_net.data_ptr() if g_net is not None else None)
         self.ctx.check(L.lib().snp_adam_step(self.ctx.handle, C.byref(ps.desc), ptr(ps.geom), ptr(ps.net),
@@ -265,13 +330,15 @@ class Renderer:
         import json
         import os
         cfg = cfg or L.make_config()
+        ps.validate()
         key = "|".join(str(x) for x in (torch.cuda.get_device_name(self.device), ps.n, ps.desc.n_sigma,
-                                        ps.desc.color_mode, ps.desc.n_c, ps.desc.weight_dtype, cfg.integral_form,
-                                        int(backward), tuple((c.width, c.height) for c in cams)))
+                                        ps.desc.color_mode, ps.desc.n_c, ps.desc.weight_dtype, ps.desc.dynamic,
+                                        cfg.integral_form, int(backward), tuple((c.width, c.height) for c in cams)))
         cache = {}
         if cache_path and os.path.exists(cache_path):
             try:
-                cache = json.load(open(cache_path))
+                with open(cache_path) as f:
+                    cache = json.load(f)
             except Exception:
                 cache = {}
         if key in cache:

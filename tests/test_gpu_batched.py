@@ -237,3 +237,30 @@ def test_backward_refuses_a_description_other_than_the_forwards(R):
     r.backward(ps, torch.ones_like(img), g_geom, None)
     torch.cuda.synchronize()
     assert torch.isfinite(g_geom).all() and torch.any(g_geom)
+
+
+def test_wrong_sized_arrays_are_refused_before_any_launch(R):
+    """The binding checks array sizes against the scene description (the ABI sees
+    only pointers).  The short arrays here are views of full-size allocations, so
+    nothing could be read out of bounds even without the check."""
+    import copy
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene
+    sc = synth.make_scene(300, seed=95, center_half=1.5, n_sigma=8)
+    cams = synth.ring_cameras(1, 6.0, 96, 64)
+    ps = pack_scene(sc)
+    bad = copy.copy(ps)
+    bad.geom = ps.geom[:200]
+    n0 = L.kernel_launches()
+    with pytest.raises(ValueError):
+        R.forward(bad, cams, L.make_config())
+    assert L.kernel_launches() == n0
+    img = R.forward(ps, cams, L.make_config())
+    g_geom = torch.zeros_like(ps.geom)
+    n1 = L.kernel_launches()
+    with pytest.raises(ValueError):
+        R.backward(ps, img[:100], g_geom, None)
+    with pytest.raises(ValueError):
+        R.backward(ps, torch.ones_like(img), g_geom[:200], None)
+    assert L.kernel_launches() == n1
+    assert not torch.any(g_geom)
