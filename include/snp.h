@@ -431,19 +431,22 @@ snp_status snp_adam_step(snp_context *ctx, const snp_scene_desc *desc, float *ge
  * service).  Sorts n (key, value) pairs in place by the low key_bits bits of the
  * key, stably (equal keys keep their input order) -- the same LSD radix sort
  * that orders the tile keys inside snp_render_forward.
- *   keys, vals  device arrays of n elements, caller-owned (read and rewritten)
- *   key_bits    1..64; higher key bits are ignored for the order
+ *   keys, vals  device arrays of n elements, caller-owned (read and rewritten);
+ *               keys 8-byte and vals 4-byte aligned
+ *   key_bits    1..64; key bits at and above key_bits do not affect the order
+ *               (they are carried along unchanged)
  *   stream      cudaStream_t; the call is asynchronous on it
- * For callers that must not allocate device memory while they run (inside a
- * region being captured into a CUDA graph, inside an application whose memory
- * pool owns the device, or in loops that cannot take cudaMalloc's implicit
- * synchronisation): it needs no context and calls no cudaMalloc / cudaFree.  Its
- * scratch is one static device array of SNP_NOALLOC_SORT_BYTES that every device
- * loading the library keeps until the process exits.  The first call on a device
- * looks up that array's address (make it before any stream capture).  All calls
- * share the array: calls that overlap on the GPU race.  Returns
- * SNP_ERR_CAPACITY when n > SNP_NOALLOC_SORT_MAX, SNP_ERR_INVALID_ARG for bad
- * pointers or key_bits, SNP_ERR_CUDA if a CUDA call fails. */
+ * For callers that must not allocate device memory while they run (inside an
+ * application whose memory pool owns the device, a plugin handed a fixed arena,
+ * or loops that cannot take cudaMalloc's implicit synchronisation): it needs no
+ * context and calls no cudaMalloc / cudaFree.  Its scratch is one static device
+ * array of SNP_NOALLOC_SORT_BYTES that every device loading the library keeps
+ * until the process exits.  The first call on a device looks up that array's
+ * address (make it before any stream capture).  All calls share the array: calls
+ * that overlap on the GPU race.  Returns SNP_ERR_CAPACITY when
+ * n > SNP_NOALLOC_SORT_MAX, SNP_ERR_INVALID_ARG for null or misaligned pointers
+ * or a bad key_bits (before any device work), SNP_ERR_CUDA if a CUDA call
+ * fails. */
 #define SNP_NOALLOC_SORT_MAX (1 << 20)
 #define SNP_NOALLOC_SORT_BYTES (13 << 20)
 snp_status snp_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t n, int32_t key_bits, void *stream);

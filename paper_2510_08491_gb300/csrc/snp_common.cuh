@@ -37,9 +37,11 @@ constexpr int kRecInvM = 21;  // 1: 1 / m
 constexpr int kRecOcm = 22;   // 3: (eye - c) / m  (literal Eq. 8 phases only)
 constexpr int kRecRgb = 25;   // 3: constant colour
 constexpr int kRecDepth = 28; // 1: camera-frame z of the centre (FP32 key value)
-constexpr int kRecGlo = 32;   // 9: FP64 remainders of G (G = hi + lo)
-constexpr int kRecElo = 41;   // 3: FP64 remainders of e
-constexpr int kRecMzlo = 44;  // 1: FP64 remainder of mu_z
+// 12: h^2 A = |e + f|^2 - mu_z^2 |e x f|^2 as a quadratic in the pixel offset
+// (X, Y) = (px + .5 - U_c, py + .5 - V_c):  c0 + c1 X + c2 Y + c3 X^2 + c4 X Y + c5 Y^2,
+// each coefficient an FP64 value split into float hi + lo, stored as
+// [c0h c1h c2h c3h] [c4h c5h c0l c1l] [c2l c3l c4l c5l]
+constexpr int kRecQ = 32;
 constexpr int kRecFloats = 48;
 
 // Per (view, primitive) gradient record (floats): d/dG columns 0 and 1 (6, row-major
@@ -80,7 +82,7 @@ __device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
 
 // Per-pixel ray data: pixel-centre coordinates (exact in FP32) and the
 // unnormalised world direction g = R_wc^T ((px+.5-cx)/fx, (py+.5-cy)/fy, 1) with
-// its length, evaluated in FP64 once per pixel and rounded.
+// its length, in FP32 (px + .5 - cx is exact; a few ulp on g and |g|).
 struct PixRay {
     float pxh, pyh, gn;
     float3 g;
@@ -91,13 +93,11 @@ __device__ __forceinline__ PixRay pixel_ray(const View &v, int px, int py)
     PixRay r;
     r.pxh = (float)px + 0.5f;
     r.pyh = (float)py + 0.5f;
-    const double x = ((double)px + 0.5 - (double)v.cx) / (double)v.fx;
-    const double y = ((double)py + 0.5 - (double)v.cy) / (double)v.fy;
-    const double gx = (double)v.R[0] * x + (double)v.R[3] * y + (double)v.R[6];
-    const double gy = (double)v.R[1] * x + (double)v.R[4] * y + (double)v.R[7];
-    const double gz = (double)v.R[2] * x + (double)v.R[5] * y + (double)v.R[8];
-    r.g = make_float3((float)gx, (float)gy, (float)gz);
-    r.gn = (float)sqrt(gx * gx + gy * gy + gz * gz);
+    const float x = __fdiv_rn(r.pxh - v.cx, v.fx);
+    const float y = __fdiv_rn(r.pyh - v.cy, v.fy);
+    r.g = make_float3(fmaf(v.R[0], x, fmaf(v.R[3], y, v.R[6])), fmaf(v.R[1], x, fmaf(v.R[4], y, v.R[7])),
+                      fmaf(v.R[2], x, fmaf(v.R[5], y, v.R[8])));
+    r.gn = __fsqrt_rn(fmaf(r.g.x, r.g.x, fmaf(r.g.y, r.g.y, r.g.z * r.g.z)));
     return r;
 }
 

@@ -5,11 +5,11 @@
 // workspace.
 //
 // Who needs it: callers that must not allocate device memory while they run --
-// code inside a region that is being captured into a CUDA graph, renderers
-// embedded in an application whose memory pool owns the whole device, or
-// real-time loops that cannot afford the implicit device synchronisation of
-// cudaMalloc / cudaFree.  They pass their own key and value arrays; nothing else
-// is needed.
+// renderers embedded in an application whose memory pool owns the whole device
+// (a cudaMalloc there fails or steals the pool's memory), plugins that are handed
+// a fixed arena and nothing else, or real-time loops that cannot afford the
+// implicit device synchronisation of cudaMalloc / cudaFree.  They pass their own
+// key and value arrays; nothing else is needed.
 //
 // The array is SNP_NOALLOC_SORT_BYTES large and lives on every device that loads
 // the library until the process exits.  All calls share it and it keeps what the
@@ -81,6 +81,8 @@ extern "C" snp_status snp_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int
     if (n < 0 || key_bits < 1 || key_bits > 64) return SNP_ERR_INVALID_ARG;
     if (n > kNoallocMax) return SNP_ERR_CAPACITY;
     if (n > 0 && (!keys || !vals)) return SNP_ERR_INVALID_ARG;
+    // element alignment: a misaligned pointer would fault on the device instead
+    if (((uintptr_t)keys & 7u) != 0 || ((uintptr_t)vals & 3u) != 0) return SNP_ERR_INVALID_ARG;
     unsigned char *base = nullptr;
     snp_status s = scratch_on_current_device(&base);
     if (s != SNP_OK) return s;

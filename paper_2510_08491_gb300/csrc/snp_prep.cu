@@ -189,25 +189,43 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ geom,
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             G[a][b] = (Rq[0][a] * Rw[b][0] + Rq[1][a] * Rw[b][1] + Rq[2][a] * Rw[b][2]) / sd[a];
+    double e[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const float hi = (float)G[a][b];
-            r[kRecG + 3 * a + b] = hi;
-            r[kRecGlo + 3 * a + b] = (float)(G[a][b] - (double)hi);
-        }
-        const double ea = G[a][0] * rc[0] + G[a][1] * rc[1] + G[a][2];
-        r[kRecE + a] = (float)ea;
-        r[kRecElo + a] = (float)(ea - (double)(float)ea);
+        for (int b = 0; b < 3; ++b) r[kRecG + 3 * a + b] = (float)G[a][b];
+        e[a] = G[a][0] * rc[0] + G[a][1] * rc[1] + G[a][2];
+        r[kRecE + a] = (float)e[a];
         // R_wc^T r_c / m
         r[kRecAc + a] = (float)((Rw[0][a] * rc[0] + Rw[1][a] * rc[1] + Rw[2][a]) / md);
         r[kRecOcm + a] = (float)(-dc[a] / md);
         r[kRecRgb + a] = rgb[a];
     }
-    r[kRecMz] = (float)mud[2];
-    r[kRecMzlo] = (float)(mud[2] - (double)(float)mud[2]);
-    r[kRecMz2] = (float)(mud[2] * mud[2]);
+    const double mz = mud[2], mz2 = mz * mz;
+    r[kRecMz] = (float)mz;
+    r[kRecMz2] = (float)mz2;
+    // h^2 A = |e + f|^2 - mu_z^2 |e x f|^2 with f = G0 dx + G1 dy (columns 0, 1 of G),
+    // dx = X / fx, dy = Y / fy: a quadratic in the pixel offset (X, Y)
+    {
+        const double G0[3] = {G[0][0], G[1][0], G[2][0]}, G1[3] = {G[0][1], G[1][1], G[2][1]};
+        const double x0[3] = {e[1] * G0[2] - e[2] * G0[1], e[2] * G0[0] - e[0] * G0[2], e[0] * G0[1] - e[1] * G0[0]};
+        const double x1[3] = {e[1] * G1[2] - e[2] * G1[1], e[2] * G1[0] - e[0] * G1[2], e[0] * G1[1] - e[1] * G1[0]};
+        auto dot = [](const double *u, const double *v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+        const double ifx = 1.0 / (double)V.fx, ify = 1.0 / (double)V.fy;
+        const double c[6] = {dot(e, e),
+                             2.0 * dot(e, G0) * ifx,
+                             2.0 * dot(e, G1) * ify,
+                             (dot(G0, G0) - mz2 * dot(x0, x0)) * ifx * ifx,
+                             2.0 * (dot(G0, G1) - mz2 * dot(x0, x1)) * ifx * ify,
+                             (dot(G1, G1) - mz2 * dot(x1, x1)) * ify * ify};
+        const int hi_slot[6] = {0, 1, 2, 3, 4, 5}, lo_slot[6] = {6, 7, 8, 9, 10, 11};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float hi = (float)c[k];
+            r[kRecQ + hi_slot[k]] = hi;
+            r[kRecQ + lo_slot[k]] = (float)(c[k] - (double)hi);
+        }
+    }
     const double uc = (double)V.cx + (double)V.fx * rc[0];
     const double vc = (double)V.cy + (double)V.fy * rc[1];
     const float uhi = (float)uc, vhi = (float)vc;
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ geom,
     r[kRecInvM] = (float)(1.0 / md);
     r[kRecDepth] = mu[2];
     r[29] = r[30] = r[31] = 0.0f;
-    r[45] = r[46] = r[47] = 0.0f;
+    r[44] = r[45] = r[46] = r[47] = 0.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -364,7 +382,8 @@ __global__ void __launch_bounds__(256) k_emit(const int4 *__restrict__ trect, co
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort of (u64 key, u32 value), 8-bit digits, 4096 items per
 // block.  Each pass: per-block digit histograms (digit-major) -> exclusive scan
-// -> stable scatter.  Inside a block a warp owns 512 consecutive items and walks
+// -> stable scatter.  A pass reads the digit (key >> shift) & dmask; the last
+// pass masks off the key bits at and above the sorted width.  Inside a block a warp owns 512 consecutive items and walks
 // them in strips of 32; the rank of an item is (items of its digit in earlier
 // warps) + (in earlier strips of its warp) + (in lower lanes of its strip).
 constexpr int kSortThreads = 256;
@@ -374,7 +393,8 @@ constexpr int kSortWarps = kSortThreads / 32;
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t *__restrict__ keys,
                                                              const uint32_t *__restrict__ n_ptr, int shift,
-                                                             uint32_t *__restrict__ hist, int nblocks)
+                                                             uint32_t dmask, uint32_t *__restrict__ hist,
+                                                             int nblocks)
 {
     __shared__ uint32_t h[kSortWarps][256];
     for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&h[0][0])[i] = 0;
@@ -385,7 +405,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t *__r
 #pragma unroll 4
     for (int k = 0; k < kSortItems; ++k) {
         const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&h[wid][(keys[idx] >> shift) & 255u], 1u);
+        if (idx < n) atomicAdd(&h[wid][(uint32_t)(keys[idx] >> shift) & dmask], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < 256; d += kSortThreads) {
@@ -401,7 +421,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
                                                                 uint64_t *__restrict__ kout,
                                                                 uint32_t *__restrict__ vout,
                                                                 const uint32_t *__restrict__ n_ptr, int shift,
-                                                                const uint32_t *__restrict__ offs, int nblocks)
+                                                                uint32_t dmask, const uint32_t *__restrict__ offs,
+                                                                int nblocks)
 {
     __shared__ uint32_t wcnt[kSortWarps][257];
     __shared__ uint32_t gofs[256];
@@ -422,7 +443,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
         const bool ok = idx < n;
         k[s] = ok ? kin[idx] : 0ull;
         v[s] = ok ? vin[idx] : 0u;
-        dig[s] = ok ? (uint32_t)((k[s] >> shift) & 255u) : 256u;
+        dig[s] = ok ? ((uint32_t)(k[s] >> shift) & dmask) : 256u;
     }
 #pragma unroll
     for (int s = 0; s < kSortItems; ++s) {
@@ -460,7 +481,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
 
 int64_t sort_hist_words(int64_t n_bound) { return 256 * ((n_bound + kSortBlock - 1) / kSortBlock); }
 
-// Sorts (keys, vals) by bits [0, nbits) of the key.  n is on the device (<= n_bound).
+// Sorts (keys, vals) by bits [0, nbits) of the key; higher bits do not take part.
+// n is on the device (<= n_bound).
 // Returns true when the result ended in the *_alt buffers.
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_n,
                 int64_t n_bound, int nbits, uint32_t *hist, uint32_t *hist_scan, uint32_t *scan_tmp, cudaStream_t st)
@@ -473,10 +495,11 @@ bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *va
         const uint32_t *vi = alt ? vals_alt : vals;
         uint64_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
-        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(ki, d_n, shift, hist, nblocks);
+        const uint32_t dmask = nbits - shift >= 8 ? 255u : (1u << (nbits - shift)) - 1u;
+        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(ki, d_n, shift, dmask, hist, nblocks);
         note_launch();
         scan_u32(hist, hist_scan, (int64_t)256 * nblocks, nullptr, scan_tmp, st);
-        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, shift, hist_scan, nblocks);
+        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, shift, dmask, hist_scan, nblocks);
         note_launch();
         alt = !alt;
     }

@@ -15,6 +15,7 @@
 #pragma once
 
 #include "snp_common.cuh"
+#include "snp_df.cuh"
 #include "snp_internal.h"
 #include "snp_mma.cuh"
 
@@ -222,51 +223,39 @@ struct Hit {
     float s, t, half;
 };
 
-// Pairs whose FP32 h^2 lies within this distance of the silhouette are evaluated
-// again in FP64 (the chord length grows like sqrt(h^2), so an FP32 error of ~1e-7
-// in h^2 would move alpha_hat by ~1e-3 at a grazing ray).
-constexpr float kRefineH2 = 1e-4f;
+// Pairs whose FP32 h^2 lies within kBandH2 of the silhouette are evaluated again
+// in float-float arithmetic.  The FP32 h^2 has an absolute error of ~1e-7
+// (2e-6 at most in an emulation over thin 1:50 primitives); the chord grows like
+// sqrt(h^2), so that is a relative error of ~0.5e-7 / h^2 in the chord and in
+// alpha_hat, and up to twice that in their derivatives: ~1e-5 at the edge of the
+// band (2e-4 at the worst).  Inside the band the value is exact to a few ulp.
+// The hit test only needs the sign, which FP32 already settles outside a much
+// narrower band (kSignBandH2, 15x the largest error seen).
+constexpr float kBandH2 = 1e-2f;
+constexpr float kSignBandH2 = 3e-5f;
 
-static __device__ __noinline__ void intersect_fp64(const float *R, const CamK &ck, const PixRay &ry, Hit &h)
+// h^2 A of a pixel ray from the record's quadratic in the pixel offset
+// (X, Y) = (px + .5 - U_c, py + .5 - V_c), in float-float arithmetic: the
+// coefficients and U_c, V_c carry their FP64 values as hi + lo, and
+// X = (px + .5 - U_hi) - U_lo is formed exactly by TwoSum.  The terms are of
+// the order of A and cancel to h^2 A near the silhouette; their float-float
+// error, ~2^-46 A, is what is left.
+static __device__ __noinline__ float h2A_df(const float *R, float pxh, float pyh)
 {
-    double G0[3], G1[3], e[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        G0[a] = (double)R[kRecG + 3 * a + 0] + (double)R[kRecGlo + 3 * a + 0];
-        G1[a] = (double)R[kRecG + 3 * a + 1] + (double)R[kRecGlo + 3 * a + 1];
-        e[a] = (double)R[kRecE + a] + (double)R[kRecElo + a];
-    }
-    const double mz = (double)R[kRecMz] + (double)R[kRecMzlo];
-    const double uc = (double)R[kRecU + 0] + (double)R[kRecU + 1];
-    const double vc = (double)R[kRecU + 2] + (double)R[kRecU + 3];
-    const double dx = ((double)ry.pxh - uc) / (double)ck.fx;
-    const double dy = ((double)ry.pyh - vc) / (double)ck.fy;
-    double f[3], dp[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        f[a] = G0[a] * dx + G1[a] * dy;
-        dp[a] = e[a] + f[a];
-    }
-    const double A = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
-    const double w[3] = {e[1] * f[2] - e[2] * f[1], e[2] * f[0] - e[0] * f[2], e[0] * f[1] - e[1] * f[0]};
-    const double W2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    const double h2 = 1.0 - mz * mz * W2 / A;
-    const double fdp = f[0] * dp[0] + f[1] * dp[1] + f[2] * dp[2];
-    const double sd = -mz * fdp / A;
-    h.dx = (float)dx;
-    h.dy = (float)dy;
-    h.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
-    h.dp = make_float3((float)dp[0], (float)dp[1], (float)dp[2]);
-    h.w = make_float3((float)w[0], (float)w[1], (float)w[2]);
-    h.A = (float)A;
-    h.iA = (float)(1.0 / A);
-    h.W2 = (float)W2;
-    h.h2 = (float)h2;
-    h.fdp = (float)fdp;
-    h.s = (float)sd;
-    h.t = (float)(mz + sd);
-    h.half = (float)sqrt(h2 > 0.0 ? h2 / A : 0.0);
-    if (!(h2 > 0.0)) h.h2 = 0.0f;
+    const float4 q0 = reinterpret_cast<const float4 *>(R + kRecQ)[0];  // c0h c1h c2h c3h
+    const float4 q1 = reinterpret_cast<const float4 *>(R + kRecQ)[1];  // c4h c5h c0l c1l
+    const float4 q2 = reinterpret_cast<const float4 *>(R + kRecQ)[2];  // c2l c3l c4l c5l
+    const float4 u = reinterpret_cast<const float4 *>(R)[3];           // mz mz2 Uhi Ulo
+    const float4 v = reinterpret_cast<const float4 *>(R)[4];           // Vhi Vlo ...
+    f2 X = df_two_sum(pxh, -u.z);
+    X = df_two_sum(X.hi, __fsub_rn(X.lo, u.w));
+    f2 Y = df_two_sum(pyh, -v.x);
+    Y = df_two_sum(Y.hi, __fsub_rn(Y.lo, v.y));
+    const f2 c0{q0.x, q1.z}, c1{q0.y, q1.w}, c2{q0.z, q2.x}, c3{q0.w, q2.y}, c4{q1.x, q2.z}, c5{q1.y, q2.w};
+    const f2 a = df_add(c1, df_add(df_mul(c3, X), df_mul(c4, Y)));
+    const f2 b = df_add(c2, df_mul(c5, Y));
+    const f2 q = df_add(c0, df_add(df_mul(X, a), df_mul(Y, b)));
+    return q.hi + q.lo;
 }
 
 __device__ __forceinline__ bool intersect(const float *R, const CamK &ck, const PixRay &ry, Hit &h)
@@ -288,22 +277,23 @@ __device__ __forceinline__ bool intersect(const float *R, const CamK &ck, const 
     h.w = make_float3(fmaf(e.y, h.f.z, -e.z * h.f.y), fmaf(e.z, h.f.x, -e.x * h.f.z), fmaf(e.x, h.f.y, -e.y * h.f.x));
     h.W2 = fmaf(h.w.x, h.w.x, fmaf(h.w.y, h.w.y, h.w.z * h.w.z));
     h.h2 = 1.0f - g3.y * h.W2 * h.iA;
-    if (fabsf(h.h2) < kRefineH2) {
-        intersect_fp64(R, ck, ry, h);
-        return h.h2 > 0.0f && h.half > 0.0f;
-    }
+    if (fabsf(h.h2) < kBandH2) h.h2 = h2A_df(R, ry.pxh, ry.pyh) * h.iA;
     if (!(h.h2 > 0.0f)) return false;
     h.fdp = fmaf(h.f.x, h.dp.x, fmaf(h.f.y, h.dp.y, h.f.z * h.dp.z));
     h.s = -g3.x * h.fdp * h.iA;
     h.t = g3.x + h.s;
     const float x = h.h2 * h.iA;
+    // a chord below ~1e-18 (only reachable through the float-float band) counts as a miss
+    if (!(x > 1e-36f)) return false;
     h.half = x * rsqrtf(x);
     return true;
 }
 
 // Whether the ray enters the ellipsoid: the sign of h^2 A = |e+f|^2 - mu_z^2 |e x f|^2
-// (no reciprocal, no chord), with the same FP64 re-evaluation band |h^2| < 1e-4
-// as intersect(), so both always agree.
+// (no reciprocal, no chord), re-evaluated in float-float arithmetic within
+// kSignBandH2 of the silhouette.  intersect() takes the float-float value in a
+// wider band; outside either band the FP32 sign is already certain, so the two
+// functions always agree on hit or miss.
 __device__ __forceinline__ bool hit_test(const float *R, const CamK &ck, const PixRay &ry)
 {
     const float4 g0 = reinterpret_cast<const float4 *>(R)[0];  // G00 G01 G02 G10
@@ -320,10 +310,7 @@ __device__ __forceinline__ bool hit_test(const float *R, const CamK &ck, const P
     const float3 w = make_float3(fmaf(e.y, f.z, -e.z * f.y), fmaf(e.z, f.x, -e.x * f.z), fmaf(e.x, f.y, -e.y * f.x));
     const float W2 = fmaf(w.x, w.x, fmaf(w.y, w.y, w.z * w.z));
     const float hA = fmaf(-g3.y, W2, A);
-    if (fabsf(hA) < kRefineH2 * A) {
-        Hit h;
-        return intersect(R, ck, ry, h);
-    }
+    if (fabsf(hA) < kSignBandH2 * A) return h2A_df(R, ry.pxh, ry.pyh) > 0.0f;
     return hA > 0.0f;
 }
 

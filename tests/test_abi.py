@@ -99,3 +99,6 @@ def test_argument_errors_are_reported_before_any_device_work():
     assert f(null, null, 4, 65, null) == bad
     assert f(null, null, (1 << 20) + 1, 32, null) == L.SNP_ERR_CAPACITY
     assert f(null, null, 4, 32, null) == bad
+    # misaligned key (8-byte) or value (4-byte) pointers are refused before the device is touched
+    assert f(4100, 8192, 4, 32, null) == bad
+    assert f(8192, 4098, 4, 32, null) == bad

@@ -6,9 +6,9 @@ colours and every density / colour-MLP weight.  dL/dC is a seeded random image.
 Pixels whose termination step is a near-tie (|T - T_min| < 1% T_min), where FP32
 may decide differently from FP64, get dL = 0.  No silhouette band is needed: the
 kernels evaluate the ray geometry relative to the ray through each primitive's
-centre (FP32 h^2 error ~1e-7) and re-evaluate pairs with |h^2| < 1e-4 in FP64,
-so the 1 / sqrt(h^2) growth of the derivative near a silhouette is followed.
-The _dl helper keeps a sil_eps option for diagnostics.
+centre (FP32 h^2 error ~1e-7) and re-evaluate pairs with |h^2| < 1e-2 in
+float-float arithmetic, so the 1 / sqrt(h^2) growth of the derivative near a
+silhouette is followed.  The _dl helper keeps a sil_eps option for diagnostics.
 
 The colour MLP's hidden layer runs on the tensor cores with split-bf16 operands
 (about 1e-5 relative per product), so a ReLU pre-activation within ~1e-5 of zero

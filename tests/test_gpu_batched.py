@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from paper_2510_08491_gb300 import synth
-from gpu_util import assert_image_close, grad_rel_errors, oracle_images
+from gpu_util import assert_image_close, grad_rel_errors, oracle_images, sample_tiles, tile_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -103,6 +103,68 @@ def test_graph_capture_matches_eager(R):
         for a, b in ((step.g_geom, gg0), (step.g_net, gn0)):
             err = (a - b).abs().max().item()
             assert err <= 1e-5 * (b.abs().max().item() + 1e-12), err
+    assert r.stats().n_keys == K
+
+
+def test_graph_step_matches_oracle_bf16_mlp64_16views(R, oracle_lib):
+    """The batched workload's form checked against the FP64 oracle: 16 views of
+    uneven size, N_sigma = 32, N_c = 64, BF16 weights, 16-pixel tiles and chunk 3
+    (the configuration the benchmark's autotuner settles on), forward + backward
+    captured in one CUDA graph and replayed twice.  dL/dC is set on three sampled
+    tiles per view (zero on termination near-ties and colour-MLP ReLU kinks); the
+    image there and every gradient group must meet the parity bars against the
+    oracle on the primitives those tiles list, and every other primitive's
+    gradient must be exactly zero."""
+    from oracle import grad as G
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import GraphStep, Renderer, pack_scene, unpack_geom_grad, unpack_net_grad
+    from test_gpu_backward import GRAD_TOL, RELU_EPS
+    O = oracle_lib
+    sc = synth.make_scene(6000, seed=41, center_half=3.0, n_sigma=32, color="mlp", n_c=64).to_bf16()
+    cams = _uneven_views(16, 10.0, seed=7)
+    tl = O.tile_keys(sc, cams, 16)
+    picks = sample_tiles(cams, tl, 16, 3, seed=43)
+    sub, prims, per_view = tile_subset(O, sc, tl, picks)
+    pix_off = np.concatenate([[0], np.cumsum([c.n_pixels for c in cams])])
+    rng = np.random.default_rng(44)
+    dL = np.zeros((int(pix_off[-1]), 3), np.float32)
+    ref_rgb, gref = {}, None
+    for v, (pix, owner, off, lst) in sorted(per_view.items()):
+        out = O.render_pixels(sub, cams[v], pix, owner, off, lst)
+        d = rng.normal(size=(len(pix), 3))
+        d[out.flags != 0] = 0.0
+        _, _, ah, amin = G.pair_diagnostics(sub, cams[v], pix, owner, off, lst)
+        pair_pix = np.repeat(np.arange(len(pix)), off[owner + 1] - off[owner])
+        d[np.unique(pair_pix[(ah > 0) & (amin < RELU_EPS)])] = 0.0
+        dL[pix_off[v] + pix] = d
+        ref_rgb[v] = out
+        _, g = G.grads(sub, cams[v], pix, owner, off, lst, d)
+        gref = g if gref is None else {k: gref[k] + g[k] for k in g}
+    r = Renderer(0)
+    ps = pack_scene(sc)
+    cfg = L.make_config(tile_size=16, chunk=3)
+    r.forward(ps, cams, cfg)
+    K = r.stats().n_keys
+    step = GraphStep(r, ps, cams, cfg, max_keys=K + 4096, dL=torch.tensor(dL, device="cuda"))
+    fields = ["centers", "log_scales", "quats", "W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3",
+              "bc3"]
+    others = np.ones(sc.n, bool)
+    others[prims] = False
+    for _ in range(2):
+        step.image.zero_()
+        step.replay()
+        torch.cuda.synchronize()
+        img = step.image.cpu().numpy()
+        for v, (pix, owner, off, lst) in per_view.items():
+            assert_image_close(img[pix_off[v] + pix], ref_rgb[v].rgb, ref_rgb[v].flags)
+        g = unpack_geom_grad(step.g_geom)
+        g.update(unpack_net_grad(ps, step.g_net, sc))
+        for f in fields:
+            assert not np.any(g[f][others]), f
+        errs = grad_rel_errors({f: g[f][prims] for f in fields}, {f: gref[f] for f in fields})
+        print({k: (f"{a:.1e}", f"{b:.1e}") for k, (a, b) in errs.items()})
+        bad = {k: e for k, e in errs.items() if e[0] > GRAD_TOL or e[1] > GRAD_TOL}
+        assert not bad, bad
     assert r.stats().n_keys == K
 
 
