@@ -112,22 +112,39 @@ __device__ __forceinline__ float ld_w(const void *p, int64_t i)
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
-// sin(t)/t: Taylor polynomial below |t| < 0.05 (truncation < 4e-12), MUFU sin over t otherwise.
-__device__ __forceinline__ float sincf_fast(float t)
+// sinc(t) = sin(t) / t and its derivative sinc'(t) = (t cos t - sin t) / t^2.
+// Below |t| < kSincSeries both come from their Maclaurin series: sinc =
+// sum_n (-1)^n t^2n / (2n+1)!, kept to t^10 (remainder < 3e-11 at |t| = 0.5), and
+// sinc' = sum_n (-1)^n 2n t^(2n-1) / (2n+1)!, kept to t^9 (remainder < 1e-12).
+// Above it sin and cos come from the MUFU unit (absolute error ~4e-7).  The
+// numerator of sinc' cancels to ~t^3 / 3 for small t, so the MUFU form would lose
+// up to 1% of sinc' near |t| = 0.05; from 0.5 on the numerator is >= 0.04 and its
+// relative error stays near 1e-5.
+constexpr float kSincSeries = 0.5f;
+
+__device__ __forceinline__ float sinc_series(float t2)
 {
-    float t2 = t * t;
-    float poly = fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
-    float big = __fdividef(__sinf(t), t);
-    return fabsf(t) < 0.05f ? poly : big;
+    float p = fmaf(t2, -1.0f / 39916800.0f, 1.0f / 362880.0f);
+    p = fmaf(t2, p, -1.0f / 5040.0f);
+    p = fmaf(t2, p, 1.0f / 120.0f);
+    p = fmaf(t2, p, -1.0f / 6.0f);
+    return fmaf(t2, p, 1.0f);
 }
 
-// d/dt sinc(t) = (t cos t - sin t) / t^2; series -t/3 + t^3/30 for small t.
-__device__ __forceinline__ float sincf_deriv(float t, float s, float c)
+__device__ __forceinline__ float sinc_deriv_series(float t, float t2)
 {
-    float t2 = t * t;
-    float poly = t * fmaf(t2, 1.0f / 30.0f, -1.0f / 3.0f);
-    float big = __fdividef(fmaf(t, c, -s), t2);
-    return fabsf(t) < 0.05f ? poly : big;
+    float p = fmaf(t2, -1.0f / 3991680.0f, 1.0f / 45360.0f);
+    p = fmaf(t2, p, -1.0f / 840.0f);
+    p = fmaf(t2, p, 1.0f / 30.0f);
+    p = fmaf(t2, p, -1.0f / 3.0f);
+    return t * p;
+}
+
+__device__ __forceinline__ float sincf_fast(float t)
+{
+    const float series = sinc_series(t * t);
+    const float big = __fdividef(__sinf(t), t);
+    return fabsf(t) < kSincSeries ? series : big;
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -200,11 +200,11 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
                     float sp, cp, st, ct;
                     __sincosf(ph, &sp, &cp);
                     __sincosf(th, &st, &ct);
-                    // sinc(th) and its derivative, series below |th| < 0.05, else one reciprocal
+                    // sinc(th) and its derivative: series below |th| < kSincSeries, else one reciprocal
                     const float t2 = th * th, rt = __fdividef(1.0f, th);
-                    const bool small = fabsf(th) < 0.05f;
-                    const float sc = small ? fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f) : st * rt;
-                    const float scp = small ? th * fmaf(t2, 1.0f / 30.0f, -1.0f / 3.0f) : fmaf(th, ct, -st) * rt * rt;
+                    const bool small = fabsf(th) < kSincSeries;
+                    const float sc = small ? sinc_series(t2) : st * rt;
+                    const float scp = small ? sinc_deriv_series(th, t2) : fmaf(th, ct, -st) * rt * rt;
                     S = fmaf(wk * cp, sc, S);
                     const float gphi = -gS * wk * sp * sc;
                     const float gth = gS * wk * cp * scp;

@@ -11,6 +11,11 @@ gradients 1e-3 per group both elementwise, |g - g*| <= 1e-3 (|g*| + rms g*),
 and in norm); the literal form is reported, and must be worse than the stable
 one on the image, since its division by a_k = w0 W1_k . d / m is what the
 stress targets.  Run with -s for the table.
+
+dL/dC is nonzero on the sampled tiles only, so the parameter groups compared
+are the primitives those tiles list (as in the other sampled-tile tests); every
+other primitive's gradient must be exactly zero, and the rms of a group is
+taken over the primitives the sampled pixels can reach.
 """
 import numpy as np
 import pytest
@@ -93,9 +98,11 @@ def test_precision_report(setup):
     refbf = _oracle(S, S["sc_bf"])
     dL_pix = S["rng"].normal(size=(len(S["pix"]), 3))
     dL_pix[~(_mask(S, S["sc"], *ref32) & _mask(S, S["sc_bf"], *refbf))] = 0.0
-    grads_ref = {}
+    grads_ref, active = {}, {}
     for name, sc, (out, tl, lp, gt) in (("f32", S["sc"], ref32), ("bf16", S["sc_bf"], refbf)):
         _, grads_ref[name] = S["G"].grads(sc, S["cam"], S["pix"], gt, tl.tile_off, lp, dL_pix)
+        listed = np.concatenate([lp[tl.tile_off[t]:tl.tile_off[t + 1]] for t in np.unique(gt)])
+        active[name] = np.unique(listed)
     rows = {}
     for wname, sc in (("f32", S["sc"]), ("bf16", S["sc_bf"])):
         out, _, _, _ = ref32 if wname == "f32" else refbf
@@ -103,7 +110,12 @@ def test_precision_report(setup):
         for fname, form in (("stable", L.FORM_STABLE), ("literal", L.FORM_NAIVE)):
             img, g = _gpu(S, sc, form, dL_pix)
             err = np.abs(img - out.rgb).max(axis=1)
-            ge = grad_rel_errors(g, {k: grads_ref[wname][k] for k in fields})
+            act = active[wname]
+            others = np.ones(sc.n, bool)
+            others[act] = False
+            for k in fields:
+                assert not np.any(g[k][others]), (wname, fname, k)
+            ge = grad_rel_errors({k: g[k][act] for k in fields}, {k: grads_ref[wname][k][act] for k in fields})
             row = dict(img_max=float(err[plain].max()), img_mean=float(err.mean()),
                        img_flag_max=float(err[~plain].max()) if (~plain).any() else 0.0,
                        grad_norm_max=max(v[1] for v in ge.values()),
