@@ -34,22 +34,126 @@ METRIC = "Mpixel/s fwd and fwd+bwd at 1080p, 100k–500k primitives vs plain FP3
 WORKLOAD = "fwd100k_1080p_4view"
 # workloads timed as graph replays with an autotuned tile size and chunk
 BATCHED = ("batch500k_16view",)
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128  # FP32 lanes per SM (4 sub-partitions x 32)
+MUFU_LANES_PER_SM = 16   # special-function lanes per SM (4 sub-partitions x 4)
 
 
 # ----------------------------------------------------------------------------- work model
-def fma_per_unit(n_sigma: int, n_c: int):
-    """Algorithmic FP32 FMA counts per candidate / hit / composited pair (forward and backward)."""
-    mlp = 0 if n_c == 0 else (3 + 8) * n_c + n_c * n_c + 3 * n_c
-    fwd = {"cand": 21, "hit": 12 + 12 * n_sigma, "comp": 10 + mlp}
-    bwd = {"cand": 21, "hit": 12 + 12 * n_sigma, "comp": 10 + 3 * mlp + 24 * n_sigma + 80}
+def work_per_unit(n_sigma: int, n_c: int, colour_store: bool):
+    """Arithmetic the raster kernels execute per unit, counted from their code, as
+    (FP32 lane-ops, tensor-core multiply-adds, MUFU ops).  Units are the run's own
+    counters: candidates (pixel, list entry) tested, hits (ray enters the
+    ellipsoid), composited pairs (alpha_hat > 0 before termination).
+
+    FP32 lane-ops: an FMA, FMUL or FADD takes one slot of the FP32 pipe (128 per SM
+    per clock; FLOP = 2 x lane-op, the convention of that peak).  Shuffles,
+    selects, conversions, shared-memory atomics and address arithmetic are not
+    counted.  Tensor multiply-adds: the colour network's hidden layer, one per
+    weight and ray (N_c^2), however many split-precision products it takes.
+      forward  candidate  28: ray offset, G dr, e + f, |e + f|^2, e x f, |e x f|^2, h^2 A
+               hit        29 + 15 N_sigma: reciprocal, h^2, f . dp, s, t, chord (12); offset
+                          direction, u_mid, scales (17); per hidden unit W1 . g, phase,
+                          theta, sinc series, accumulate (15); MUFU 2 + 3 N_sigma
+               composited 10 (weight, optical depth, blend; MUFU 2); colour network
+                          6 N_c + 3 (layers 1 and 3, sigmoid), N_c^2 tensor, MUFU 6
+      backward composited 177 + 40 N_sigma: compositing derivative (15), geometry and its
+                          reverse (38 + 17 + 92), per hidden unit the integral and its
+                          derivatives (40); MUFU 3 + 5 N_sigma; colour network 14 N_c
+                          (layer-1 replay, layer-3 and layer-1 reverse), 3 N_c^2 tensor
+                          (hidden-layer replay, its input gradient, its weight gradient)
+               no store   + the forward's hit and candidate work per composited pair (the
+                          alpha_hat replay) and, with a colour network, its forward
+    The backward tests no candidates: its pair lists come from the forward's
+    composited masks."""
+    ns, nc = n_sigma, n_c
+    mlp = nc > 0
+    fwd = {"cand": (28, 0, 0),
+           "hit": (29 + 15 * ns, 0, 2 + 3 * ns),
+           "comp": (10 + (6 * nc + 3 if mlp else 0), nc * nc, 2 + (6 if mlp else 0))}
+    comp = [177 + 40 * ns + 14 * nc, 3 * nc * nc, 3 + 5 * ns]
+    if not (mlp and colour_store):
+        comp[0] += 28 + 29 + 15 * ns
+        comp[2] += 2 + 3 * ns
+        if mlp:
+            comp[0] += 6 * nc + 3
+            comp[1] += nc * nc
+            comp[2] += 6
+    bwd = {"cand": (0, 0, 0), "hit": (0, 0, 0), "comp": tuple(comp)}
     return fwd, bwd
 
 
-def flops(counts, per_unit):
-    return 2.0 * (counts["cand"] * per_unit["cand"] + counts["hit"] * per_unit["hit"] +
-                  counts["comp"] * per_unit["comp"])
+def kernel_work(counts, per_unit):
+    """(FP32 FLOP, tensor FLOP, MUFU ops) of one launch."""
+    tot = [0.0, 0.0, 0.0]
+    for u, c in counts.items():
+        for i in range(3):
+            tot[i] += float(c) * per_unit[u][i]
+    return 2.0 * tot[0], 2.0 * tot[1], tot[2]
+
+
+def pipe_roofline(work, t_ms, traffic, peaks):
+    """Achieved rate and fraction of peak per pipe for one kernel launch of t_ms."""
+    fp32, tensor, mufu = work
+    t = t_ms * 1e-3
+    out = {"fp32": {"achieved": fp32 / t / 1e12, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s"},
+           "tensor": {"achieved": tensor / t / 1e12, "peak": peaks["tensor_tflops"], "unit": "TFLOP/s"},
+           "mufu": {"achieved": mufu / t / 1e12, "peak": peaks["mufu_tops"], "unit": "Tops/s"}}
+    if traffic:
+        out["hbm"] = {"achieved": traffic / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    for v in out.values():
+        v["frac"] = round(v["achieved"] / v["peak"], 4)
+        v["achieved"] = round(v["achieved"], 3)
+    return out
+
+
+def raster_sources_digest() -> str:
+    """Digest of the raster kernels' sources (the traffic counters stay valid only for them)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2510_08491_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith(("snp_raster", "snp_common", "snp_df", "snp_mma")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def raster_traffic(workload: str) -> dict:
+    """DRAM bytes per launch of each raster kernel from the committed ncu summary
+    (profiles/traffic.json), when it was taken on this workload from the current
+    kernel sources; otherwise nothing (the counters no longer describe the kernel)."""
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return {}
+    if tr.get("workload") != workload or tr.get("sources") != raster_sources_digest():
+        return {}
+    return {k: tr[k]["bytes_per_launch"] for k in ("k_raster_fwd", "k_raster_bwd") if k in tr}
+
+
+def device_peaks(dev: int):
+    """Peaks of the roofline: FP32 and MUFU from the device's SM count and the
+    measured maximum SM clock, bf16 tensor and HBM copy bandwidth as measured
+    (MEASURED_PEAKS.json; the sustained bf16 figure, since the raster kernels run
+    inside a long step).  Falls back to the recipe's figures without that file."""
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    measured = "sm_max_mhz" in peaks
+    return {"sms": sms, "sm_mhz": mhz,
+            "fp32_tflops": round(sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, 2),
+            "mufu_tops": round(sms * MUFU_LANES_PER_SM * mhz * 1e6 / 1e12, 3),
+            "tensor_tflops": float(peaks.get("bf16_tflops_sustained", 1700.0)),
+            "hbm_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+            "note": (f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {mhz:.0f} MHz; MUFU: {sms} SMs x "
+                     f"{MUFU_LANES_PER_SM} lanes x {mhz:.0f} MHz; " +
+                     ("sm_max_mhz, sustained bf16 TFLOP/s and HBM GB/s of measured peaks" if measured
+                      else "2070 MHz, 1700 TFLOP/s bf16 sustained, 6800 GB/s (fallback: no measured peaks file)"))}
 
 
 # ----------------------------------------------------------------------------- multi-rank
@@ -128,10 +232,16 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle (CPU) leg
-def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True):
+def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True, keep: bool = False):
     """Time the FP64 oracle on a bounded sample of the workload: the key stage of every
     view (pro-rated to the sample), then forward (+ gradient) of `tiles_per_view`
-    seeded 16 x 16 tiles per view.  Returns (pixels, seconds, cores)."""
+    seeded 16 x 16 tiles per view.  Returns (pixels, seconds, cores[, kept]).
+
+    keep: also return the sample (per view: pixels, oracle colours, termination
+    near-tie flags and the dL/dC used) and the oracle's gradient summed over the
+    views, for the accuracy report.  dL/dC is then zero on pixels at a termination
+    near-tie or with a composited pair at a colour-network ReLU kink, where FP32
+    and FP64 may take different branches; that check runs outside the timing."""
     import numpy as np
 
     from oracle import grad as G
@@ -146,6 +256,7 @@ def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True
     npx = 0
     t_pix = 0.0
     total_px = sum(c.n_pixels for c in cams)
+    kept = {"views": [], "grads": None, "prims": []}
     for v, cam in enumerate(cams):
         tx_n, ty_n = O.tiles_xy(cam, 16)
         tiles = rng.choice(tx_n * ty_n, size=tiles_per_view, replace=False)
@@ -157,15 +268,82 @@ def oracle_sample(wl, tiles_per_view: int, seed: int = 0, with_grad: bool = True
         pix = np.concatenate(pix).astype(np.int32)
         t1 = time.perf_counter()
         out = O.render_view_tiled(sc, cams, v, tl, 16, pix, cs=cs)
+        t_pix += time.perf_counter() - t1
         if with_grad:
             gt = tl.view_tile_off[v] + O.pixel_tile(cam, 16, pix)
             lp = (tl.vals.astype(np.int64) % sc.n).astype(np.int32)
             dL = rng.normal(size=(len(pix), 3))
-            G.grads(sc, cam, pix, gt, tl.tile_off, lp, dL)
-        t_pix += time.perf_counter() - t1
+            if keep:
+                dL[out.flags != 0] = 0.0
+                if sc.color == "mlp":
+                    _, _, ah, amin = G.pair_diagnostics(sc, cam, pix, gt, tl.tile_off, lp)
+                    lens = tl.tile_off[gt + 1] - tl.tile_off[gt]
+                    owner = np.repeat(np.arange(len(pix)), lens)
+                    dL[np.unique(owner[(ah > 0) & (amin < 1e-4)])] = 0.0
+                ut = np.unique(gt)
+                kept["prims"].append(np.concatenate([lp[tl.tile_off[t]:tl.tile_off[t + 1]] for t in ut]))
+            t1 = time.perf_counter()
+            _, g = G.grads(sc, cam, pix, gt, tl.tile_off, lp, dL)
+            t_pix += time.perf_counter() - t1
+            if keep:
+                kept["grads"] = g if kept["grads"] is None else {k: kept["grads"][k] + g[k] for k in g}
+                kept["views"].append((pix, out.rgb, out.flags, dL))
         npx += len(pix)
     secs = t_keys * (npx / total_px) + t_pix
+    if keep:
+        kept["prims"] = np.unique(np.concatenate(kept["prims"])) if kept["prims"] else np.zeros(0, np.int64)
+        return npx, secs, os.cpu_count() or 1, kept
     return npx, secs, os.cpu_count() or 1
+
+
+def accuracy_vs_oracle(r, ps, sc, cams, cfg, kept):
+    """Image and gradient error of the CUDA path against the FP64 oracle on the
+    oracle leg's sampled tiles: max and mean |C - C*| per channel (pixels at a
+    termination near-tie reported apart), and per parameter group the elementwise
+    max |g - g*| / (|g*| + rms g*) and ||g - g*|| / ||g*|| over the primitives the
+    sampled tiles list (dL/dC set on the sampled pixels only)."""
+    import numpy as np
+    import torch
+
+    from paper_2510_08491_gb300.render import unpack_geom_grad, unpack_net_grad
+    P = sum(c.n_pixels for c in cams)
+    img = r.forward(ps, cams, cfg).cpu().numpy().astype(np.float64)
+    off = np.concatenate([[0], np.cumsum([c.n_pixels for c in cams])])
+    errs, flags = [], []
+    dL = np.zeros((P, 3), np.float32)
+    for v, (pix, rgb, fl, d) in enumerate(kept["views"]):
+        errs.append(np.abs(img[off[v] + pix] - rgb).max(axis=1))
+        flags.append(fl)
+        dL[off[v] + pix] = d
+    err, fl = np.concatenate(errs), np.concatenate(flags)
+    plain = fl == 0
+    g_geom = torch.zeros_like(ps.geom)
+    g_net = torch.zeros(ps.net.shape, dtype=torch.float32, device=ps.net.device)
+    r.backward(ps, torch.tensor(dL, device=ps.geom.device), g_geom, g_net)
+    torch.cuda.synchronize()
+    g = unpack_geom_grad(g_geom)
+    g.update(unpack_net_grad(ps, g_net, sc))
+    act = kept["prims"]
+    groups = {}
+    for k, ref in kept["grads"].items():
+        if k not in g:
+            continue
+        a, b = np.asarray(g[k], np.float64)[act], np.asarray(ref, np.float64)[act]
+        rms = float(np.sqrt((b ** 2).mean()))
+        nb = float(np.linalg.norm(b))
+        if rms == 0.0 or nb == 0.0:
+            continue
+        groups[k] = (float((np.abs(a - b) / (np.abs(b) + rms)).max()), float(np.linalg.norm(a - b) / nb))
+    worst_e = max(groups, key=lambda k: groups[k][0])
+    worst_n = max(groups, key=lambda k: groups[k][1])
+    return {"image_max_abs": float(err[plain].max()), "image_mean_abs": float(err.mean()),
+            "image_flagged_max_abs": float(err[~plain].max()) if (~plain).any() else 0.0,
+            "pixels": int(len(err)), "flagged_pixels": int((~plain).sum()),
+            "grad_elem_max": round(groups[worst_e][0], 7), "grad_elem_group": worst_e,
+            "grad_norm_max": round(groups[worst_n][1], 7), "grad_norm_group": worst_n,
+            "primitives": int(len(act)),
+            "bars": "image 1e-4 abs (flagged 2e-4); gradients 1e-3 elementwise and in norm",
+            "oracle": "FP64 CPU oracle on the cpu_baseline leg's sampled tiles"}
 
 
 # ----------------------------------------------------------------------------- GPU leg
@@ -488,30 +666,20 @@ def run_ours(args, rank, world):
     h2d_bytes = h_geom.numel() * h_geom.element_size() + h_net.numel() * h_net.element_size() + h_in.numel() * 4
     d2h_bytes = P * 3 * 4 + g_geom.numel() * 4 + g_net.numel() * 4 + (4 if loss is not None else 0)
 
-    # roofline of the dominant kernel (FP32 ALU bound)
-    fwd_u, bwd_u = fma_per_unit(sc.n_sigma, sc.n_c if sc.color == "mlp" else 0)
+    # roofline of the raster kernels (per pipe; the dominant kernel's binding pipe is the headline)
+    peaks = device_peaks(dev)
+    nc_eff = sc.n_c if sc.color == "mlp" else 0
+    colour_store = sc.color == "mlp" and not args.replay_color
+    fwd_u, bwd_u = work_per_unit(sc.n_sigma, nc_eff, colour_store)
     t_fwd = st["raster_fwd"][0] / max(st["raster_fwd"][1], 1)
     t_bwd = st["raster_bwd"][0] / max(st["raster_bwd"][1], 1)
-    if t_bwd >= t_fwd:
-        kern, t_k, fl = "k_raster_bwd", t_bwd, flops(counts, bwd_u)
-    else:
-        kern, t_k, fl = "k_raster_fwd", t_fwd, flops(counts, fwd_u)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    traffic = raster_traffic(args.workload)
+    kernels = {"k_raster_fwd": pipe_roofline(kernel_work(counts, fwd_u), t_fwd, traffic.get("k_raster_fwd"), peaks),
+               "k_raster_bwd": pipe_roofline(kernel_work(counts, bwd_u), t_bwd, traffic.get("k_raster_bwd"), peaks)}
+    kern = "k_raster_bwd" if t_bwd >= t_fwd else "k_raster_fwd"
+    pipes = kernels[kern]
+    bind = max(pipes, key=lambda k: pipes[k]["frac"])
     clocks = clk.summary()
-    sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
-    achieved = fl / (t_k * 1e-3) / 1e12
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if tr.get("workload") == args.workload:
-            traffic = tr.get(kern, {}).get("bytes_per_launch")
-    except Exception:
-        pass
 
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -529,12 +697,12 @@ def run_ours(args, rank, world):
                                                                               / 1e9)},
         "fwd_mpix_s": round(world * P / (ms_fwd * 1e-3) / 1e6, 3),
         "fwd_ms": round(ms_fwd, 4),
-        "roofline": {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3),
-                     "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                     "traffic": traffic,
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x " +
-                                  ("sm_max_mhz of measured peaks" if "sm_max_mhz" in peaks
-                                   else "2070 MHz (fallback: no measured peaks file)")},
+        "roofline": {"bound": {"fp32": "alu", "mufu": "alu", "tensor": "tensor", "hbm": "hbm"}[bind],
+                     "pipe": bind, "kernel": kern, "achieved": pipes[bind]["achieved"], "peak": pipes[bind]["peak"],
+                     "unit": pipes[bind]["unit"], "frac": pipes[bind]["frac"],
+                     "traffic": traffic.get(kern), "kernels": kernels, "peak_note": peaks["note"],
+                     "work_note": "executed arithmetic per candidate / hit / composited pair counted from the "
+                                  "kernels (bench.work_per_unit) x the run's counters; fraction = max over pipes"},
         "e2e": {"value": round(world * P / (ms_e2e * 1e-3) / 1e6, 3), "unit": "Mpixel/s",
                 "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes),
                 "ms_per_step": round(ms_e2e, 4),
@@ -550,16 +718,76 @@ def run_ours(args, rank, world):
         res["loss"] = float(h_loss.item())
     if train_state is not None:
         res["config"]["step"] += "+regulariser+statistic+adam"
-        res["train"] = train_state.measure(g_geom, g_net, float(peaks.get("hbm_gbs", 6800.0)),
-                                           "HBM copy bandwidth of measured peaks" if "hbm_gbs" in peaks
-                                           else "HBM 6800 GB/s (fallback: no measured peaks file)")
+        res["train"] = train_state.measure(g_geom, g_net, peaks["hbm_gbs"],
+                                           "HBM copy bandwidth: " + peaks["note"].split("; ")[-1])
     if rank == 0 and not args.no_cpu_baseline and (args.workload == WORKLOAD or args.cpu_baseline):
-        npx, secs, cores = oracle_sample(wl, args.cpu_tiles)
+        npx, secs, cores, kept = oracle_sample(wl, args.cpu_tiles, keep=True)
         res["cpu_baseline"] = {"value": round(npx / secs / 1e6, 6), "unit": "Mpixel/s", "cores": cores,
                                "kind": "oracle",
                                "sample": f"forward+gradient of {args.cpu_tiles} seeded 16x16 tiles per view "
                                          f"({npx} px) plus the key stage pro-rated to the sample; {secs:.1f} s"}
+        res["accuracy"] = accuracy_vs_oracle(r, ps, sc, cams, cfg, kept)
+    if args.workload == WORKLOAD and not args.no_forms and not args.train:
+        # the metric's comparison: the BF16-weight, batched, differentiable form beside
+        # the plain FP32 forward (and FP32 forward + backward) of this run
+        res["forms"] = {"fp32_forward": {"workload": args.workload, "mpix_s": res["fwd_mpix_s"],
+                                         "ms": res["fwd_ms"]},
+                        "fp32_fwd_bwd": {"workload": args.workload, "mpix_s": res["value"], "ms": res["ms_per_step"]},
+                        "bf16_batched_graph": batched_form(dev, max(min(args.steps, 5), 3), args.warmup)}
     return res
+
+
+def batched_form(dev: int, steps: int, warmup: int):
+    """The BF16-weight, batched, differentiable form on its own workload
+    (batch500k_16view: 500k primitives, N_sigma = 32, N_c = 64, BF16 weights, 16
+    views of uneven size): forward + backward of all views, one persistent launch
+    each, captured in one CUDA graph with the autotuned tile size and chunk, timed
+    as graph replays on the device (inputs resident); and its forward alone."""
+    import torch
+
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300 import synth
+    from paper_2510_08491_gb300.render import GraphStep, Renderer, pack_scene
+    wl = synth.workload("batch500k_16view")
+    cams = wl.cameras
+    P = sum(c.n_pixels for c in cams)
+    r = Renderer(dev)
+    ps = pack_scene(wl.scene)
+    cfg = r.autotune(ps, cams, L.make_config(t_min=wl.t_min), backward=True)
+    r.forward(ps, cams, cfg)
+    torch.cuda.synchronize()
+    K = r.stats().n_keys
+    dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 1e-3
+    step = GraphStep(r, ps, cams, cfg, max_keys=int(K * 1.05) + 4096, dL=dL)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    ms = timed(step.replay, steps)
+    img = torch.empty((P, 3), device="cuda")
+    ms_fwd = timed(lambda: r.forward(ps, cams, cfg, out=img), steps)
+    out = {"workload": "batch500k_16view", "weights": "bf16", "views": len(cams), "pixels": P,
+           "tile": int(cfg.tile_size), "chunk": int(cfg.chunk), "graph": True, "autotuned": True,
+           "fwd_bwd_mpix_s": round(P / (ms * 1e-3) / 1e6, 3), "fwd_bwd_ms": round(ms, 3),
+           "fwd_mpix_s": round(P / (ms_fwd * 1e-3) / 1e6, 3), "fwd_ms": round(ms_fwd, 3), "keys": int(K),
+           "accuracy": "held to the same bars by tests/test_gpu_batched.py::"
+                       "test_graph_step_matches_oracle_bf16_mlp64_16views (the graph-captured step, "
+                       "16 uneven views at a quarter of these sizes) and tests/test_gpu_fullsize.py "
+                       "(this workload at full size: keys bit-exact, sampled tiles)"}
+    del step, r, ps, img, dL
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -594,6 +822,8 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=16)
     ap.add_argument("--ref-tiles", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the BF16 batched graph form (batch500k_16view) beside the default workload")
     ap.add_argument("--cpu-baseline", action="store_true",
                     help="also time the oracle sample on a workload other than the default one")
     ap.add_argument("--graph", action="store_true", help="time replays of a captured CUDA graph of the step")

@@ -452,7 +452,11 @@ static snp_status ensure_frame(snp_context *ctx, int64_t n, int n_views, int64_t
 static int64_t col_pairs_wanted(const snp_context *ctx, int64_t K, int ts)
 {
     int64_t want = ctx->last_comp > 0 ? ctx->last_comp + ctx->last_comp / 4 : K * 16;
-    want += (int64_t)4 * 152 * kColBlock;
+    // up to four forward CTAs per SM each hold one partly used block
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms <= 0)
+        sms = 1024;
+    want += (int64_t)4 * sms * kColBlock;
     want = std::max<int64_t>(want, (int64_t)1 << 16);
     want = std::min<int64_t>(want, std::max<int64_t>(K, 1) * ts * ts);
     return std::min<int64_t>(want, (int64_t)0xfffffffe);

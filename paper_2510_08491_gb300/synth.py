@@ -124,15 +124,23 @@ class Scene:
 
 
 def bf16_round(x: np.ndarray) -> np.ndarray:
-    """Round float32 values to the nearest bfloat16 (ties to even); return float32."""
+    """Round float32 values to the nearest bfloat16 (ties to even); return float32.
+
+    On the bit pattern u: add 0x7FFF plus the lowest kept bit, clear the low 16
+    bits.  In uint32 this wraps only for negative NaN patterns (>= 0xFFFF8000);
+    finite values and infinities round exactly, overflow going to infinity."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     out = np.empty_like(x)
     src, dst = x.reshape(-1).view(np.uint32), out.reshape(-1).view(np.uint32)
     step = 1 << 24  # bounded temporaries for the 500k-primitive scenes
     for a in range(0, src.size, step):
-        u = src[a:a + step].astype(np.uint64)
-        r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-        dst[a:a + step] = (r & 0xFFFFFFFF).astype(np.uint32)
+        u = src[a:a + step]
+        r = dst[a:a + step]
+        np.right_shift(u, 16, out=r)
+        r &= np.uint32(1)
+        r += np.uint32(0x7FFF)
+        r += u
+        r &= np.uint32(0xFFFF0000)
     return out
 
 
@@ -259,13 +267,19 @@ def make_scene(n: int, seed: int = 0, *, center_half: float = 1.0, n_sigma: int 
                centers=centers, log_scales=log_scales, quats=quats, W1=W1, b1=b1, w2=w2,
                b2=b2, rgb=rgb)
     if color == "mlp":
+        # the colour-network weights (up to 2.6 G values at 500k primitives) are drawn
+        # directly in float32, without float64 temporaries
+        def normal32(std, size):
+            out = g.standard_normal(size=size, dtype=f32)
+            out *= f32(std)
+            return out
         fin1 = 3 + FEAT_DIM
         sc.feat = g.normal(0.0, 1.0, size=(n, FEAT_DIM)).astype(f32)
-        sc.Wc1 = g.normal(0.0, 1.0 / math.sqrt(fin1), size=(n, n_c, fin1)).astype(f32)
+        sc.Wc1 = normal32(1.0 / math.sqrt(fin1), (n, n_c, fin1))
         sc.bc1 = np.zeros((n, n_c), dtype=f32)
-        sc.Wc2 = g.normal(0.0, 1.0 / math.sqrt(n_c), size=(n, n_c, n_c)).astype(f32)
+        sc.Wc2 = normal32(1.0 / math.sqrt(n_c), (n, n_c, n_c))
         sc.bc2 = np.zeros((n, n_c), dtype=f32)
-        sc.Wc3 = g.normal(0.0, 1.0 / math.sqrt(n_c), size=(n, 3, n_c)).astype(f32)
+        sc.Wc3 = normal32(1.0 / math.sqrt(n_c), (n, 3, n_c))
         sc.bc3 = np.zeros((n, 3), dtype=f32)
     if color == "sh":
         sh = g.normal(0.0, 0.2, size=(n, 16, 3))

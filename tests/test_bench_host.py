@@ -1,7 +1,7 @@
-"""Host logic of bench.py (CPU): the algorithmic work model behind
-roofline.achieved, the parsing of nvidia-smi clock samples, and the reference
-arm's JSON line (the FP64 oracle on a bounded sample of the 64-primitive
-workload)."""
+"""Host logic of bench.py (CPU): the executed-work model behind
+roofline.achieved (per pipe), the validity rule of the committed DRAM traffic,
+the parsing of nvidia-smi clock samples, and the reference arm's JSON line (the
+FP64 oracle on a bounded sample of the 64-primitive workload)."""
 import argparse
 
 import pytest
@@ -9,15 +9,46 @@ import pytest
 
 def test_work_model_counts():
     import bench
-    fwd, bwd = bench.fma_per_unit(16, 32)
-    mlp = (3 + 8) * 32 + 32 * 32 + 3 * 32          # first layer, hidden layer, output layer
-    assert mlp == 1472
-    assert fwd == {"cand": 21, "hit": 12 + 12 * 16, "comp": 10 + mlp}
-    assert bwd["comp"] == 10 + 3 * mlp + 24 * 16 + 80 and bwd["hit"] == fwd["hit"]
-    f0, _ = bench.fma_per_unit(8, 0)
-    assert f0["comp"] == 10                          # no colour network
+    ns, nc = 16, 32
+    fwd, bwd = bench.work_per_unit(ns, nc, colour_store=True)
+    # (FP32 lane-ops, tensor multiply-adds, MUFU ops) per unit
+    assert fwd["cand"] == (28, 0, 0)
+    assert fwd["hit"] == (29 + 15 * ns, 0, 2 + 3 * ns)
+    assert fwd["comp"] == (10 + 6 * nc + 3, nc * nc, 8)      # the hidden layer is tensor-core work
+    # the backward tests no candidates and, with the colour store, replays no alpha_hat
+    assert bwd["cand"] == (0, 0, 0) and bwd["hit"] == (0, 0, 0)
+    assert bwd["comp"] == (177 + 40 * ns + 14 * nc, 3 * nc * nc, 3 + 5 * ns)
+    _, bwd_replay = bench.work_per_unit(ns, nc, colour_store=False)
+    assert bwd_replay["comp"][0] == bwd["comp"][0] + 28 + 29 + 15 * ns + 6 * nc + 3
+    assert bwd_replay["comp"][1] == 4 * nc * nc
+    f0, b0 = bench.work_per_unit(8, 0, colour_store=True)   # no colour network: no store, alpha_hat replayed
+    assert f0["comp"] == (10, 0, 2) and b0["comp"][1] == 0
+    assert b0["comp"][0] == 177 + 40 * 8 + 28 + 29 + 15 * 8
     counts = {"cand": 1000, "hit": 400, "comp": 100}
-    assert bench.flops(counts, fwd) == 2.0 * (1000 * 21 + 400 * 204 + 100 * 1482)
+    fp32, tensor, mufu = bench.kernel_work(counts, fwd)
+    assert fp32 == 2.0 * (1000 * 28 + 400 * (29 + 15 * ns) + 100 * (10 + 6 * nc + 3))
+    assert tensor == 2.0 * 100 * nc * nc and mufu == 400 * (2 + 3 * ns) + 100 * 8
+    peaks = {"fp32_tflops": 80.0, "tensor_tflops": 1700.0, "mufu_tops": 5.0, "hbm_gbs": 6800.0}
+    roof = bench.pipe_roofline((80e9, 17e9, 5e9), 10.0, 6.8e9, peaks)   # 10 ms
+    assert roof["fp32"]["frac"] == 0.1 and roof["tensor"]["frac"] == 0.001
+    assert roof["mufu"]["frac"] == 0.1 and roof["hbm"]["frac"] == 0.1
+
+
+def test_traffic_is_dropped_when_the_kernels_change(tmp_path, monkeypatch):
+    import json
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({"workload": "w", "sources": bench.raster_sources_digest(),
+                                                    "k_raster_bwd": {"bytes_per_launch": 7}}))
+    real_root = bench.ROOT
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "raster_sources_digest", lambda: json.loads((prof / "traffic.json").read_text())["sources"])
+    assert bench.raster_traffic("w") == {"k_raster_bwd": 7}
+    assert bench.raster_traffic("other") == {}
+    monkeypatch.setattr(bench, "raster_sources_digest", lambda: "changed")
+    assert bench.raster_traffic("w") == {}
+    monkeypatch.setattr(bench, "ROOT", real_root)
 
 
 def test_clock_summary_median_and_reasons():
