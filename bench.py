@@ -756,7 +756,8 @@ def batched_form(dev: int, steps: int, warmup: int):
     cfg = r.autotune(ps, cams, L.make_config(t_min=wl.t_min), backward=True)
     r.forward(ps, cams, cfg)
     torch.cuda.synchronize()
-    K = r.stats().n_keys
+    stats = r.stats()
+    K = stats.n_keys
     dL = torch.randn((P, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 1e-3
     step = GraphStep(r, ps, cams, cfg, max_keys=int(K * 1.05) + 4096, dL=dL)
     stream = torch.cuda.current_stream()
@@ -780,6 +781,8 @@ def batched_form(dev: int, steps: int, warmup: int):
            "tile": int(cfg.tile_size), "chunk": int(cfg.chunk), "graph": True, "autotuned": True,
            "fwd_bwd_mpix_s": round(P / (ms * 1e-3) / 1e6, 3), "fwd_bwd_ms": round(ms, 3),
            "fwd_mpix_s": round(P / (ms_fwd * 1e-3) / 1e6, 3), "fwd_ms": round(ms_fwd, 3), "keys": int(K),
+           "work": {"candidates": int(stats.n_candidates), "hits": int(stats.n_hits),
+                    "composited": int(stats.n_composited)},
            "accuracy": "held to the same bars by tests/test_gpu_batched.py::"
                        "test_graph_step_matches_oracle_bf16_mlp64_16views (the graph-captured step, "
                        "16 uneven views at a quarter of these sizes) and tests/test_gpu_fullsize.py "

@@ -67,12 +67,14 @@ __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, 
 // and scale W1 / b1 by w0 in place (for a time-conditioned scene first setting
 // dL/dW_t,k = xi dL/d(staged phase offset k), since the staged offset is
 // w0 b1_k + xi W_t,k), then reduce every block into the caller's arrays with bulk
-// asynchronous adds issued by thread 0.  All threads call it.  The reads of the
-// bulk adds complete in the background: the kernel waits for them (thread 0) and
-// clears the accumulators only in the next chunk, before its first accumulation.
+// asynchronous adds issued by thread 0.  Entries that no pixel composited (na[e]
+// = 0: no work item touched their accumulators, which are still zero) are
+// skipped.  All threads call it.  The reads of the bulk adds complete in the
+// background: the kernel waits for them (thread 0) and clears the accumulators
+// only in the next chunk, before its first accumulation.
 template <int NC, int NT>
 __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int vg, const uint32_t *s_gid, int cnt,
-                                            int64_t vn, int tid, int nt, float xi)
+                                            const int *na, int64_t vn, int tid, int nt, float xi)
 {
     const int ns = a.n_sigma;
     if constexpr (NC > 0) {
@@ -83,6 +85,7 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
         constexpr int NG8 = NC / 8, PB = 16 * NC / NT, BR = (16 / PB < 1 ? 1 : (16 / PB > NC / 16 ? NC / 16 : 16 / PB));
         static_assert(PB * NT == 16 * NC, "a row block must split evenly over the threads");
         for (int e = 0; e < cnt; ++e) {
+            if (na[e] == 0) continue;  // uniform over the block
             float *W = acc + e * vg + a.off_Wc2;
             for (int b0 = 0; b0 < NC / 16; b0 += BR) {
                 float v[BR][PB];
@@ -112,11 +115,12 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
         for (int q = tid; q < cnt * (4 * ns); q += nt) {
             const int e = q / (4 * ns), r = q - e * (4 * ns);
             float *A = acc + e * vg;
-            if (r >= 3 * ns) A[a.off_wt + r - 3 * ns] = xi * A[a.off_b1 + r - 3 * ns];
+            if (r >= 3 * ns && na[e] != 0) A[a.off_wt + r - 3 * ns] = xi * A[a.off_b1 + r - 3 * ns];
         }
     }
     for (int q = tid; q < cnt * (4 * ns); q += nt) {
         const int e = q / (4 * ns), r = q - e * (4 * ns);
+        if (na[e] == 0) continue;
         float *A = acc + e * vg;
         if (r < 3 * ns) A[a.off_W1 + r] *= a.omega0;
         else A[a.off_b1 + (r - 3 * ns)] *= a.omega0;
@@ -125,6 +129,7 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         for (int e = 0; e < cnt; ++e) {
+            if (na[e] == 0) continue;
             const int64_t gid = s_gid[e], prim = gid - vn;
             const float *A = acc + e * vg;
             if (a.g_net) bulk_reduce_add(a.g_net + prim * a.stride, A, (uint32_t)a.stride * 4u);
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 }
             }
             __syncthreads();
-            flush_chunk<NC, NT>(a, acc, vg, cg, cnt, vn, tid, NT, V.time);
+            flush_chunk<NC, NT>(a, acc, vg, cg, cnt, s_na, vn, tid, NT, V.time);
             clear_n = cnt * vg / 4;
         }
         __syncthreads();
