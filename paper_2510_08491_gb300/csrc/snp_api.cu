@@ -351,6 +351,7 @@ static void fill_args(RasterArgs &a, const snp_context *ctx, const snp_scene_des
     a.npack = (float *)ctx->npack.p;
     a.cmask = (uint32_t *)ctx->cmask.p;
     a.npack_stride = raster_npack_stride(d->color_mode, d->n_c, d->n_sigma);
+    a.wait_status = (int *)((char *)ctx->small.p + kSmallFlags) + 1;
 }
 
 extern "C" {
@@ -630,7 +631,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         key_bound = ctx->key_cap;
         ctx->K = -1;  // known on the device only
     }
-    CK(cudaMemsetAsync(d_flags, 0, 4, st));
+    CK(cudaMemsetAsync(d_flags, 0, 8, st));  // key overflow, device-wait timeout
     STAGE_BEGIN(SNP_STAGE_EMIT);
     launch_emit((const int4 *)ctx->trect.p, (const uint32_t *)ctx->counts.p, (const uint32_t *)ctx->offsets.p,
                 (const float *)ctx->rec.p, n, (const View *)ctx->views.p, n_cams, (uint64_t *)ctx->keys.p,
@@ -922,6 +923,7 @@ snp_status snp_get_stats(snp_context *ctx, int64_t token, snp_stats *out, void *
     out->n_hits = (int64_t)h[1];
     out->n_composited = (int64_t)h[2];
     if (ctx->h_small[4] != 0) return fail(ctx, SNP_ERR_CAPACITY, "tile keys exceeded the reserved capacity");
+    if (ctx->h_small[5] != 0) return fail(ctx, SNP_ERR_TIMEOUT, "a bounded device wait of the backward gave up");
     return SNP_OK;
 }
 

@@ -78,6 +78,8 @@ struct RasterArgs {
     uint32_t *key_off;        // [K] first colstore index of each key's pairs (kNoStore: not stored)
     unsigned long long *col_count;  // bump allocator of the forward (zeroed before it)
     uint32_t col_cap;         // capacity in pairs
+    // set to 1 by a kernel whose bounded device wait gave up (zeroed with each forward)
+    int *wait_status;
 };
 
 constexpr uint32_t kNoStore = 0xffffffffu;

@@ -18,6 +18,7 @@
 #include "snp_df.cuh"
 #include "snp_internal.h"
 #include "snp_mma.cuh"
+#include "snp_tmem.cuh"
 
 namespace snp {
 
@@ -547,7 +548,7 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 }
 
 // Backward of the colour MLP for the composited pairs at positions r0 .. r0+15 of
-// an entry's list.  Per pair: dL/dc = w dL (w: compositing weight at w_e[slot],
+// an entry's list (n pairs in all).  Per pair: dL/dc = w dL (w: compositing weight at w_e[slot],
 // dL: dl[c * npix + slot]) and dL/da3 = dL/dc c (1 - c) (c at col_e[slot * qs +
 // c * plane]).  Accumulates, with shared-memory atomics, in the network record layout:
 //   WC1 [NC][11]  dL/dWc1 for the direction columns 0..2;   H0 [NC] dL/dh0;
@@ -557,13 +558,18 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 //   W3 [3][NC]    dL/dWc3;  BC2 [NC] dL/dbc2;  AB3 [3] dL/dbc3.
 // a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays dL/da2 z1^T run on
 // the tensor cores; the last takes movmatrix transposes of the pass's register
-// fragments, with the 16 rays as the reduction dimension.
-template <int NC, bool BF16>
+// fragments, with the 16 rays as the reduction dimension.  With TM (N_c = 64)
+// dL/dWc2 is not added to AW2: tcgen05.mma accumulates it in the entry's 64 x 64
+// TMEM accumulator (tp.d_tmem) over all of the entry's passes, and the flush reads
+// it from there.  ncommit counts this warp's committed MMA groups.
+template <int NC, bool BF16, bool TM>
 __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float4 *s_ray, const uint16_t *list,
                                                     int r0, int n, const float *w_e, const float *dl, int npix,
                                                     const float *col_e, int qs, int plane, float *WC1, float *H0,
-                                                    float *AW2, float *W3, float *BC2, float *AB3)
+                                                    float *AW2, float *W3, float *BC2, float *AB3,
+                                                    const TmemPass &tp, int &ncommit)
 {
+    static_assert(!TM || NC == 64, "the TMEM accumulation is built for N_c = 64");
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
     const float *B2 = Cb + cb_B2(NC);
@@ -671,23 +677,88 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
         tzl[nk][0] = movm_trans(zl[kt][o]);
         tzl[nk][1] = movm_trans(zl[kt][o + 1]);
     }
-#pragma unroll
-    for (int mn = 0; mn < NC / 16; ++mn) {
-        const uint32_t th[4] = {movm_trans(gh[mn][0]), movm_trans(gh[mn][2]), movm_trans(gh[mn][1]),
-                                movm_trans(gh[mn][3])};
-        const uint32_t tl[4] = {movm_trans(gl[mn][0]), movm_trans(gl[mn][2]), movm_trans(gl[mn][1]),
-                                movm_trans(gl[mn][3])};
+    if constexpr (TM) {
+        // The 5th-generation tensor core accumulates the entry's dL/dWc2 in TMEM
+        // across all of its passes: this warp writes its pass's operands (A = dL/da2^T,
+        // 64 output units x 16 rays; B^T = z1^T, 64 input units x 16 rays; bf16 hi and
+        // lo each) to its shared-memory tiles in the K-major core-matrix layout and
+        // lane 0 issues the three split products.  After the transposes, lane (g, t)
+        // holds unit 8 b + g of block b at rays 2t, 2t + 1 (+8 for the second half),
+        // one 4-byte pair of the layout.
+        if (ncommit > 0 && !mbar_wait_bounded(tp.bar, (uint32_t)((ncommit - 1) & 1))) *tp.wait_status = 1;
+        char *const st = reinterpret_cast<char *>(tp.stage_ptr);
+        const int within = g * 16 + 4 * t;
 #pragma unroll
         for (int nk = 0; nk < NC / 8; ++nk) {
-            float d4[4] = {0.f, 0.f, 0.f, 0.f};
-            mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
-            mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
-            mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
-            // fragment order: each atomic of the warp hits 32 consecutive words (no bank conflicts)
-            float *dst = AW2 + (mn * (NC / 8) + nk) * 128 + lane;
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (d4[i] != 0.0f) atomicAdd(dst + 32 * i, d4[i]);
+            for (int h = 0; h < 2; ++h) {
+                const int off = nk * (int)kUmmaSbo + h * (int)kUmmaLbo + within;
+                *reinterpret_cast<uint32_t *>(st + 4096 + off) = tzh[nk][h];
+                *reinterpret_cast<uint32_t *>(st + 6144 + off) = tzl[nk][h];
+            }
+        }
+#pragma unroll
+        for (int mn = 0; mn < NC / 16; ++mn) {
+            // (unit block, ray half) of th[i]: (2 mn, 0), (2 mn + 1, 0), (2 mn, 1), (2 mn + 1, 1)
+            const uint32_t th[4] = {movm_trans(gh[mn][0]), movm_trans(gh[mn][2]), movm_trans(gh[mn][1]),
+                                    movm_trans(gh[mn][3])};
+            const uint32_t tl[4] = {movm_trans(gl[mn][0]), movm_trans(gl[mn][2]), movm_trans(gl[mn][1]),
+                                    movm_trans(gl[mn][3])};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int off = (2 * mn + (i & 1)) * (int)kUmmaSbo + (i >> 1) * (int)kUmmaLbo + within;
+                *reinterpret_cast<uint32_t *>(st + off) = th[i];
+                *reinterpret_cast<uint32_t *>(st + 2048 + off) = tl[i];
+            }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            // One issuer at a time across the CTA, so that the MMAs of one entry's passes
+            // (and its first, overwriting one) reach the tensor core in a defined order.
+            int it = 0;
+            while (atomicCAS(tp.lock, 0, 1) != 0) {
+                if (++it > kWaitLimit) {
+                    *tp.wait_status = 1;
+                    break;
+                }
+            }
+            __threadfence_block();
+            tc_fence_after_sync();
+            volatile int *started = tp.started;
+            const bool acc_in = *started != 0;
+            *started = 1;
+            const uint32_t sa = tp.stage;
+            constexpr uint32_t idesc = umma_idesc_bf16(64, NC);
+            umma_bf16(tp.d_tmem, umma_smem_desc(sa + 2048), umma_smem_desc(sa + 4096), idesc, acc_in);
+            umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + 6144), idesc, true);
+            umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + 4096), idesc, true);
+            umma_commit(tp.bar);
+            tc_fence_before_sync();
+            __threadfence_block();
+            atomicExch(tp.lock, 0);
+        }
+        __syncwarp();
+        ++ncommit;
+    } else {
+#pragma unroll
+        for (int mn = 0; mn < NC / 16; ++mn) {
+            const uint32_t th[4] = {movm_trans(gh[mn][0]), movm_trans(gh[mn][2]), movm_trans(gh[mn][1]),
+                                    movm_trans(gh[mn][3])};
+            const uint32_t tl[4] = {movm_trans(gl[mn][0]), movm_trans(gl[mn][2]), movm_trans(gl[mn][1]),
+                                    movm_trans(gl[mn][3])};
+#pragma unroll
+            for (int nk = 0; nk < NC / 8; ++nk) {
+                float d4[4] = {0.f, 0.f, 0.f, 0.f};
+                mma16816(d4, tl, tzh[nk][0], tzh[nk][1]);
+                mma16816(d4, th, tzl[nk][0], tzl[nk][1]);
+                mma16816(d4, th, tzh[nk][0], tzh[nk][1]);
+                // fragment order: each atomic of the warp hits 32 consecutive words (no bank conflicts)
+                float *dst = AW2 + (mn * (NC / 8) + nk) * 128 + lane;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (d4[i] != 0.0f) atomicAdd(dst + 32 * i, d4[i]);
+            }
         }
     }
 }

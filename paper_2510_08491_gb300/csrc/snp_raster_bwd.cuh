@@ -49,7 +49,9 @@ __host__ __device__ constexpr int net_stride(int ns, int nc, bool sh, bool dyn)
 //   [0, stride)             the primitive's network-gradient record in the caller's
 //                           layout (snp_net_layout).  W1 and b1 hold gradients w.r.t.
 //                           the staged rows w0 W1, w0 b1, and Wc2 is in mma fragment
-//                           order (see warp_color_bwd_pass), until the flush;
+//                           order (see warp_color_bwd_pass), until the flush (at
+//                           N_c = 64 it is accumulated in tensor memory instead and
+//                           written here row-major just before the flush);
 //   [stride, +kGvFloats)    the per-(view, primitive) geometry gradient record;
 //   [.., +n_c)              dL/dh0 (the folded first-layer bias).
 // The flush adds the three blocks to global memory with bulk asynchronous
@@ -72,12 +74,12 @@ __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, 
 // skipped.  All threads call it.  The reads of the bulk adds complete in the
 // background: the kernel waits for them (thread 0) and clears the accumulators
 // only in the next chunk, before its first accumulation.
-template <int NC, int NT>
+template <int NC, int NT, bool TM>
 __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int vg, const uint32_t *s_gid, int cnt,
                                             const int *na, int64_t vn, int tid, int nt, float xi)
 {
     const int ns = a.n_sigma;
-    if constexpr (NC > 0) {
+    if constexpr (NC > 0 && !TM) {  // (TM: the blocks came out of tensor memory row-major)
         // The fragment-order tiles (mn, nk) of row block mn hold exactly the rows
         // 16 mn .. 16 mn + 15 of Wc2, and in both layouts that block occupies the
         // same 16 NC words: permute block by block, in rounds of BR blocks held in
@@ -332,12 +334,18 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
 
 }
 
+// Whether the backward accumulates dL/dWc2 in tensor memory (tcgen05; N_c = 64 on
+// 256-thread tiles, which run one CTA per SM) instead of shared-memory atomics.
+__host__ __device__ constexpr bool bwd_tmem(int ts, int nc) { return nc == 64 && ts >= 16; }
+constexpr int kTmemStageBytes = 8192;  // per warp: A hi, A lo, B hi, B lo tiles of 64 x 16 bf16
+
 template <int TS>
 __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk, int stride)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
     const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(stride, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2);
-    return NPIX * (32 + 12) + (size_t)chunk * per_entry;
+    const size_t stage = bwd_tmem(TS, nc) ? (size_t)(TileCfg<TS>::NT / 32) * kTmemStageBytes + 128 : 0;
+    return NPIX * (32 + 12) + (size_t)chunk * per_entry + stage;
 }
 
 template <int TS, int NC, int FORM, bool BF16>
@@ -360,6 +368,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     float4 *s_cs = reinterpret_cast<float4 *>(acc + CH * vg);
     float *s_w = reinterpret_cast<float *>(s_cs + CH * NPIX);  // [CH][NPIX] weights of the composited pairs
     uint16_t *s_al = reinterpret_cast<uint16_t *>(s_w + CH * NPIX);  // [CH][NPIX] pair lists
+    constexpr bool TM = bwd_tmem(TS, NC);
+    // TM: per warp, the operand tiles of its tcgen05.mma (128-byte aligned)
+    char *s_stage = reinterpret_cast<char *>(
+        (reinterpret_cast<uintptr_t>(s_al + CH * NPIX) + 127) & ~static_cast<uintptr_t>(127));
     __shared__ uint32_t s_gid[kMaxChunk];
     __shared__ uint32_t s_koff[64];         // colour-store offsets of the chunk's keys (two halves)
     __shared__ bool s_stored;               // every composited pair of the chunk is in the store
@@ -368,11 +380,32 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     __shared__ int s_view, s_item;
     __shared__ int s_item6;  // P6 item counter (items past the first one of each warp)
     __shared__ uint32_t s_maxwalk;
+    // TM: per-warp MMA barriers, the TMEM base address, the issue lock and per-entry
+    // "accumulator written in this chunk" flags
+    __shared__ __align__(8) uint64_t s_tmbar[NT / 32];
+    __shared__ uint32_t s_tmaddr;
+    __shared__ int s_tmlock;
+    __shared__ int s_tmstart[kMaxChunk / 2];
 
     const int tid = threadIdx.x;
     const unsigned lane = lane_id();
     const int wid = tid >> 5;
     for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
+    // TM: TMEM columns for the chunk's 64 x 64 accumulators (entry e at columns 64 e)
+    uint32_t tm_cols = 64;
+    while ((int)tm_cols < 64 * CH) tm_cols <<= 1;
+    int ncommit = 0;
+    if constexpr (TM) {
+        if (tid < NT / 32) mbar_init(&s_tmbar[tid], 1);
+        if (tid == 0) {
+            s_tmlock = 0;
+            mbar_init_fence();
+        }
+        if (wid == 0) tmem_alloc(&s_tmaddr, tm_cols);
+        tc_fence_before_sync();
+        __syncthreads();
+        tc_fence_after_sync();
+    }
     int clear_n = 0;  // float4s of accumulators the next chunk clears (after the bulk reads)
 
     for (;;) {
@@ -454,6 +487,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             }
             if (tid < cnt) {
                 s_na[tid] = 0;
+                if constexpr (TM) s_tmstart[tid] = 0;
             }
             if (tid == 0) s_item6 = 0;
             __syncthreads();
@@ -612,12 +646,23 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         if constexpr (NC > 0) {
                             while (it >= s_pp[ec + 1]) ++ec;
                             float *A = acc + ec * vg;
-                            warp_color_bwd_pass<NC, BF16>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
-                                                          s_al + ec * NPIX, (it - s_pp[ec]) * 16, s_na[ec],
-                                                          s_w + ec * NPIX, s_dl, NPIX,
-                                                          reinterpret_cast<const float *>(s_cs + ec * NPIX), 4, 1,
-                                                          A + a.off_Wc1, A + a.stride + kGvFloats, A + a.off_Wc2,
-                                                          A + a.off_Wc3, A + a.off_bc2, A + a.off_bc3);
+                            TmemPass tp{};
+                            if constexpr (TM) {
+                                tp.stage_ptr = s_stage + wid * kTmemStageBytes;
+                                tp.stage = cvta_smem(tp.stage_ptr);
+                                tp.bar = &s_tmbar[wid];
+                                tp.d_tmem = s_tmaddr + 64u * (uint32_t)ec;
+                                tp.started = &s_tmstart[ec];
+                                tp.lock = &s_tmlock;
+                                tp.wait_status = a.wait_status;
+                            }
+                            warp_color_bwd_pass<NC, BF16, TM>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
+                                                              s_al + ec * NPIX, (it - s_pp[ec]) * 16, s_na[ec],
+                                                              s_w + ec * NPIX, s_dl, NPIX,
+                                                              reinterpret_cast<const float *>(s_cs + ec * NPIX), 4,
+                                                              1, A + a.off_Wc1, A + a.stride + kGvFloats,
+                                                              A + a.off_Wc2, A + a.off_Wc3, A + a.off_bc2,
+                                                              A + a.off_bc3, tp, ncommit);
                         }
                     } else {
                         const int q = it - np;
@@ -641,14 +686,49 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     it = __shfl_sync(0xffffffffu, nx, 0);
                 }
             }
+            if constexpr (TM) {
+                // this warp's last MMAs have completed (and read its operand tiles)
+                if (ncommit > 0 && !mbar_wait_bounded(&s_tmbar[wid], (uint32_t)((ncommit - 1) & 1)))
+                    *a.wait_status = 1;
+                tc_fence_before_sync();
+            }
             __syncthreads();
-            flush_chunk<NC, NT>(a, acc, vg, cg, cnt, s_na, vn, tid, NT, V.time);
+            if constexpr (TM) {
+                // dL/dWc2 of every composited entry from TMEM into its accumulator block,
+                // row-major (the layout the flush reduces): warp w reads TMEM lanes
+                // 32 (w % 4) .. + 15, i.e. rows 16 (w % 4) .. + 15, columns 32 (w / 4) .. + 31
+                tc_fence_after_sync();
+                const int q = wid & 3, half = wid >> 2;
+                for (int e = 0; e < cnt; ++e) {
+                    if (s_na[e] == 0) continue;
+                    uint32_t r[32];
+                    tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)e + 32u * (uint32_t)half, r);
+                    if (lane < 16) {
+                        float4 *dst = reinterpret_cast<float4 *>(acc + e * vg + a.off_Wc2 + (16 * q + (int)lane) * 64 +
+                                                                 32 * half);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                    }
+                }
+                tc_fence_before_sync();
+                __syncthreads();
+            }
+            flush_chunk<NC, NT, TM>(a, acc, vg, cg, cnt, s_na, vn, tid, NT, V.time);
             clear_n = cnt * vg / 4;
         }
         __syncthreads();
     }
     // the bulk reductions must complete before the CTA exits
     if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+    if constexpr (TM) {
+        // every MMA completed at its chunk's end; give the columns back
+        tc_fence_before_sync();
+        __syncthreads();
+        tc_fence_after_sync();
+        if (wid == 0) tmem_dealloc(s_tmaddr, tm_cols);
+    }
 }
 
 }  // namespace snp

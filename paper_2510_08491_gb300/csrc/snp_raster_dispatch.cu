@@ -31,7 +31,10 @@ int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, in
 {
     const int fmb = fwd_min_blocks(ts, nc_of(color_mode, n_c));
     const size_t fwd_budget = fmb == 4 ? 52 * 1024 : (fmb == 3 ? 70 * 1024 : 104 * 1024);
-    const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2 ? 110 * 1024 : 200 * 1024;
+    // (the tensor-memory backward at N_c = 64 also holds its operand tiles: most of one SM)
+    const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2
+                                  ? 110 * 1024
+                                  : (bwd_tmem(ts, nc_of(color_mode, n_c)) ? 220 * 1024 : 200 * 1024);
     int ch = backward ? 8 : 32;
     if (backward) {
         while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts, dyn) > bwd_budget) --ch;

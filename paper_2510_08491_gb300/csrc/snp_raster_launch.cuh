@@ -60,8 +60,9 @@ template <int TS, int NC, int FORM, bool BF16>
 static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
 {
     const size_t smem = bwd_smem_bytes<TS>(NC, a.n_sigma, a.chunk, a.stride);
+    // (the tensor-memory accumulators of a chunk take 64 columns per entry, at most 512)
     if (smem > kSmemMax || a.chunk < 1 || a.chunk > 32 || a.chunk * (TS * TS / 32) > kMaskWords / 2 ||
-        a.stride != net_stride(a.n_sigma, NC, a.off_sh >= 0, a.off_wt >= 0))
+        (bwd_tmem(TS, NC) && a.chunk > 8) || a.stride != net_stride(a.n_sigma, NC, a.off_sh >= 0, a.off_wt >= 0))
         return SNP_ERR_INVALID_ARG;
     if (a.n_tiles <= 0) return SNP_OK;
     auto kern = k_raster_bwd<TS, NC, FORM, BF16>;
