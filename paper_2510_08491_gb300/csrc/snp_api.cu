@@ -749,6 +749,10 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     a.g_h0 = (float *)ctx->g_h0.p;
     a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true, ctx->ts, desc->dynamic != 0);
     if (ctx->cfg.chunk > 0 && ctx->cfg.chunk < a.chunk) a.chunk = ctx->cfg.chunk;
+    // test hook: SNP_TEST_STUCK_WAIT=1 makes the tensor-memory backward (N_c = 64) run
+    // one bounded wait out, so that tests can check that it is reported
+    // (SNP_ERR_TIMEOUT from snp_get_stats) and that the context stays usable
+    if (const char *sw = getenv("SNP_TEST_STUCK_WAIT")) a.test_stuck_wait = atoi(sw) != 0;
     int *d_work = (int *)((char *)ctx->small.p + kSmallWork);
     a.work_counter = d_work;
     a.queue = (ctx->cfg.flags & SNP_FLAG_LENGTH_QUEUE)

@@ -80,6 +80,9 @@ struct RasterArgs {
     uint32_t col_cap;         // capacity in pairs
     // set to 1 by a kernel whose bounded device wait gave up (zeroed with each forward)
     int *wait_status;
+    // test hook: the tensor-memory backward first waits, with a short limit, on a
+    // barrier phase that nothing completes, so that a test can see the status
+    int32_t test_stuck_wait;
 };
 
 constexpr uint32_t kNoStore = 0xffffffffu;

@@ -70,20 +70,34 @@ __device__ __forceinline__ void cp_async_wait_all()
 // cp.async.wait_group has completed.  (The colour-MLP kernels keep the
 // per-entry loop and never see the shift, so their register allocation is
 // unchanged.)
+// With BF16 weights the lo half of the staged Wc2 is zero and never read: its
+// 16-byte pieces of an entry, [w2lo_first, + w2lo_count), are not copied.
+__device__ __forceinline__ int w2lo_first(int ns, int nc)
+{
+    return (kRecFloats + den_stride(ns) + cb_W2(nc) + nc * w2_ld(nc) / 2) / 4;
+}
+__host__ __device__ constexpr int w2lo_count(int nc) { return nc * w2_ld(nc) / 8; }
+
 // The copies of stage_chunk for a colour-network kernel, without the wait: the
 // caller issues more copies (the colour store's) and waits once for all.
+template <int NC, bool BF16>
 __device__ __forceinline__ void stage_chunk_issue(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
                                                   const RasterArgs &a, int es)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr int kRec16 = kRecFloats / 4;
-    const int per = es / 4;
+    constexpr int skip = BF16 ? w2lo_count(NC) : 0;
+    const int lo0 = w2lo_first(a.n_sigma, NC);
+    const int per = es / 4 - skip;
     for (int e = 0; e < cnt; ++e) {
         const int64_t gid = s_gid[e];
         const float *rec = a.rec + gid * kRecFloats;
         const float *net = a.npack + (gid - vn) * a.npack_stride;
         float *dst = sm + e * es;
-        for (int q = tid; q < per; q += nt) cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
+        for (int c = tid; c < per; c += nt) {
+            const int q = (skip > 0 && c >= lo0) ? c + skip : c;
+            cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
+        }
     }
 }
 
@@ -114,14 +128,7 @@ __device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, in
             }
         }
     } else {
-        for (int e = 0; e < cnt; ++e) {
-            const int64_t gid = s_gid[e];
-            const float *rec = a.rec + gid * kRecFloats;
-            const float *net = a.npack + (gid - vn) * a.npack_stride;
-            float *dst = sm + e * es;
-            for (int q = tid; q < per; q += nt)
-                cp_async16(dst + 4 * q, q < kRec16 ? rec + 4 * q : net + 4 * (q - kRec16));
-        }
+        stage_chunk_issue<NC, BF16>(sm, s_gid, cnt, vn, a, es);
         cp_async_wait_all();
     }
 }

@@ -405,6 +405,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
         tc_fence_before_sync();
         __syncthreads();
         tc_fence_after_sync();
+        // test hook: phase 0 of this barrier completes only after this warp's first MMA
+        // group, which has not been issued yet, so this wait runs out
+        if (a.test_stuck_wait && tid == 0 && !mbar_wait_bounded(&s_tmbar[0], 0u, 1 << 12)) *a.wait_status = 1;
     }
     int clear_n = 0;  // float4s of accumulators the next chunk clears (after the bulk reads)
 
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             if constexpr (NC > 0) {
                 // staging copies in flight through P1, which needs only the masks; one
                 // wait below covers them and P1's colour-store copies
-                stage_chunk_issue(sm, cg, cnt, vn, a, es);
+                stage_chunk_issue<NC, BF16>(sm, cg, cnt, vn, a, es);
             } else {
                 stage_chunk<NC, BF16>(sm, cg, cnt, vn, a, es, V.time);
                 __syncthreads();

@@ -197,3 +197,40 @@ def test_mlp_colour_store_partly_full(R, oracle_lib, monkeypatch):
     for k in fields:
         scale = np.abs(g[k]).max() + 1e-30
         assert np.abs(g[k] - g_replay[k]).max() <= 1e-5 * scale, k
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_recovers(R, monkeypatch):
+    """The backward at N_c = 64 (tensor-memory accumulation) bounds every wait.  A
+    host-side hook (SNP_TEST_STUCK_WAIT) makes one of them wait on a barrier phase
+    that nothing completes: the wait gives up, the backward still finishes with the
+    same gradients, snp_get_stats reports SNP_ERR_TIMEOUT, and the next forward
+    clears the status."""
+    from paper_2510_08491_gb300 import _lib as L
+    from paper_2510_08491_gb300.render import pack_scene
+    sc = synth.make_scene(800, seed=8, center_half=1.5, n_sigma=32, omega0=5.0, color="mlp", n_c=64).to_bf16()
+    cams = [synth.look_at_camera((0.0, 0.0, 6.0), (0, 0, 0), 64, 48)]
+    ps = pack_scene(sc)
+    dL = torch.randn((cams[0].n_pixels, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+
+    def run():
+        R.forward(ps, cams, L.make_config())
+        gg = torch.zeros_like(ps.geom)
+        gn = torch.zeros(ps.net.shape, dtype=torch.float32, device="cuda")
+        R.backward(ps, dL, gg, gn)
+        torch.cuda.synchronize()
+        return gg, gn
+
+    ref = run()
+    R.stats()
+    monkeypatch.setenv("SNP_TEST_STUCK_WAIT", "1")
+    got = run()
+    with pytest.raises(L.SnpError) as ei:
+        R.stats()
+    assert ei.value.status == L.SNP_ERR_TIMEOUT
+    for a, b in zip(got, ref):
+        assert (a - b).abs().max().item() <= 1e-5 * (b.abs().max().item() + 1e-12)
+    monkeypatch.delenv("SNP_TEST_STUCK_WAIT")
+    again = run()
+    R.stats()  # cleared by the forward, and no wait gave up
+    for a, b in zip(again, ref):
+        assert (a - b).abs().max().item() <= 1e-5 * (b.abs().max().item() + 1e-12)
