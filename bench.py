@@ -62,7 +62,8 @@ def work_per_unit(n_sigma: int, n_c: int, colour_store: bool):
                           (layer-1 replay, layer-3 and layer-1 reverse), 3 N_c^2 tensor
                           (hidden-layer replay, its input gradient, its weight gradient)
                no store   + the forward's hit and candidate work per composited pair (the
-                          alpha_hat replay) and, with a colour network, its forward
+                          alpha_hat replay) and, with a colour network, its forward (the
+                          store holds colour and alpha_hat, or alpha_hat alone)
     The backward tests no candidates: its pair lists come from the forward's
     composited masks."""
     ns, nc = n_sigma, n_c
@@ -71,7 +72,7 @@ def work_per_unit(n_sigma: int, n_c: int, colour_store: bool):
            "hit": (29 + 15 * ns, 0, 2 + 3 * ns),
            "comp": (10 + (6 * nc + 3 if mlp else 0), nc * nc, 2 + (6 if mlp else 0))}
     comp = [177 + 40 * ns + 14 * nc, 3 * nc * nc, 3 + 5 * ns]
-    if not (mlp and colour_store):
+    if not colour_store:
         comp[0] += 28 + 29 + 15 * ns
         comp[2] += 2 + 3 * ns
         if mlp:
@@ -669,7 +670,7 @@ def run_ours(args, rank, world):
     # roofline of the raster kernels (per pipe; the dominant kernel's binding pipe is the headline)
     peaks = device_peaks(dev)
     nc_eff = sc.n_c if sc.color == "mlp" else 0
-    colour_store = sc.color == "mlp" and not args.replay_color
+    colour_store = not args.replay_color
     fwd_u, bwd_u = work_per_unit(sc.n_sigma, nc_eff, colour_store)
     t_fwd = st["raster_fwd"][0] / max(st["raster_fwd"][1], 1)
     t_bwd = st["raster_bwd"][0] / max(st["raster_bwd"][1], 1)
@@ -691,7 +692,7 @@ def run_ours(args, rank, world):
                    "tile": int(cfg.tile_size), "chunk": int(cfg.chunk),
                    "step": "forward+loss+backward" if target is not None else "forward+backward",
                    "graph": graph is not None, "autotuned": bool(args.autotune or batched),
-                   "colour_store": sc.color == "mlp" and not args.replay_color,
+                   "colour_store": not args.replay_color,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (network weights %.2f GB)" % (h_net.numel() * h_net.element_size()
                                                                               / 1e9)},

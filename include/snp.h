@@ -178,10 +178,11 @@ typedef struct {
  * decreasing list length instead of row-major order (trades L2 reuse of
  * primitive records between neighbouring tiles for a shorter tail). */
 #define SNP_FLAG_LENGTH_QUEUE 2
-/* snp_config.flags: keep no colour store.  By default a forward of a colour-MLP
- * scene saves the colour and alpha_hat of every composited pair (16 bytes per pair,
- * in a context buffer sized from the previous forward's count) so that the backward
- * does not evaluate the colour network again; with this flag the backward
+/* snp_config.flags: keep no colour store.  By default a forward saves, for every
+ * composited pair, the colour and alpha_hat (colour-MLP scenes, 16 bytes per pair)
+ * or alpha_hat alone (constant or SH colour, 4 bytes per pair), in a context
+ * buffer sized from the previous forward's count, so that the backward evaluates
+ * neither the colour network nor the integral again; with this flag the backward
  * recomputes them (less device memory, slower backward).  Pairs that do not fit the
  * buffer are recomputed either way.  Test hook: a non-negative integer in the
  * environment variable SNP_TEST_COLSTORE_PAIRS caps the store at that many pairs

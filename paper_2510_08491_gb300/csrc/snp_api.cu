@@ -447,6 +447,10 @@ static snp_status ensure_frame(snp_context *ctx, int64_t n, int n_views, int64_t
     return SNP_OK;
 }
 
+// Bytes per composited pair of the forward's store: (colour, alpha_hat) with a
+// colour network, alpha_hat alone otherwise.
+static size_t store_pair_bytes(const snp_scene_desc *d) { return d->color_mode == SNP_COLOR_MLP ? 16 : 4; }
+
 // Colour-store capacity (pairs) for K keys: the previous forward's composited count
 // plus a quarter, else 16 per key, plus the partly used blocks of the forward CTAs;
 // at most every (key, pixel) pair and 2^32 - 2.
@@ -507,8 +511,8 @@ snp_status snp_reserve(snp_context *ctx, const snp_scene_desc *desc, const snp_c
         ENS(g_view, (size_t)desc->n * n_cams * kGvFloats * 4);
         ENS(g_h0, (size_t)desc->n * nc * 4);
     }
-    if (desc->color_mode == SNP_COLOR_MLP && !(cfg && (cfg->flags & SNP_FLAG_REPLAY_COLOR)))
-        ENS(colstore, (size_t)col_pairs_wanted(ctx, max_keys, ts) * 16);
+    if (!(cfg && (cfg->flags & SNP_FLAG_REPLAY_COLOR)))
+        ENS(colstore, (size_t)col_pairs_wanted(ctx, max_keys, ts) * store_pair_bytes(desc));
     ctx->key_cap = max_keys;
     ctx->reserved = true;
     return SNP_OK;
@@ -672,22 +676,24 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
                   ? (const uint32_t *)(ctx->queue_in_alt ? ctx->qvals_alt.p : ctx->qvals.p)
                   : nullptr;
     CK(cudaMemsetAsync(d_work, 0, 4, st));
-    ctx->col_on = desc->color_mode == SNP_COLOR_MLP && !(c.flags & SNP_FLAG_REPLAY_COLOR);
+    const size_t spb = store_pair_bytes(desc);
+    ctx->col_on = !(c.flags & SNP_FLAG_REPLAY_COLOR);
     if (ctx->col_on && !ctx->reserved &&
-        ensure(ctx, ctx->colstore, (size_t)col_pairs_wanted(ctx, key_bound, ts) * 16, "colstore") != SNP_OK) {
-        // no room for the store: the backward recomputes the colours instead
+        ensure(ctx, ctx->colstore, (size_t)col_pairs_wanted(ctx, key_bound, ts) * spb, "colstore") != SNP_OK) {
+        // no room for the store: the backward recomputes the colours / alpha_hat instead
         cudaGetLastError();
         ctx->err[0] = 0;
         ctx->col_on = false;
     }
-    if (ctx->col_on) ctx->col_on = ctx->colstore.bytes >= 16;
+    if (ctx->col_on) ctx->col_on = ctx->colstore.bytes >= spb;
     if (ctx->col_on) {
         unsigned long long *d_col = (unsigned long long *)((char *)ctx->small.p + kSmallColCount);
         CK(cudaMemsetAsync(d_col, 0, 8, st));
-        a.colstore = (float4 *)ctx->colstore.p;
+        if (desc->color_mode == SNP_COLOR_MLP) a.colstore = (float4 *)ctx->colstore.p;
+        else a.ahstore = (float *)ctx->colstore.p;
         a.key_off = (uint32_t *)ctx->key_off.p;
         a.col_count = d_col;
-        a.col_cap = (uint32_t)std::min<size_t>(ctx->colstore.bytes / 16, (size_t)0xfffffffe);
+        a.col_cap = (uint32_t)std::min<size_t>(ctx->colstore.bytes / spb, (size_t)0xfffffffe);
         // test hook: SNP_TEST_COLSTORE_PAIRS caps the store, so that tests can drive the
         // backward's per-chunk recomputation of the pairs that did not fit
         if (const char *cap_env = getenv("SNP_TEST_COLSTORE_PAIRS")) {
@@ -738,7 +744,8 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     RasterArgs a;
     fill_args(a, ctx, desc, scene, svals);
     if (ctx->col_on) {
-        a.colstore = (float4 *)ctx->colstore.p;
+        if (desc->color_mode == SNP_COLOR_MLP) a.colstore = (float4 *)ctx->colstore.p;
+        else a.ahstore = (float *)ctx->colstore.p;
         a.key_off = (uint32_t *)ctx->key_off.p;
     }
     a.px_state = (float4 *)ctx->px_state.p;

@@ -78,6 +78,9 @@ struct RasterArgs {
     uint32_t *key_off;        // [K] first colstore index of each key's pairs (kNoStore: not stored)
     unsigned long long *col_count;  // bump allocator of the forward (zeroed before it)
     uint32_t col_cap;         // capacity in pairs
+    // alpha_hat store (scenes without a colour network): the same scheme with one
+    // float per composited pair, in the colour store's buffer.  NULL: off.
+    float *ahstore;
     // set to 1 by a kernel whose bounded device wait gave up (zeroed with each forward)
     int *wait_status;
     // test hook: the tensor-memory backward first waits, with a short limit, on a

@@ -6,8 +6,9 @@
 //          from the forward's composited masks (a pixel's position is its rank
 //          among the mask's set bits);
 //   P2/P4  alpha_hat and the colour of every composited pair are copied back from
-//          the forward's colour store at that rank, or -- where the store was
-//          full or is off, and always without a colour network -- recomputed;
+//          the forward's colour store at that rank (without a colour network:
+//          alpha_hat from the alpha_hat store, the colour from the staged record),
+//          or -- where the store was full or is off -- recomputed;
 //   P3/P5  each pixel replays its weights and the gradient of its colour with
 //          respect to alpha_hat in list order;
 //   P6     the per-pair gradients run as work items (colour passes first).
@@ -390,6 +391,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const int tid = threadIdx.x;
     const unsigned lane = lane_id();
     const int wid = tid >> 5;
+    // the forward's per-pair store: (colour, alpha_hat) with a colour network, else alpha_hat
+    const bool has_store = NC > 0 ? a.colstore != nullptr : a.ahstore != nullptr;
     for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
     // TM: TMEM columns for the chunk's 64 x 64 accumulators (entry e at columns 64 e)
     uint32_t tm_cols = 64;
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             } else {
                 if (tid < cnt) {
                     cg[tid] = a.vals[c0 + tid];
-                    if constexpr (NC > 0) cko[tid] = a.colstore ? a.key_off[c0 + tid] : kNoStore;
+                    cko[tid] = has_store ? a.key_off[c0 + tid] : kNoStore;
                 }
                 // composited masks of the chunk's entries (none past the tile's walk length)
                 for (int i = tid; i < cnt * (NPIX / 32); i += NT) {
@@ -520,11 +523,21 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     if (act) {
                         const uint32_t rank = mask_rank<NPIX>(cmw + e * (NPIX / 32), slot);
                         s_al[e * NPIX + rank] = (uint16_t)slot;
-                        if constexpr (NC > 0) {
-                            // the pair's (colour, alpha_hat) from the forward's store, copied
-                            // asynchronously while the lists are built
-                            const uint32_t o = cko[e];
-                            if (o != kNoStore) cp_async16(s_cs + e * NPIX + slot, a.colstore + o + rank);
+                        const uint32_t o = cko[e];
+                        if (o != kNoStore) {
+                            if constexpr (NC > 0) {
+                                // the pair's (colour, alpha_hat) from the forward's store, copied
+                                // asynchronously while the lists are built
+                                cp_async16(s_cs + e * NPIX + slot, a.colstore + o + rank);
+                            } else {
+                                // the primitive's colour from its staged record, alpha_hat from the store
+                                const float *R = sm + e * es;
+                                float *cs = reinterpret_cast<float *>(s_cs + e * NPIX + slot);
+                                cs[0] = R[kRecRgb + 0];
+                                cs[1] = R[kRecRgb + 1];
+                                cs[2] = R[kRecRgb + 2];
+                                cp_async4(cs + 3, a.ahstore + o + rank);
+                            }
                         }
                     }
                 }
@@ -534,7 +547,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 for (int w = 0; w < NPIX / 32; ++w) c += __popc(cmw[tid * (NPIX / 32) + w]);
                 s_na[tid] = c;
             }
-            if constexpr (NC > 0) cp_async_wait_all();
+            if (NC > 0 || has_store) cp_async_wait_all();
             // the previous chunk's bulk adds have read its accumulators by now
             if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
             __syncthreads();
@@ -546,23 +559,20 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 warp_prefix64(s_na, cnt, s_pa);
                 warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
                 warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
-                if constexpr (NC > 0) {
-                    const bool miss = (int)lane < cnt && s_na[lane] > 0 && cko[lane] == kNoStore;
-                    const bool miss2 = (int)lane + 32 < cnt && s_na[lane + 32] > 0 && cko[lane + 32] == kNoStore;
-                    const bool any = __any_sync(0xffffffffu, miss || miss2);
-                    if (lane == 0) s_stored = !any;
-                }
+                const bool miss = (int)lane < cnt && s_na[lane] > 0 && cko[lane] == kNoStore;
+                const bool miss2 = (int)lane + 32 < cnt && s_na[lane + 32] > 0 && cko[lane + 32] == kNoStore;
+                const bool any = __any_sync(0xffffffffu, miss || miss2);
+                if (lane == 0) s_stored = !any;
             }
             __syncthreads();
-            bool stored = false;
-            if constexpr (NC > 0) stored = s_stored;
+            const bool stored = s_stored;
             // P2: alpha_hat of every composited pair (per thread), then P4: their colours
             // (per warp, 16 pairs of one entry); independent, so one phase.  With the
             // colour store both come from the forward (one 16-byte load per pair).
             {
                 const int na = s_pa[cnt];
                 int e = 0;
-                for (int q = tid; q < (NC > 0 && stored ? 0 : na); q += NT) {
+                for (int q = tid; q < (stored ? 0 : na); q += NT) {
                     while (q >= s_pa[e + 1]) ++e;
                     const int pix = s_al[e * NPIX + (q - s_pa[e])];
                     const float *R = sm + e * es;
@@ -622,10 +632,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     uint32_t *const nmw = s_cmw + ((ci + 1) & 1) * (kMaskWords / 2);
                     if (tid < cntn) {
                         cp_async4(ng + tid, a.vals + c0n + tid);
-                        if constexpr (NC > 0) {
-                            if (a.colstore) cp_async4(nko + tid, a.key_off + c0n + tid);
-                            else nko[tid] = kNoStore;
-                        }
+                        if (has_store) cp_async4(nko + tid, a.key_off + c0n + tid);
+                        else nko[tid] = kNoStore;
                     }
                     for (int i = tid; i < cntn * (NPIX / 32); i += NT) {
                         const int e = i / (NPIX / 32);

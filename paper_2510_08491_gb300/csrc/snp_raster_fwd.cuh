@@ -32,9 +32,79 @@ __host__ __device__ inline size_t fwd_smem_bytes(int nc, int ns, int chunk)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
     const size_t per_entry = (size_t)entry_stride(ns, nc) * 4 + NPIX * 4 /* alpha_hat */ + NPIX * 2 /* hit list */ +
-                             (nc > 0 ? NPIX * (4 + 12 + 2) /* weight, colour, list */ +
-                                           (NPIX / 32 + 1) * 4 /* mask words, store offset */ : 0);
+                             (nc > 0 ? NPIX * (4 + 12 + 2) /* weight, colour, list */ : 0) +
+                             (NPIX / 32 + 1) * 4 /* mask words, store offset */;
     return NPIX * 32 /* rays */ + (size_t)chunk * per_entry;
+}
+
+// One warp: the chunk's slice of the forward's store (colour store, or alpha_hat
+// store without a colour network), split by entry in list order (count[e] pairs
+// each), taken from the CTA's current block or a new block of the global bump
+// allocator; a chunk that does not fit gets kNoStore and the backward recomputes
+// it.  Writes koff[e] and the keys' global offsets.
+__device__ __forceinline__ void store_slices(const RasterArgs &a, const int *count, int cnt, uint32_t c0, int *pc,
+                                             uint32_t *koff, unsigned long long &cbase, unsigned long long &blk_next,
+                                             unsigned long long &blk_end)
+{
+    const int lane = threadIdx.x & 31;
+    warp_prefix64(count, cnt, pc);
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned long long tot = (unsigned long long)pc[cnt];
+        if (blk_next + tot > blk_end) {
+            // a new block of the store for this CTA (the rest of the old one is left unused)
+            const unsigned long long want = tot > kColBlock ? tot : kColBlock;
+            const unsigned long long b = atomicAdd(a.col_count, want);
+            const bool fits = b + want <= (unsigned long long)a.col_cap;
+            blk_next = fits ? b : 0ull;
+            blk_end = fits ? b + want : 0ull;
+        }
+        if (blk_next + tot <= blk_end) {
+            cbase = blk_next;
+            blk_next += tot;
+        } else {
+            cbase = ~0ull;  // store full: the backward recomputes this chunk
+        }
+    }
+    __syncwarp();
+    for (int ei = lane; ei < cnt; ei += 32) {
+        const uint32_t o = cbase == ~0ull ? kNoStore : (uint32_t)(cbase + pc[ei]);
+        koff[ei] = o;
+        a.key_off[c0 + ei] = o;
+    }
+}
+
+// One warp: per-entry composited counts of a chunk (cnt entries) from its masks,
+// then the chunk's slice of the alpha_hat store.
+template <int NPIX>
+__device__ __forceinline__ void ahstore_slices(const RasterArgs &a, const uint32_t *cw, int cnt, uint32_t c0,
+                                                 int *count, int *pc, uint32_t *koff, unsigned long long &cbase,
+                                                 unsigned long long &blk_next, unsigned long long &blk_end)
+{
+    for (int e = threadIdx.x & 31; e < cnt; e += 32) {
+        int c = 0;
+        for (int w = 0; w < NPIX / 32; ++w) c += __popc(cw[e * (NPIX / 32) + w]);
+        count[e] = c;
+    }
+    __syncwarp();
+    store_slices(a, count, cnt, c0, pc, koff, cbase, blk_next, blk_end);
+}
+
+// Each thread writes alpha_hat of its pixels' composited pairs of a chunk (bit e of
+// m[k]: pixel k composited entry e) at their ranks in the entries' store slices.
+template <int NPIX, int NT, int PPT>
+__device__ __forceinline__ void ahstore_write(const RasterArgs &a, const uint64_t (&m)[PPT], const uint32_t *koff,
+                                              const uint32_t *cw, const float *s_ah, int tid)
+{
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int slot = k * NT + tid;
+        for (uint64_t mm = m[k]; mm != 0ull; mm &= mm - 1ull) {
+            const int e = __ffsll((long long)mm) - 1;
+            const uint32_t o = koff[e];
+            if (o != kNoStore) a.ahstore[o + mask_rank<NPIX>(cw + e * (NPIX / 32), slot)] = s_ah[e * NPIX + slot];
+        }
+    }
 }
 
 template <int TS, int NC, int FORM, bool BF16>
@@ -54,8 +124,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
     float *s_col = s_w + (NC > 0 ? CH * NPIX : 0);              // [3][CH][NPIX] colours (MLP)
     uint16_t *s_hl = reinterpret_cast<uint16_t *>(s_col + (NC > 0 ? 3 * CH * NPIX : 0));  // [CH][NPIX]
     uint16_t *s_al = s_hl + CH * NPIX;                          // [CH][NPIX] (MLP)
-    uint32_t *s_cw = reinterpret_cast<uint32_t *>(s_al + (NC > 0 ? CH * NPIX : 0));  // [CH][NPIX/32] masks (MLP)
-    uint32_t *s_koff = s_cw + (NC > 0 ? CH * (NPIX / 32) : 0);  // [CH] colour-store offsets (MLP)
+    uint32_t *s_cw = reinterpret_cast<uint32_t *>(s_al + (NC > 0 ? CH * NPIX : 0));  // [CH][NPIX/32] masks
+    uint32_t *s_koff = s_cw + CH * (NPIX / 32);                  // [CH] store offsets
     __shared__ uint32_t s_gid[kMaxChunk];
     __shared__ int s_pc[65];
     __shared__ unsigned long long s_cbase, s_blk_next, s_blk_end;  // colour store: chunk base, CTA block
@@ -102,6 +172,13 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
         }
         const uint2 rg = a.ranges[tile];
         const int64_t vn = (int64_t)v * a.n;
+        // alpha_hat store (no colour network): the chunk whose writes are still to be made
+        bool pend = false;
+        uint32_t pend_c0 = 0;
+        int pend_cnt = 0;
+        uint64_t pend_m[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) pend_m[k] = 0ull;
 
         // The chunk's record ids live in one half of s_gid; with a colour network the
         // next chunk's are copied into the other half (4-byte cp.async) from P2 on.
@@ -116,10 +193,19 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                 s_nh[tid] = 0;
                 s_na[tid] = 0;
             }
+            if constexpr (NC == 0) {
+                if (pend && tid < 32) ahstore_slices<NPIX>(a, s_cw, pend_cnt, pend_c0, s_nb, s_pc, s_koff, s_cbase, s_blk_next,
+                                                    s_blk_end);
+            }
             if (pre) cp_async_wait_all();
             __syncthreads();
             stage_chunk<NC, BF16>(sm, cg, cnt, vn, a, es, V.time);
             __syncthreads();
+            if constexpr (NC == 0) {
+                // the previous chunk's alpha_hat before P1 clears s_ah (each thread its own pixels)
+                if (pend) ahstore_write<NPIX, NT, PPT>(a, pend_m, s_koff, s_cw, s_ah, tid);
+                pend = false;
+            }
 
             // P1: which pixels' rays enter which ellipsoids
             for (int e = 0; e < cnt; ++e) {
@@ -167,6 +253,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
             __syncthreads();
 
             // P3: compositing weights and termination, in list order
+            uint64_t cmk[PPT];  // (alpha_hat store) entries of the chunk each pixel composited
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) cmk[k] = 0ull;
             for (int e = 0; e < cnt; ++e) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
@@ -182,6 +271,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                             T[k] = __expf(-tau[k]);
                             nwalk[k] = c0 - rg.x + e + 1;
                             act = true;
+                            if constexpr (NC == 0) cmk[k] |= 1ull << e;
                             if constexpr (NC == 0) {
                                 const float *R = sm + e * es;
                                 C[k].x = fmaf(w, R[kRecRgb + 0], C[k].x);
@@ -195,7 +285,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                     const unsigned word = __ballot_sync(0xffffffffu, act);
                     if (lane_id() == 0 && a.cmask)
                         a.cmask[(int64_t)(c0 + e) * (NPIX / 32) + (slot >> 5)] = word;
-                    if constexpr (NC > 0) {
+                    if (NC > 0 || a.ahstore) {
                         if (lane_id() == 0) s_cw[e * (NPIX / 32) + (slot >> 5)] = word;
                     }
                     if constexpr (NC > 0) {
@@ -220,34 +310,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                 if (tid < 32) {
                     // colour-store slice of the chunk (needed from P5 on; here it overlaps
                     // the other warps' colour passes)
-                    if (a.colstore) {
-                        // one slice of the colour store per chunk, split by entry
-                        warp_prefix64(s_na, cnt, s_pc);
-                        __syncwarp();
-                        if (tid == 0) {
-                            const unsigned long long tot = (unsigned long long)s_pc[cnt];
-                            if (s_blk_next + tot > s_blk_end) {
-                                // a new block of the store for this CTA (the rest of the old one is left unused)
-                                const unsigned long long want = tot > kColBlock ? tot : kColBlock;
-                                const unsigned long long b = atomicAdd(a.col_count, want);
-                                const bool fits = b + want <= (unsigned long long)a.col_cap;
-                                s_blk_next = fits ? b : 0ull;
-                                s_blk_end = fits ? b + want : 0ull;
-                            }
-                            if (s_blk_next + tot <= s_blk_end) {
-                                s_cbase = s_blk_next;
-                                s_blk_next += tot;
-                            } else {
-                                s_cbase = ~0ull;  // store full: the backward recomputes this chunk
-                            }
-                        }
-                        __syncwarp();
-                        for (int ei = tid; ei < cnt; ei += 32) {
-                            const uint32_t o = s_cbase == ~0ull ? kNoStore : (uint32_t)(s_cbase + s_pc[ei]);
-                            s_koff[ei] = o;
-                            a.key_off[c0 + ei] = o;
-                        }
-                    }
+                    if (a.colstore) store_slices(a, s_na, cnt, c0, s_pc, s_koff, s_cbase, s_blk_next, s_blk_end);
                 }
                 __syncthreads();
                 // P5: accumulate in list order
@@ -272,12 +335,30 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, fwd_min_blocks(TS, NC)) k_ras
                     }
                 }
             }
+            if constexpr (NC == 0) {
+                // the alpha_hat store's writes of this chunk are made early in the next
+                // chunk (or at the end of the tile), where barriers already are
+                pend = a.ahstore != nullptr;
+                pend_c0 = c0;
+                pend_cnt = cnt;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) pend_m[k] = cmk[k];
+            }
             bool any_alive = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) any_alive |= alive[k];
             if (__syncthreads_and(!any_alive)) break;
         }
         if constexpr (NC > 0) cp_async_wait_all();  // a copy for a chunk the early exit skipped must land first
+        if constexpr (NC == 0) {
+            if (pend) {  // the tile's last chunk
+                __syncthreads();
+                if (tid < 32) ahstore_slices<NPIX>(a, s_cw, pend_cnt, pend_c0, s_nb, s_pc, s_koff, s_cbase, s_blk_next,
+                                             s_blk_end);
+                __syncthreads();
+                ahstore_write<NPIX, NT, PPT>(a, pend_m, s_koff, s_cw, s_ah, tid);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             if (!inside[k]) continue;

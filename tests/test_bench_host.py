@@ -21,9 +21,10 @@ def test_work_model_counts():
     _, bwd_replay = bench.work_per_unit(ns, nc, colour_store=False)
     assert bwd_replay["comp"][0] == bwd["comp"][0] + 28 + 29 + 15 * ns + 6 * nc + 3
     assert bwd_replay["comp"][1] == 4 * nc * nc
-    f0, b0 = bench.work_per_unit(8, 0, colour_store=True)   # no colour network: no store, alpha_hat replayed
-    assert f0["comp"] == (10, 0, 2) and b0["comp"][1] == 0
-    assert b0["comp"][0] == 177 + 40 * 8 + 28 + 29 + 15 * 8
+    f0, b0 = bench.work_per_unit(8, 0, colour_store=True)   # no colour network: alpha_hat store
+    assert f0["comp"] == (10, 0, 2) and b0["comp"] == (177 + 40 * 8, 0, 3 + 5 * 8)
+    _, b0r = bench.work_per_unit(8, 0, colour_store=False)  # alpha_hat replayed
+    assert b0r["comp"][0] == 177 + 40 * 8 + 28 + 29 + 15 * 8
     counts = {"cand": 1000, "hit": 400, "comp": 100}
     fp32, tensor, mufu = bench.kernel_work(counts, fwd)
     assert fp32 == 2.0 * (1000 * 28 + 400 * (29 + 15 * ns) + 100 * (10 + 6 * nc + 3))
