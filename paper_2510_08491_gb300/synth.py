@@ -363,7 +363,7 @@ class Workload:
 
 
 def workload(name: str, seed: int = 0) -> Workload:
-    """The five benchmark workloads, by name (all seeded, synthetic)."""
+    """The benchmark workloads (WORKLOADS) and their profiler cases, by name (all seeded, synthetic)."""
     if name == "tiny64_128px":
         sc = make_scene(64, seed, center_half=1.0, n_sigma=8, omega0=5.0, color="const")
         cam = look_at_camera((0.0, 0.0, 4.0), (0, 0, 0), 128, 128)
@@ -375,6 +375,18 @@ def workload(name: str, seed: int = 0) -> Workload:
         # the first view of the 100k / four-view workload, for profiler captures
         wl = workload("fwd100k_1080p_4view", seed)
         return Workload(name, wl.scene, wl.cameras[:1], 16)
+    if name == "prof100k_540p_1view":
+        # the 100k-primitive scene seen by one ring view at a quarter of the 1080p
+        # pixels, for full-set profiler captures of a small case
+        wl = workload("fwd100k_1080p_4view", seed)
+        return Workload(name, wl.scene, ring_cameras(1, 8.0, 960, 540), 16)
+    if name == "batch100k_16view_quarter":
+        # the batched workload's primitive (N_sigma = 32, N_c = 64, BF16) at 100k
+        # primitives, its 16 view sizes at a quarter of the pixels, for captures
+        sc = make_scene(100_000, seed, center_half=3.0, n_sigma=32, omega0=5.0, color="mlp", n_c=64)
+        g = np.random.Generator(np.random.PCG64(seed + 7))
+        res = [(w // 2, h // 2) for (w, h) in (RESOLUTIONS[i] for i in g.integers(0, 4, size=16))]
+        return Workload(name, sc.to_bf16(), fibonacci_cameras(16, 10.0, res), 16)
     if name == "diff300k_720p":
         sc = make_scene(300_000, seed, center_half=3.0, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
         return Workload(name, sc, ring_cameras(1, 8.0, 1280, 720), 16, target_scene=perturb(sc, seed + 11, 0.01))
@@ -420,3 +432,5 @@ def workload(name: str, seed: int = 0) -> Workload:
 
 WORKLOADS = ("tiny64_128px", "fwd100k_1080p_4view", "diff300k_720p", "thin50k_1080p",
              "batch500k_16view", "fps100k_800px_sh", "dyn100k_800px_8t")
+# smaller cases of the same scenes for profiler captures
+PROFILE_WORKLOADS = ("prof100k_1080p_1view", "prof100k_540p_1view", "batch100k_16view_quarter")
