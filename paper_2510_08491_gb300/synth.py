@@ -401,6 +401,10 @@ def workload(name: str, seed: int = 0) -> Workload:
         g = np.random.Generator(np.random.PCG64(seed + 7))
         res = [RESOLUTIONS[i] for i in g.integers(0, 4, size=16)]
         return Workload(name, sc.to_bf16(), fibonacci_cameras(16, 10.0, res), 16)
+    if name == "fps100k_800px_sh_1view":
+        # the first view of the speed-protocol workload, for full-set profiler captures
+        wl = workload("fps100k_800px_sh", seed)
+        return Workload(name, wl.scene, wl.cameras[:1], 16)
     if name in ("fps100k_800px_sh", "dyn100k_800px_8t"):
         # The speed protocol of App. A (Integration Cost): 100k random primitives in a
         # volume, the primitive of Sec. 3.3 (Implementation Details: N_sigma = 8, w0 = 30,
@@ -433,4 +437,5 @@ def workload(name: str, seed: int = 0) -> Workload:
 WORKLOADS = ("tiny64_128px", "fwd100k_1080p_4view", "diff300k_720p", "thin50k_1080p",
              "batch500k_16view", "fps100k_800px_sh", "dyn100k_800px_8t")
 # smaller cases of the same scenes for profiler captures
-PROFILE_WORKLOADS = ("prof100k_1080p_1view", "prof100k_540p_1view", "batch100k_16view_quarter")
+PROFILE_WORKLOADS = ("prof100k_1080p_1view", "prof100k_540p_1view", "batch100k_16view_quarter",
+                     "fps100k_800px_sh_1view")
