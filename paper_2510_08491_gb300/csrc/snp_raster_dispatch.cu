@@ -30,9 +30,9 @@ size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts, 
 int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts, bool dyn)
 {
     const int fmb = fwd_min_blocks(ts, nc_of(color_mode, n_c));
-    // (at 16-pixel tiles and N_c = 32 the 74 KB budget gives chunk 5: two CTAs of
-    // the three the kernel is built for then fit an SM, and that measured faster
-    // than chunk 4 at three, 22.3 against 23.2 ms at the four-view 1080p workload)
+    // (at 16-pixel tiles and N_c = 32 the 74 KB budget gives chunk 5, 73 KB, which
+    // still fits three CTAs per SM and measured faster than chunk 4: 22.3 against
+    // 23.2 ms at the four-view 1080p workload)
     const size_t fwd_budget = fmb == 4 ? 52 * 1024 : (fmb == 3 ? 74 * 1024 : 104 * 1024);
     // (the tensor-memory backward at N_c = 64 also holds its operand tiles: most of one SM)
     const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2
