@@ -313,7 +313,11 @@ static snp_status build_views(snp_context *ctx, const snp_camera *cams, int n_ca
             I[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) * id;
             I[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) * id;
             for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) V.Rti[3 * a + b] = I[a][b];
+                for (int b = 0; b < 3; ++b) {
+                    V.Rti[3 * a + b] = I[a][b];
+                    V.Rti_hi[3 * a + b] = (float)I[a][b];
+                    V.Rti_lo[3 * a + b] = (float)(I[a][b] - (double)V.Rti_hi[3 * a + b]);
+                }
         }
         t += (int64_t)V.tiles_x * V.tiles_y;
         p += (int64_t)c.width * c.height;

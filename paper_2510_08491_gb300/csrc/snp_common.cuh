@@ -61,10 +61,12 @@ struct View {
     int32_t tile_off;  // first global tile id of this view
     float time;        // timestamp xi_t (time-conditioned scenes)
     int64_t pix_off;   // first pixel of this view in the concatenated image
-    // Inverse of R_wc^T in FP64: the stored FP32 rotation is not exactly
-    // orthonormal, so the camera-frame centre used for the ray geometry is
-    // mu' = (R_wc^T)^-1 (c - eye), for which c - eye = R_wc^T mu' holds exactly.
+    // Inverse of R_wc^T (computed on the host in FP64): the stored FP32 rotation is
+    // not exactly orthonormal, so the camera-frame centre used for the ray geometry
+    // is mu' = (R_wc^T)^-1 (c - eye), for which c - eye = R_wc^T mu' holds exactly.
+    // Also as float hi + lo pairs for the float-float record set-up.
     double Rti[9];
+    float Rti_hi[9], Rti_lo[9];
 };
 
 // Field offsets of one primitive's network record (elements), see snp_net_layout.

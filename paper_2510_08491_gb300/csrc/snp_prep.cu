@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "snp_common.cuh"
+#include "snp_df.cuh"
 #include "snp_internal.h"
 
 namespace snp {
@@ -163,77 +164,105 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ geom,
     trect[gid] = tr;
     counts[gid] = cnt;
 
-    // Projection record: evaluated in FP64 from the float32 inputs and rounded once.
+    // Projection record: evaluated in float-float arithmetic (~2^-47 relative per
+    // operation, snp_df.cuh) from the float32 inputs and rounded once; the fields
+    // the grazing-ray evaluation needs exactly keep their hi + lo parts.
     float *r = rec + gid * kRecFloats;
-    const double sd[3] = {exp((double)ls[0]), exp((double)ls[1]), exp((double)ls[2])};
-    const double qd[4] = {q[0], q[1], q[2], q[3]};
-    const double iqn = 1.0 / sqrt(qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3]);
-    const double W = qd[0] * iqn, X = qd[1] * iqn, Y = qd[2] * iqn, Z = qd[3] * iqn;
-    const double Rq[3][3] = {
-        {1.0 - 2.0 * (Y * Y + Z * Z), 2.0 * (X * Y - W * Z), 2.0 * (X * Z + W * Y)},
-        {2.0 * (X * Y + W * Z), 1.0 - 2.0 * (X * X + Z * Z), 2.0 * (Y * Z - W * X)},
-        {2.0 * (X * Z - W * Y), 2.0 * (Y * Z + W * X), 1.0 - 2.0 * (X * X + Y * Y)}};
-    const double md = fmax(fmax(sd[0], sd[1]), sd[2]);
-    double Rw[3][3];
+    const f2 one = df_from(1.0f);
+    const f2 sd[3] = {df_exp(ls[0]), df_exp(ls[1]), df_exp(ls[2])};
+    f2 qd = df_two_prod(q[0], q[0]);
+    qd = df_add(qd, df_two_prod(q[1], q[1]));
+    qd = df_add(qd, df_two_prod(q[2], q[2]));
+    qd = df_add(qd, df_two_prod(q[3], q[3]));
+    const f2 iqn = df_rsqrt(qd);
+    const f2 W = df_mul_f(iqn, q[0]), X = df_mul_f(iqn, q[1]), Y = df_mul_f(iqn, q[2]), Z = df_mul_f(iqn, q[3]);
+    const f2 XX = df_mul(X, X), YY = df_mul(Y, Y), ZZ = df_mul(Z, Z);
+    const f2 XY = df_mul(X, Y), XZ = df_mul(X, Z), YZ = df_mul(Y, Z);
+    const f2 WX = df_mul(W, X), WY = df_mul(W, Y), WZ = df_mul(W, Z);
+    auto two = [](f2 a) { return f2{2.0f * a.hi, 2.0f * a.lo}; };
+    const f2 Rq[3][3] = {{df_sub(one, two(df_add(YY, ZZ))), two(df_sub(XY, WZ)), two(df_add(XZ, WY))},
+                         {two(df_add(XY, WZ)), df_sub(one, two(df_add(XX, ZZ))), two(df_sub(YZ, WX))},
+                         {two(df_sub(XZ, WY)), two(df_add(YZ, WX)), df_sub(one, two(df_add(XX, YY)))}};
+    int am = 0;  // m = max(s), ties to the lowest axis
+    if (sd[1].hi > sd[am].hi || (sd[1].hi == sd[am].hi && sd[1].lo > sd[am].lo)) am = 1;
+    if (sd[2].hi > sd[am].hi || (sd[2].hi == sd[am].hi && sd[2].lo > sd[am].lo)) am = 2;
+    const float md = sd[am].hi;
+    f2 dc[3];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Rw[k / 3][k % 3] = V.R[k];
-    const double dc[3] = {(double)c[0] - V.eye[0], (double)c[1] - V.eye[1], (double)c[2] - V.eye[2]};
-    double mud[3];  // mu' = (R_wc^T)^-1 (c - eye)
+    for (int a = 0; a < 3; ++a) dc[a] = df_two_sum(c[a], -V.eye[a]);  // c - eye, exactly
+    f2 mud[3];  // mu' = (R_wc^T)^-1 (c - eye)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) mud[a] = V.Rti[3 * a + 0] * dc[0] + V.Rti[3 * a + 1] * dc[1] + V.Rti[3 * a + 2] * dc[2];
-    const double rc[3] = {mud[0] / mud[2], mud[1] / mud[2], 1.0};
+    for (int a = 0; a < 3; ++a) {
+        f2 acc = df_mul(f2{V.Rti_hi[3 * a + 0], V.Rti_lo[3 * a + 0]}, dc[0]);
+        acc = df_add(acc, df_mul(f2{V.Rti_hi[3 * a + 1], V.Rti_lo[3 * a + 1]}, dc[1]));
+        mud[a] = df_add(acc, df_mul(f2{V.Rti_hi[3 * a + 2], V.Rti_lo[3 * a + 2]}, dc[2]));
+    }
+    const f2 rc[2] = {df_div(mud[0], mud[2]), df_div(mud[1], mud[2])};
     // G = diag(1/s) R_q^T R_wc^T:  G[a][b] = sum_j R_q[j][a] R_wc[b][j] / s_a
-    double G[3][3];
+    f2 G[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
+        const f2 is = df_div(one, sd[a]);
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            G[a][b] = (Rq[0][a] * Rw[b][0] + Rq[1][a] * Rw[b][1] + Rq[2][a] * Rw[b][2]) / sd[a];
-    double e[3];
+        for (int b = 0; b < 3; ++b) {
+            f2 t = df_mul_f(Rq[0][a], V.R[3 * b + 0]);
+            t = df_add(t, df_mul_f(Rq[1][a], V.R[3 * b + 1]));
+            t = df_add(t, df_mul_f(Rq[2][a], V.R[3 * b + 2]));
+            G[a][b] = df_mul(t, is);
+        }
+    }
+    f2 e[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
-        for (int b = 0; b < 3; ++b) r[kRecG + 3 * a + b] = (float)G[a][b];
-        e[a] = G[a][0] * rc[0] + G[a][1] * rc[1] + G[a][2];
-        r[kRecE + a] = (float)e[a];
+        for (int b = 0; b < 3; ++b) r[kRecG + 3 * a + b] = G[a][b].hi;
+        e[a] = df_add(df_add(df_mul(G[a][0], rc[0]), df_mul(G[a][1], rc[1])), G[a][2]);
+        r[kRecE + a] = e[a].hi;
         // R_wc^T r_c / m
-        r[kRecAc + a] = (float)((Rw[0][a] * rc[0] + Rw[1][a] * rc[1] + Rw[2][a]) / md);
-        r[kRecOcm + a] = (float)(-dc[a] / md);
+        const float rwc = fmaf(V.R[0 + a], rc[0].hi, fmaf(V.R[3 + a], rc[1].hi, V.R[6 + a]));
+        r[kRecAc + a] = rwc / md;
+        r[kRecOcm + a] = -(dc[a].hi + dc[a].lo) / md;
         r[kRecRgb + a] = rgb[a];
     }
-    const double mz = mud[2], mz2 = mz * mz;
-    r[kRecMz] = (float)mz;
-    r[kRecMz2] = (float)mz2;
+    const f2 mz = mud[2], mz2 = df_mul(mz, mz);
+    r[kRecMz] = mz.hi;
+    r[kRecMz2] = mz2.hi;
     // h^2 A = |e + f|^2 - mu_z^2 |e x f|^2 with f = G0 dx + G1 dy (columns 0, 1 of G),
     // dx = X / fx, dy = Y / fy: a quadratic in the pixel offset (X, Y)
     {
-        const double G0[3] = {G[0][0], G[1][0], G[2][0]}, G1[3] = {G[0][1], G[1][1], G[2][1]};
-        const double x0[3] = {e[1] * G0[2] - e[2] * G0[1], e[2] * G0[0] - e[0] * G0[2], e[0] * G0[1] - e[1] * G0[0]};
-        const double x1[3] = {e[1] * G1[2] - e[2] * G1[1], e[2] * G1[0] - e[0] * G1[2], e[0] * G1[1] - e[1] * G1[0]};
-        auto dot = [](const double *u, const double *v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
-        const double ifx = 1.0 / (double)V.fx, ify = 1.0 / (double)V.fy;
-        const double c[6] = {dot(e, e),
-                             2.0 * dot(e, G0) * ifx,
-                             2.0 * dot(e, G1) * ify,
-                             (dot(G0, G0) - mz2 * dot(x0, x0)) * ifx * ifx,
-                             2.0 * (dot(G0, G1) - mz2 * dot(x0, x1)) * ifx * ify,
-                             (dot(G1, G1) - mz2 * dot(x1, x1)) * ify * ify};
-        const int hi_slot[6] = {0, 1, 2, 3, 4, 5}, lo_slot[6] = {6, 7, 8, 9, 10, 11};
+        const f2 G0[3] = {G[0][0], G[1][0], G[2][0]}, G1[3] = {G[0][1], G[1][1], G[2][1]};
+        auto cross = [](const f2 *u, const f2 *w, f2 *o) {
+            o[0] = df_sub(df_mul(u[1], w[2]), df_mul(u[2], w[1]));
+            o[1] = df_sub(df_mul(u[2], w[0]), df_mul(u[0], w[2]));
+            o[2] = df_sub(df_mul(u[0], w[1]), df_mul(u[1], w[0]));
+        };
+        auto dot = [](const f2 *u, const f2 *w) {
+            return df_add(df_add(df_mul(u[0], w[0]), df_mul(u[1], w[1])), df_mul(u[2], w[2]));
+        };
+        f2 x0[3], x1[3];
+        cross(e, G0, x0);
+        cross(e, G1, x1);
+        const f2 ifx = df_div(one, df_from(V.fx)), ify = df_div(one, df_from(V.fy));
+        const f2 ifxx = df_mul(ifx, ifx), ifyy = df_mul(ify, ify), ifxy = df_mul(ifx, ify);
+        const f2 c[6] = {dot(e, e),
+                         two(df_mul(dot(e, G0), ifx)),
+                         two(df_mul(dot(e, G1), ify)),
+                         df_mul(df_sub(dot(G0, G0), df_mul(mz2, dot(x0, x0))), ifxx),
+                         two(df_mul(df_sub(dot(G0, G1), df_mul(mz2, dot(x0, x1))), ifxy)),
+                         df_mul(df_sub(dot(G1, G1), df_mul(mz2, dot(x1, x1))), ifyy)};
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const float hi = (float)c[k];
-            r[kRecQ + hi_slot[k]] = hi;
-            r[kRecQ + lo_slot[k]] = (float)(c[k] - (double)hi);
+            r[kRecQ + k] = c[k].hi;
+            r[kRecQ + 6 + k] = c[k].lo;
         }
     }
-    const double uc = (double)V.cx + (double)V.fx * rc[0];
-    const double vc = (double)V.cy + (double)V.fy * rc[1];
-    const float uhi = (float)uc, vhi = (float)vc;
-    r[kRecU + 0] = uhi;
-    r[kRecU + 1] = (float)(uc - (double)uhi);
-    r[kRecU + 2] = vhi;
-    r[kRecU + 3] = (float)(vc - (double)vhi);
-    r[kRecInvM] = (float)(1.0 / md);
+    const f2 uc = df_add(df_from(V.cx), df_mul_f(rc[0], V.fx));
+    const f2 vc = df_add(df_from(V.cy), df_mul_f(rc[1], V.fy));
+    r[kRecU + 0] = uc.hi;
+    r[kRecU + 1] = uc.lo;
+    r[kRecU + 2] = vc.hi;
+    r[kRecU + 3] = vc.lo;
+    r[kRecInvM] = 1.0f / md;
     r[kRecDepth] = mu[2];
     r[29] = r[30] = r[31] = 0.0f;
     r[44] = r[45] = r[46] = r[47] = 0.0f;
