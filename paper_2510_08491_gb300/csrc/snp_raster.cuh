@@ -237,10 +237,9 @@ struct Hit {
 // sqrt(h^2), so that is a relative error of ~0.5e-7 / h^2 in the chord and in
 // alpha_hat, and up to twice that in their derivatives: ~1e-5 at the edge of the
 // band (2e-4 at the worst).  Inside the band the value is exact to a few ulp.
-// The hit test only needs the sign, which FP32 already settles outside a much
-// narrower band (kSignBandH2, 15x the largest error seen).
+// The hit test only needs the sign, which it takes from the record's quadratic in
+// FP32 with a per-pair rounding-error margin (hit_test).
 constexpr float kBandH2 = 1e-2f;
-constexpr float kSignBandH2 = 3e-5f;
 
 // h^2 A of a pixel ray from the record's quadratic in the pixel offset
 // (X, Y) = (px + .5 - U_c, py + .5 - V_c), in float-float arithmetic: the
@@ -297,29 +296,29 @@ __device__ __forceinline__ bool intersect(const float *R, const CamK &ck, const 
     return true;
 }
 
-// Whether the ray enters the ellipsoid: the sign of h^2 A = |e+f|^2 - mu_z^2 |e x f|^2
-// (no reciprocal, no chord), re-evaluated in float-float arithmetic within
-// kSignBandH2 of the silhouette.  intersect() takes the float-float value in a
-// wider band; outside either band the FP32 sign is already certain, so the two
+// Whether the ray enters the ellipsoid: the sign of h^2 A = |e+f|^2 - mu_z^2 |e x f|^2,
+// from the record's quadratic in the pixel offset (X, Y) evaluated in FP32 with
+// the coefficients' hi parts.  S bounds the sum of the absolute values of its terms;
+// the FP32 result is within ~10 ulp of S of the exact value (coefficient rounding,
+// the rounding of X and Y, five fused operations), so where |Q| <= 16 2^-24 S the
+// sign is taken from the float-float value instead.  Outside that margin and
+// outside intersect()'s float-float band the FP32 signs are certain, so the two
 // functions always agree on hit or miss.
 __device__ __forceinline__ bool hit_test(const float *R, const CamK &ck, const PixRay &ry)
 {
-    const float4 g0 = reinterpret_cast<const float4 *>(R)[0];  // G00 G01 G02 G10
-    const float4 g1 = reinterpret_cast<const float4 *>(R)[1];  // G11 G12 G20 G21
-    const float4 g2 = reinterpret_cast<const float4 *>(R)[2];  // G22 ex ey ez
-    const float4 g3 = reinterpret_cast<const float4 *>(R)[3];  // mz mz2 Uhi Ulo
-    const float4 g4 = reinterpret_cast<const float4 *>(R)[4];  // Vhi Vlo ...
-    const float dx = ((ry.pxh - g3.z) - g3.w) * ck.ifx;
-    const float dy = ((ry.pyh - g4.x) - g4.y) * ck.ify;
-    const float3 f = make_float3(fmaf(g0.x, dx, g0.y * dy), fmaf(g0.w, dx, g1.x * dy), fmaf(g1.z, dx, g1.w * dy));
-    const float3 e = make_float3(g2.y, g2.z, g2.w);
-    const float3 dp = make_float3(e.x + f.x, e.y + f.y, e.z + f.z);
-    const float A = fmaf(dp.x, dp.x, fmaf(dp.y, dp.y, dp.z * dp.z));
-    const float3 w = make_float3(fmaf(e.y, f.z, -e.z * f.y), fmaf(e.z, f.x, -e.x * f.z), fmaf(e.x, f.y, -e.y * f.x));
-    const float W2 = fmaf(w.x, w.x, fmaf(w.y, w.y, w.z * w.z));
-    const float hA = fmaf(-g3.y, W2, A);
-    if (fabsf(hA) < kSignBandH2 * A) return h2A_df(R, ry.pxh, ry.pyh) > 0.0f;
-    return hA > 0.0f;
+    (void)ck;
+    const float4 q0 = reinterpret_cast<const float4 *>(R + kRecQ)[0];  // c0h c1h c2h c3h
+    const float4 q1 = reinterpret_cast<const float4 *>(R + kRecQ)[1];  // c4h c5h ..
+    const float4 g3 = reinterpret_cast<const float4 *>(R)[3];          // mz mz2 Uhi Ulo
+    const float4 g4 = reinterpret_cast<const float4 *>(R)[4];          // Vhi Vlo ..
+    const float X = (ry.pxh - g3.z) - g3.w;
+    const float Y = (ry.pyh - g4.x) - g4.y;
+    const float Q = fmaf(X, fmaf(q0.w, X, fmaf(q1.x, Y, q0.y)), fmaf(Y, fmaf(q1.y, Y, q0.z), q0.x));
+    const float ax = fabsf(X), ay = fabsf(Y);
+    const float S = fmaf(ax, fmaf(fabsf(q0.w), ax, fmaf(fabsf(q1.x), ay, fabsf(q0.y))),
+                         fmaf(ay, fmaf(fabsf(q1.y), ay, fabsf(q0.z)), fabsf(q0.x)));
+    if (fabsf(Q) <= 9.5367432e-07f * S) return h2A_df(R, ry.pxh, ry.pyh) > 0.0f;  // 16 * 2^-24
+    return Q > 0.0f;
 }
 
 // alpha_hat of one (ray, primitive) pair.  With u_mid = s a_c + (t / m) dg,
