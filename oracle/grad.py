@@ -27,8 +27,6 @@ from typing import Dict, Optional
 import numpy as np
 import torch
 
-from paper_2510_08491_gb300.synth import FEAT_DIM
-
 F64 = torch.float64
 
 
