@@ -152,7 +152,8 @@ typedef struct {
 
 /* Renderer configuration.
  *   tile_size     screen tile edge in pixels: 8, 16 or 32 (0 = 16)
- *   chunk         primitives staged per shared-memory batch (0 = library default)
+ *   chunk         primitives staged per shared-memory batch of the forward
+ *                 (0 = library default)
  *   integral_form SNP_FORM_STABLE: alpha_hat = Delta_t [b2 + sum_k w2_k cos(phi_k) sinc(theta_k)]
  *                 (Eq. 8 rewritten with sin A - sin B = 2 cos((A+B)/2) sin((A-B)/2), finite
  *                 as w0 W1_k . d -> 0); SNP_FORM_NAIVE: Eq. 8 literally, a difference of
@@ -168,6 +169,10 @@ typedef struct {
     float t_min;
     float bg[3];
     int32_t flags; /* SNP_FLAG_* bits */
+    /* primitives per shared-memory batch of the backward (0 = library default: the
+     * largest that fits the backward's own shared-memory budget, which differs from
+     * the forward's; a larger value is lowered to that default; < 0 is refused) */
+    int32_t bwd_chunk;
 } snp_config;
 
 /* snp_config.flags: record CUDA events around every stage on the call's stream so

@@ -55,7 +55,7 @@ class GradPtrs(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("chunk", C.c_int32), ("integral_form", C.c_int32),
-                ("t_min", C.c_float), ("bg", C.c_float * 3), ("flags", C.c_int32)]
+                ("t_min", C.c_float), ("bg", C.c_float * 3), ("flags", C.c_int32), ("bwd_chunk", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -163,9 +163,10 @@ def make_cameras(cams):
 
 
 def make_config(tile_size=16, chunk=0, form=FORM_STABLE, t_min=1e-4, bg=(0.0, 0.0, 0.0), timing=False,
-                length_queue=False, replay_color=False) -> Config:
+                length_queue=False, replay_color=False, bwd_chunk=0) -> Config:
     cfg = Config()
     cfg.tile_size, cfg.chunk, cfg.integral_form = int(tile_size), int(chunk), int(form)
+    cfg.bwd_chunk = int(bwd_chunk)
     cfg.flags = (FLAG_STAGE_TIMING if timing else 0) | (FLAG_LENGTH_QUEUE if length_queue else 0) | \
         (FLAG_REPLAY_COLOR if replay_color else 0)
     cfg.t_min = float(t_min)

@@ -548,6 +548,7 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
     if (c.integral_form != SNP_FORM_STABLE && c.integral_form != SNP_FORM_NAIVE)
         return fail(ctx, SNP_ERR_INVALID_ARG, "bad integral_form %d", c.integral_form);
     if (!(c.t_min >= 0.0f) || !(c.t_min < 1.0f)) return fail(ctx, SNP_ERR_INVALID_ARG, "t_min must be in [0, 1)");
+    if (c.chunk < 0 || c.bwd_chunk < 0) return fail(ctx, SNP_ERR_INVALID_ARG, "negative chunk");
     const int ts = c.tile_size;
     const int chunk =
         c.chunk > 0 ? c.chunk : raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts, desc->dynamic != 0);
@@ -759,7 +760,7 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
     a.g_view = (float *)ctx->g_view.p;
     a.g_h0 = (float *)ctx->g_h0.p;
     a.chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true, ctx->ts, desc->dynamic != 0);
-    if (ctx->cfg.chunk > 0 && ctx->cfg.chunk < a.chunk) a.chunk = ctx->cfg.chunk;
+    if (ctx->cfg.bwd_chunk > 0 && ctx->cfg.bwd_chunk < a.chunk) a.chunk = ctx->cfg.bwd_chunk;
     // test hook: SNP_TEST_STUCK_WAIT=1 makes the tensor-memory backward (N_c = 64) run
     // one bounded wait out, so that tests can check that it is reported
     // (SNP_ERR_TIMEOUT from snp_get_stats) and that the context stays usable

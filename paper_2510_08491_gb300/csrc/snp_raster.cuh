@@ -564,9 +564,9 @@ __device__ __forceinline__ void warp_color_pass(const float *Cb, const float4 *s
 //   W3 [3][NC]    dL/dWc3;  BC2 [NC] dL/dbc2;  AB3 [3] dL/dbc3.
 // a2 = Wc2 z1, dL/dz1 = Wc2^T dL/da2 and dL/dWc2 = sum_rays dL/da2 z1^T run on
 // the tensor cores; the last takes movmatrix transposes of the pass's register
-// fragments, with the 16 rays as the reduction dimension.  With TM (N_c = 64)
-// dL/dWc2 is not added to AW2: tcgen05.mma accumulates it in the entry's 64 x 64
-// TMEM accumulator (tp.d_tmem) over all of the entry's passes, and the flush reads
+// fragments, with the 16 rays as the reduction dimension.  With TM (N_c = 32, 64)
+// dL/dWc2 is not added to AW2: tcgen05.mma accumulates it in the entry's TMEM
+// accumulator (tp.d_tmem) over all of the entry's passes, and the chunk's end reads
 // it from there.  ncommit counts this warp's committed MMA groups.
 template <int NC, bool BF16, bool TM>
 __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float4 *s_ray, const uint16_t *list,
@@ -575,7 +575,7 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
                                                     float *AW2, float *W3, float *BC2, float *AB3,
                                                     const TmemPass &tp, int &ncommit)
 {
-    static_assert(!TM || NC == 64, "the TMEM accumulation is built for N_c = 64");
+    static_assert(!TM || NC == 32 || NC == 64, "the TMEM accumulation is built for N_c = 32 and 64");
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float4 *C1 = reinterpret_cast<const float4 *>(Cb + cb_C1(NC));
     const float *B2 = Cb + cb_B2(NC);
@@ -686,11 +686,20 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
     if constexpr (TM) {
         // The 5th-generation tensor core accumulates the entry's dL/dWc2 in TMEM
         // across all of its passes: this warp writes its pass's operands (A = dL/da2^T,
-        // 64 output units x 16 rays; B^T = z1^T, 64 input units x 16 rays; bf16 hi and
-        // lo each) to its shared-memory tiles in the K-major core-matrix layout and
-        // lane 0 issues the three split products.  After the transposes, lane (g, t)
-        // holds unit 8 b + g of block b at rays 2t, 2t + 1 (+8 for the second half),
-        // one 4-byte pair of the layout.
+        // output units x 16 rays; B^T = z1^T, input units x 16 rays; bf16 hi and lo
+        // each) to its shared-memory tiles in the K-major core-matrix layout (8-row
+        // groups kUmmaSbo apart, the two 8-ray halves kUmmaLbo apart) and lane 0
+        // issues the split products.  After the transposes, lane (g, t) holds unit
+        // 8 b + g of block b at rays 2t, 2t + 1 (+8 for the second half), one 4-byte
+        // pair of the layout.
+        //   N_c = 64: A hi at 0, A lo at 2048, B hi at 4096, B lo at 6144 (64 rows
+        //             each); D (64 x 64) += A_lo B_hi + A_hi B_lo + A_hi B_hi.
+        //   N_c = 32: one 64-row A whose 8-row group 2 b holds the hi half of unit
+        //             block b and group 2 b + 1 its lo half (at 0), B hi at 2048, B lo
+        //             at 3072 (32 rows each); D (64 x 32) += A B_hi + A B_lo, so that
+        //             D row 16 j + r (r < 8) is hi x (hi + lo) of unit 8 j + r and row
+        //             16 j + 8 + r is lo x (hi + lo) of the same unit.
+        constexpr int kBh = NC == 64 ? 4096 : 2048, kBl = NC == 64 ? 6144 : 3072;
         if (ncommit > 0 && !mbar_wait_bounded(tp.bar, (uint32_t)((ncommit - 1) & 1))) *tp.wait_status = 1;
         char *const st = reinterpret_cast<char *>(tp.stage_ptr);
         const int within = g * 16 + 4 * t;
@@ -699,8 +708,8 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int off = nk * (int)kUmmaSbo + h * (int)kUmmaLbo + within;
-                *reinterpret_cast<uint32_t *>(st + 4096 + off) = tzh[nk][h];
-                *reinterpret_cast<uint32_t *>(st + 6144 + off) = tzl[nk][h];
+                *reinterpret_cast<uint32_t *>(st + kBh + off) = tzh[nk][h];
+                *reinterpret_cast<uint32_t *>(st + kBl + off) = tzl[nk][h];
             }
         }
 #pragma unroll
@@ -712,9 +721,11 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
                                     movm_trans(gl[mn][3])};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int off = (2 * mn + (i & 1)) * (int)kUmmaSbo + (i >> 1) * (int)kUmmaLbo + within;
-                *reinterpret_cast<uint32_t *>(st + off) = th[i];
-                *reinterpret_cast<uint32_t *>(st + 2048 + off) = tl[i];
+                const int b = 2 * mn + (i & 1), kh = (i >> 1) * (int)kUmmaLbo + within;
+                const int oh = (NC == 64 ? b : 2 * b) * (int)kUmmaSbo + kh;
+                const int ol = NC == 64 ? 2048 + oh : oh + (int)kUmmaSbo;
+                *reinterpret_cast<uint32_t *>(st + oh) = th[i];
+                *reinterpret_cast<uint32_t *>(st + ol) = tl[i];
             }
         }
         fence_proxy_async_smem();
@@ -736,9 +747,14 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
             *started = 1;
             const uint32_t sa = tp.stage;
             constexpr uint32_t idesc = umma_idesc_bf16(64, NC);
-            umma_bf16(tp.d_tmem, umma_smem_desc(sa + 2048), umma_smem_desc(sa + 4096), idesc, acc_in);
-            umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + 6144), idesc, true);
-            umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + 4096), idesc, true);
+            if constexpr (NC == 64) {
+                umma_bf16(tp.d_tmem, umma_smem_desc(sa + 2048), umma_smem_desc(sa + kBh), idesc, acc_in);
+                umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + kBl), idesc, true);
+                umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + kBh), idesc, true);
+            } else {
+                umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + kBh), idesc, acc_in);
+                umma_bf16(tp.d_tmem, umma_smem_desc(sa), umma_smem_desc(sa + kBl), idesc, true);
+            }
             umma_commit(tp.bar);
             tc_fence_before_sync();
             __threadfence_block();

@@ -50,13 +50,14 @@ __host__ __device__ constexpr int net_stride(int ns, int nc, bool sh, bool dyn)
 //   [0, stride)             the primitive's network-gradient record in the caller's
 //                           layout (snp_net_layout).  W1 and b1 hold gradients w.r.t.
 //                           the staged rows w0 W1, w0 b1, and Wc2 is in mma fragment
-//                           order (see warp_color_bwd_pass), until the flush (at
-//                           N_c = 64 it is accumulated in tensor memory instead and
-//                           written here row-major just before the flush);
+//                           order (see warp_color_bwd_pass), until the flush;
 //   [stride, +kGvFloats)    the per-(view, primitive) geometry gradient record;
 //   [.., +n_c)              dL/dh0 (the folded first-layer bias).
-// The flush adds the three blocks to global memory with bulk asynchronous
-// reductions (cp.reduce.async.bulk ... add.f32), one per block.
+// With the tensor-memory path (bwd_tmem) dL/dWc2 accumulates in TMEM, and the
+// record has no Wc2 block: the fields after it, and the two blocks after the
+// record, sit N_c^2 floats lower (the caller's layout has Wc2 followed only by
+// bc2, Wc3 and bc3).  The flush adds the blocks to global memory with bulk
+// asynchronous reductions (cp.reduce.async.bulk ... add.f32).
 __host__ __device__ constexpr int acc_stride(int stride, int nc) { return stride + kGvFloats + nc; }
 
 __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, uint32_t bytes)
@@ -75,9 +76,11 @@ __device__ __forceinline__ void bulk_reduce_add(float *gdst, const float *ssrc, 
 // skipped.  All threads call it.  The reads of the bulk adds complete in the
 // background: the kernel waits for them (thread 0) and clears the accumulators
 // only in the next chunk, before its first accumulation.
+// With TM, land holds the entries' dL/dWc2 blocks (row-major, N_c^2 floats each,
+// written from tensor memory) and the accumulators are in the compact layout.
 template <int NC, int NT, bool TM>
 __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int vg, const uint32_t *s_gid, int cnt,
-                                            const int *na, int64_t vn, int tid, int nt, float xi)
+                                            const int *na, int64_t vn, int tid, int nt, float xi, const float *land)
 {
     const int ns = a.n_sigma;
     if constexpr (NC > 0 && !TM) {  // (TM: the blocks came out of tensor memory row-major)
@@ -128,16 +131,29 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
         if (r < 3 * ns) A[a.off_W1 + r] *= a.omega0;
         else A[a.off_b1 + (r - 3 * ns)] *= a.omega0;
     }
+    // every thread's shared-memory writes become visible to the bulk copies' async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        constexpr int sw = TM ? NC * NC : 0;
+        const int gvo = a.stride - sw;  // the geometry record's offset in the accumulator
         for (int e = 0; e < cnt; ++e) {
             if (na[e] == 0) continue;
             const int64_t gid = s_gid[e], prim = gid - vn;
             const float *A = acc + e * vg;
-            if (a.g_net) bulk_reduce_add(a.g_net + prim * a.stride, A, (uint32_t)a.stride * 4u);
-            bulk_reduce_add(a.g_view + gid * kGvFloats, A + a.stride, kGvFloats * 4u);
-            if constexpr (NC > 0) bulk_reduce_add(a.g_h0 + prim * NC, A + a.stride + kGvFloats, NC * 4u);
+            if (a.g_net) {
+                float *G = a.g_net + prim * a.stride;
+                if constexpr (TM) {
+                    const int w2 = a.off_Wc2, tail = a.stride - w2 - NC * NC;
+                    bulk_reduce_add(G, A, (uint32_t)w2 * 4u);
+                    bulk_reduce_add(G + w2, land + e * NC * NC, (uint32_t)(NC * NC) * 4u);
+                    bulk_reduce_add(G + w2 + NC * NC, A + w2, (uint32_t)tail * 4u);
+                } else {
+                    bulk_reduce_add(G, A, (uint32_t)a.stride * 4u);
+                }
+            }
+            bulk_reduce_add(a.g_view + gid * kGvFloats, A + gvo, kGvFloats * 4u);
+            if constexpr (NC > 0) bulk_reduce_add(a.g_h0 + prim * NC, A + gvo + kGvFloats, NC * 4u);
         }
         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
     }
@@ -151,7 +167,8 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
 template <int NC, int FORM>
 __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *R, const float *D, int ns,
                                               const CamK &ck,
-                                              const PixRay &ry, bool contrib, float g_ah, float3 g_c, float *A)
+                                              const PixRay &ry, bool contrib, float g_ah, float3 g_c, float *A,
+                                              int gvo)
 {
     const unsigned lane = lane_id();
     Hit h;
@@ -328,7 +345,7 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
         for (int q = 25; q < 32; ++q) vv[q] = 0.0f;
         const float r = warp_reduce_scatter32(vv);
         if (r != 0.0f) {
-            if (lane < (unsigned)kGvFloats) atomicAdd(A + a.stride + lane, r);
+            if (lane < (unsigned)kGvFloats) atomicAdd(A + gvo + lane, r);
             else if (lane == 24) atomicAdd(A + a.off_b2, r);
         }
     }
@@ -336,16 +353,32 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
 }
 
 // Whether the backward accumulates dL/dWc2 in tensor memory (tcgen05; N_c = 64 on
-// 256-thread tiles, which run one CTA per SM) instead of shared-memory atomics.
+// 256-thread tiles) instead of shared-memory atomics.  The N_c = 32 form below
+// (warp_color_bwd_pass) is built and correct but measured slower than the atomics
+// there: its operand tiles cost a chunk entry at two CTAs per SM, and the short
+// passes leave the per-pass MMA issue exposed.
 __host__ __device__ constexpr bool bwd_tmem(int ts, int nc) { return nc == 64 && ts >= 16; }
-constexpr int kTmemStageBytes = 8192;  // per warp: A hi, A lo, B hi, B lo tiles of 64 x 16 bf16
+// Per-warp operand tiles of the tensor-memory path (bytes).  N_c = 64: A hi, A lo,
+// B hi, B lo, each 64 x 16 bf16.  N_c = 32: A = the hi and lo halves of dL/da2^T
+// stacked into one 64 x 16 tile, B hi, B lo (32 x 16 each).
+__host__ __device__ constexpr int tmem_stage_bytes(int nc) { return nc == 64 ? 8192 : 4096; }
+// With the tensor-memory path the per-entry accumulator has no Wc2 block (the
+// record's fields after it move down by N_c^2 floats): at the chunk's end the
+// accumulators leave tensor memory into the warps' operand tiles, which are free
+// then, one N_c x N_c block per entry.  So a chunk holds at most this many entries.
+__host__ __device__ constexpr int tmem_max_chunk(int nt, int nc)
+{
+    return (nt / 32) * tmem_stage_bytes(nc) / (nc * nc * 4);
+}
+__host__ __device__ constexpr int tmem_wc2_floats(int ts, int nc) { return bwd_tmem(ts, nc) ? nc * nc : 0; }
 
 template <int TS>
 __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk, int stride)
 {
     constexpr int NPIX = TileCfg<TS>::NPIX;
-    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(stride, nc)) * 4 + (size_t)NPIX * (5 * 4 + 2);
-    const size_t stage = bwd_tmem(TS, nc) ? (size_t)(TileCfg<TS>::NT / 32) * kTmemStageBytes + 128 : 0;
+    const size_t per_entry = (size_t)(entry_stride(ns, nc) + acc_stride(stride, nc) - tmem_wc2_floats(TS, nc)) * 4 +
+                             (size_t)NPIX * (5 * 4 + 2);
+    const size_t stage = bwd_tmem(TS, nc) ? (size_t)(TileCfg<TS>::NT / 32) * tmem_stage_bytes(nc) + 128 : 0;
     return NPIX * (32 + 12) + (size_t)chunk * per_entry + stage;
 }
 
@@ -359,7 +392,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     const int CH = a.chunk;
     const int ns = a.n_sigma;
     const int es = entry_stride(ns, NC);
-    const int vg = acc_stride(a.stride, NC);
+    constexpr int SW = tmem_wc2_floats(TS, NC);  // Wc2 floats not in the accumulator (TMEM path)
+    const int vg = acc_stride(a.stride, NC) - SW;
+    const int gvo = a.stride - SW;  // offset of the geometry record in an accumulator
     float4 *s_ray = smem4;                                 // [2 NPIX] pixel rays
     float *s_dl = reinterpret_cast<float *>(smem4 + 2 * NPIX);  // [3][NPIX] dL/dC of the tile's pixels
     float *sm = s_dl + 3 * NPIX;                           // [CH][es] staged entries
@@ -394,9 +429,11 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     // the forward's per-pair store: (colour, alpha_hat) with a colour network, else alpha_hat
     const bool has_store = NC > 0 ? a.colstore != nullptr : a.ahstore != nullptr;
     for (int q = tid; q < CH * vg; q += NT) acc[q] = 0.0f;
-    // TM: TMEM columns for the chunk's 64 x 64 accumulators (entry e at columns 64 e)
-    uint32_t tm_cols = 64;
-    while ((int)tm_cols < 64 * CH) tm_cols <<= 1;
+    // TM: TMEM columns for the chunk's accumulators (entry e at columns N_c e; 64
+    // lanes by N_c columns at N_c = 64, 64 lanes by 32 columns at N_c = 32, where
+    // the hi and lo halves of dL/da2 are stacked along M)
+    uint32_t tm_cols = 32;
+    while ((int)tm_cols < (NC > 0 ? NC : 1) * CH) tm_cols <<= 1;
     int ncommit = 0;
     if constexpr (TM) {
         if (tid < NT / 32) mbar_init(&s_tmbar[tid], 1);
@@ -659,10 +696,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                             float *A = acc + ec * vg;
                             TmemPass tp{};
                             if constexpr (TM) {
-                                tp.stage_ptr = s_stage + wid * kTmemStageBytes;
+                                tp.stage_ptr = s_stage + wid * tmem_stage_bytes(NC);
                                 tp.stage = cvta_smem(tp.stage_ptr);
                                 tp.bar = &s_tmbar[wid];
-                                tp.d_tmem = s_tmaddr + 64u * (uint32_t)ec;
+                                tp.d_tmem = s_tmaddr + (uint32_t)NC * (uint32_t)ec;
                                 tp.started = &s_tmstart[ec];
                                 tp.lock = &s_tmlock;
                                 tp.wait_status = a.wait_status;
@@ -671,9 +708,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                                                               s_al + ec * NPIX, (it - s_pp[ec]) * 16, s_na[ec],
                                                               s_w + ec * NPIX, s_dl, NPIX,
                                                               reinterpret_cast<const float *>(s_cs + ec * NPIX), 4,
-                                                              1, A + a.off_Wc1, A + a.stride + kGvFloats,
-                                                              A + a.off_Wc2, A + a.off_Wc3, A + a.off_bc2,
-                                                              A + a.off_bc3, tp, ncommit);
+                                                              1, A + a.off_Wc1, A + gvo + kGvFloats,
+                                                              A + a.off_Wc2, A + a.off_Wc3 - SW,
+                                                              A + a.off_bc2 - SW, A + a.off_bc3 - SW, tp, ncommit);
                         }
                     } else {
                         const int q = it - np;
@@ -690,7 +727,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                             g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
                         }
                         pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_cs[e * NPIX + pix].w, g_c,
-                                                acc + e * vg);
+                                                acc + e * vg, gvo);
                     }
                     int nx = 0;
                     if (lane == 0) nx = atomicAdd(&s_item6, 1) + NT / 32;
@@ -704,29 +741,55 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 tc_fence_before_sync();
             }
             __syncthreads();
+            float *land = reinterpret_cast<float *>(s_stage);  // TM: entry e's dL/dWc2 at e N_c^2
             if constexpr (TM) {
-                // dL/dWc2 of every composited entry from TMEM into its accumulator block,
-                // row-major (the layout the flush reduces): warp w reads TMEM lanes
-                // 32 (w % 4) .. + 15, i.e. rows 16 (w % 4) .. + 15, columns 32 (w / 4) .. + 31
+                // dL/dWc2 of every composited entry from TMEM into the (now idle) operand
+                // tiles, row-major.  The M = 64 accumulator keeps rows 16 j .. 16 j + 15 in
+                // TMEM lanes 32 j .. 32 j + 15, which only warps w with w % 4 = j can read.
                 tc_fence_after_sync();
-                const int q = wid & 3, half = wid >> 2;
-                for (int e = 0; e < cnt; ++e) {
-                    if (s_na[e] == 0) continue;
-                    uint32_t r[32];
-                    tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)e + 32u * (uint32_t)half, r);
-                    if (lane < 16) {
-                        float4 *dst = reinterpret_cast<float4 *>(acc + e * vg + a.off_Wc2 + (16 * q + (int)lane) * 64 +
-                                                                 32 * half);
+                const int q = wid & 3;
+                if constexpr (NC == 64) {
+                    // warp w: rows 16 (w % 4) .. + 15, columns 32 (w / 4) .. + 31
+                    const int half = wid >> 2;
+                    for (int e = 0; e < cnt; ++e) {
+                        if (s_na[e] == 0) continue;
+                        uint32_t r[32];
+                        tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)e + 32u * (uint32_t)half, r);
+                        if (lane < 16) {
+                            float4 *dst = reinterpret_cast<float4 *>(land + e * NC * NC + (16 * q + (int)lane) * 64 +
+                                                                     32 * half);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                            for (int j = 0; j < 8; ++j)
+                                dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                     __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                        }
+                    }
+                } else {
+                    // N_c = 32: lane l < 8 of warp w holds output unit 8 (w % 4) + l from the
+                    // hi half of dL/da2, lane l + 8 the same unit from the lo half; their sum
+                    // is the row.  Warps w and w + 4 take alternate entries.
+                    for (int e = wid >> 2; e < cnt; e += 2) {
+                        if (s_na[e] == 0) continue;
+                        uint32_t r[32];
+                        tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 32u * (uint32_t)e, r);
+                        float v[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            v[j] = __uint_as_float(r[j]);
+                            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 8);
+                        }
+                        if (lane < 8) {
+                            float4 *dst = reinterpret_cast<float4 *>(land + e * NC * NC + (8 * q + (int)lane) * 32);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                        }
                     }
                 }
                 tc_fence_before_sync();
                 __syncthreads();
             }
-            flush_chunk<NC, NT, TM>(a, acc, vg, cg, cnt, s_na, vn, tid, NT, V.time);
+            flush_chunk<NC, NT, TM>(a, acc, vg, cg, cnt, s_na, vn, tid, NT, V.time, land);
             clear_n = cnt * vg / 4;
         }
         __syncthreads();

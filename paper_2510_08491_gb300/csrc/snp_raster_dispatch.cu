@@ -39,6 +39,8 @@ int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, in
                                   ? 110 * 1024
                                   : (bwd_tmem(ts, nc_of(color_mode, n_c)) ? 220 * 1024 : 200 * 1024);
     int ch = backward ? 8 : 32;
+    if (backward && bwd_tmem(ts, nc_of(color_mode, n_c)))
+        ch = tmem_max_chunk(ts == 8 ? 64 : 256, nc_of(color_mode, n_c));
     if (backward) {
         while (ch > 1 && raster_bwd_smem(color_mode, n_c, n_sigma, ch, ts, dyn) > bwd_budget) --ch;
     } else {

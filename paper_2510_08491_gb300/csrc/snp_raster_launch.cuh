@@ -31,12 +31,35 @@ static void allow_smem(K kern)
 }
 
 template <typename K>
-static int persistent_grid(K kern, int threads, size_t smem, int64_t n_tiles)
+static int persistent_grid(K kern, int threads, size_t smem, int64_t n_tiles, int tmem_per_sm = 0)
 {
     int dev = 0, sms = 1, nb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    if (tmem_per_sm > 0) {
+        // The occupancy query answers one CTA per SM for any kernel that allocates
+        // tensor memory, whatever its registers and shared memory; the CTAs of this
+        // one allocate a fixed share of the SM's columns (tmem_per_sm CTAs fit), so
+        // count the resident CTAs from registers, shared memory and threads instead.
+        cudaFuncAttributes fa{};
+        int regs_sm = 65536, smem_sm = 0, resv = 0, thr_sm = 2048, blk_sm = 32;
+        cudaFuncGetAttributes(&fa, kern);
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+        const int warps = (threads + 31) / 32;
+        const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in 256s
+        const size_t smem_blk = smem + fa.sharedSizeBytes + (size_t)resv;
+        nb = tmem_per_sm;
+        if (regs_warp > 0 && regs_sm / (warps * regs_warp) < nb) nb = regs_sm / (warps * regs_warp);
+        if (smem_blk > 0 && (int)((size_t)smem_sm / smem_blk) < nb) nb = (int)((size_t)smem_sm / smem_blk);
+        if (thr_sm / threads < nb) nb = thr_sm / threads;
+        if (blk_sm < nb) nb = blk_sm;
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    }
     int64_t g = (int64_t)(nb > 0 ? nb : 1) * sms;
     if (g > n_tiles) g = n_tiles;
     return (int)(g > 0 ? g : 1);
@@ -60,14 +83,24 @@ template <int TS, int NC, int FORM, bool BF16>
 static snp_status run_bwd(const RasterArgs &a, cudaStream_t st)
 {
     const size_t smem = bwd_smem_bytes<TS>(NC, a.n_sigma, a.chunk, a.stride);
-    // (the tensor-memory accumulators of a chunk take 64 columns per entry, at most 512)
+    // (with the tensor-memory accumulators a chunk's entries land in the warps'
+    // operand tiles at its end: at most tmem_max_chunk of them)
     if (smem > kSmemMax || a.chunk < 1 || a.chunk > 32 || a.chunk * (TS * TS / 32) > kMaskWords / 2 ||
-        (bwd_tmem(TS, NC) && a.chunk > 8) || a.stride != net_stride(a.n_sigma, NC, a.off_sh >= 0, a.off_wt >= 0))
+        (bwd_tmem(TS, NC) && a.chunk > tmem_max_chunk(TileCfg<TS>::NT, NC)) ||
+        a.stride != net_stride(a.n_sigma, NC, a.off_sh >= 0, a.off_wt >= 0))
         return SNP_ERR_INVALID_ARG;
     if (a.n_tiles <= 0) return SNP_OK;
     auto kern = k_raster_bwd<TS, NC, FORM, BF16>;
     allow_smem(kern);
-    const int grid = persistent_grid(kern, TileCfg<TS>::NT, smem, a.n_tiles);
+    // A CTA of the tensor-memory path allocates N_c x chunk columns (rounded up to a
+    // power of two, at least 32) of the SM's 512: no more CTAs per SM than fit.
+    int tm_per_sm = 0;
+    if (bwd_tmem(TS, NC)) {
+        int cols = 32;
+        while (cols < NC * a.chunk) cols <<= 1;
+        tm_per_sm = 512 / cols;
+    }
+    const int grid = persistent_grid(kern, TileCfg<TS>::NT, smem, a.n_tiles, tm_per_sm);
     kern<<<grid, TileCfg<TS>::NT, smem, st>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SNP_OK : SNP_ERR_CUDA;

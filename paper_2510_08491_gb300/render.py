@@ -343,7 +343,7 @@ class Renderer:
                 cache = {}
         if key in cache:
             best = L.make_config(tile_size=cache[key]["tile_size"], chunk=cache[key]["chunk"], form=cfg.integral_form,
-                                 t_min=cfg.t_min, bg=tuple(cfg.bg))
+                                 t_min=cfg.t_min, bg=tuple(cfg.bg), bwd_chunk=cfg.bwd_chunk)
             best.flags = cfg.flags
             return best
         best = L.Config()

@@ -160,6 +160,28 @@ def test_mlp64_ns32_bf16(R, oracle_lib):
     _check(g, gref, sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
 
 
+@pytest.mark.parametrize("bwd_chunk", [1, 3, 0])
+def test_mlp64_backward_chunk_is_set_apart_from_the_forwards(R, oracle_lib, bwd_chunk):
+    """The backward's chunk is its own setting (0: the largest that fits, 4 entries
+    at N_c = 64 with the tensor-memory dL/dWc2), not bounded by the forward's: with
+    the forward at chunk 2, backward chunks of 1, 3 and the default all match the
+    oracle.  A negative chunk is refused."""
+    from paper_2510_08491_gb300 import _lib as L
+    O = oracle_lib
+    sc = synth.make_scene(900, seed=18, center_half=1.5, n_sigma=32, omega0=5.0, color="mlp", n_c=64).to_bf16()
+    cams = [synth.look_at_camera((0.0, 0.3, 6.0), (0, 0, 0), 72, 40),
+            synth.look_at_camera((4.0, 1.0, 4.0), (0, 0, 0), 40, 56)]
+    dLv = _dl(O, sc, cams, 6)
+    g = _gpu_grads_cfg(R, sc, cams, np.concatenate(dLv), chunk=2, bwd_chunk=bwd_chunk)
+    _check(g, _oracle_grads(O, sc, cams, dLv),
+           sc.fields()[:3] + ["W1", "b1", "w2", "b2", "feat", "Wc1", "bc1", "Wc2", "bc2", "Wc3", "bc3"])
+    if bwd_chunk == 0:
+        from paper_2510_08491_gb300.render import pack_scene
+        with pytest.raises(L.SnpError) as ei:
+            R.forward(pack_scene(sc), cams, L.make_config(bwd_chunk=-1))
+        assert ei.value.status == L.SNP_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("replay", [False, True])
 def test_mlp_colour_store_and_replay(R, oracle_lib, replay):
     """The backward with the forward's colour store (default) and with the colours

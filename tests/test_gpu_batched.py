@@ -108,8 +108,9 @@ def test_graph_capture_matches_eager(R):
 
 def test_graph_step_matches_oracle_bf16_mlp64_16views(R, oracle_lib):
     """The batched workload's form checked against the FP64 oracle: 16 views of
-    uneven size, N_sigma = 32, N_c = 64, BF16 weights, 16-pixel tiles and chunk 3
-    (the configuration the benchmark's autotuner settles on), forward + backward
+    uneven size, N_sigma = 32, N_c = 64, BF16 weights, 16-pixel tiles, forward chunk 3
+    and the backward's default chunk (4 entries: the configuration the benchmark's
+    autotuner settles on, tensor-memory dL/dWc2), forward + backward
     captured in one CUDA graph and replayed twice.  dL/dC is set on three sampled
     tiles per view (zero on termination near-ties and colour-MLP ReLU kinks); the
     image there and every gradient group must meet the parity bars against the
