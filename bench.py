@@ -38,7 +38,18 @@ FP32_LANES_PER_SM = 128  # FP32 lanes per SM (4 sub-partitions x 32)
 MUFU_LANES_PER_SM = 16   # special-function lanes per SM (4 sub-partitions x 4)
 
 
+def chunks_used(ps, cfg):
+    """(forward chunk, backward chunk) a render with cfg stages for this packed scene."""
+    from paper_2510_08491_gb300 import _lib as L
+    d = ps.desc
+    f, b = L.default_chunks(int(d.n_sigma), int(d.color_mode), int(d.n_c), int(cfg.tile_size) or 16, bool(d.dynamic))
+    fc = int(cfg.chunk) if cfg.chunk > 0 else f
+    bc = min(b, int(cfg.bwd_chunk)) if cfg.bwd_chunk > 0 else b
+    return fc, bc
+
+
 # ----------------------------------------------------------------------------- work model
+
 def work_per_unit(n_sigma: int, n_c: int, colour_store: bool):
     """Arithmetic the raster kernels execute per unit, counted from their code, as
     (FP32 lane-ops, tensor-core multiply-adds, MUFU ops).  Units are the run's own
@@ -706,7 +717,8 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "primitives": sc.n, "views": len(cams),
                    "resolution": f"{cams[0].width}x{cams[0].height}", "n_sigma": sc.n_sigma,
                    "n_c": sc.n_c if sc.color == "mlp" else 0, "weights": sc.weight_dtype,
-                   "tile": int(cfg.tile_size), "chunk": int(cfg.chunk),
+                   "tile": int(cfg.tile_size), "chunk": chunks_used(ps, cfg)[0],
+                   "bwd_chunk": chunks_used(ps, cfg)[1],
                    "step": "forward+loss+backward" if target is not None else "forward+backward",
                    "graph": graph is not None, "autotuned": bool(args.autotune or batched),
                    "colour_store": not args.replay_color,
@@ -802,7 +814,8 @@ def batched_form(dev: int, steps: int, warmup: int):
     img = torch.empty((P, 3), device="cuda")
     ms_fwd = timed(lambda: r.forward(ps, cams, cfg, out=img), steps)
     out = {"workload": "batch500k_16view", "weights": "bf16", "views": len(cams), "pixels": P,
-           "tile": int(cfg.tile_size), "chunk": int(cfg.chunk), "graph": True, "autotuned": True,
+           "tile": int(cfg.tile_size), "chunk": chunks_used(ps, cfg)[0], "bwd_chunk": chunks_used(ps, cfg)[1],
+           "graph": True, "autotuned": True,
            "fwd_bwd_mpix_s": round(P / (ms * 1e-3) / 1e6, 3), "fwd_bwd_ms": round(ms, 3),
            "fwd_mpix_s": round(P / (ms_fwd * 1e-3) / 1e6, 3), "fwd_ms": round(ms_fwd, 3), "keys": int(K),
            "work": {"candidates": int(stats.n_candidates), "hits": int(stats.n_hits),

@@ -131,6 +131,14 @@ typedef struct {
 } snp_net_layout;
 snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out);
 
+/* The staging chunks (primitives per shared-memory batch) the library uses for
+ * this scene description at tile_size (8, 16 or 32; 0 = 16) when snp_config.chunk
+ * and snp_config.bwd_chunk are 0: *fwd_chunk for the forward (Sec. 3.2's per-tile
+ * blend) and *bwd_chunk for the backward, each the largest that fits its kernel's
+ * shared-memory budget.  Pure host function: SNP_ERR_INVALID_ARG for a NULL
+ * pointer or a bad description, SNP_ERR_UNSUPPORTED for a tile size not built. */
+snp_status snp_default_chunks(const snp_scene_desc *desc, int32_t tile_size, int32_t *fwd_chunk, int32_t *bwd_chunk);
+
 /* Scene parameters (device, caller-owned, read-only):
  *   geom  float32 [n][16]: centre xyz, log-scale xyz, quaternion (w, x, y, z; need
  *         not be normalised), constant rgb, 3 unused floats.

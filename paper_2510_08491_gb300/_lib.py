@@ -79,6 +79,7 @@ _lib = None
 
 _SIGS = {
     "snp_get_net_layout": [C.POINTER(SceneDesc), C.POINTER(NetLayout)],
+    "snp_default_chunks": [C.POINTER(SceneDesc), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "snp_create": [C.c_int32, C.POINTER(C.c_void_p)],
     "snp_destroy": [C.c_void_p],
     "snp_last_error": [C.c_void_p],
@@ -142,6 +143,16 @@ def net_layout(n_sigma: int, color_mode: int, n_c: int, dynamic: bool = False):
     if st != SNP_OK:
         raise SnpError(st, "bad scene description")
     return list(L.off), L.stride
+
+
+def default_chunks(n_sigma: int, color_mode: int, n_c: int, tile_size: int = 16, dynamic: bool = False):
+    """(forward chunk, backward chunk) the library picks for this scene shape (snp_default_chunks)."""
+    d = SceneDesc(0, n_sigma, color_mode, n_c if color_mode == COLOR_MLP else 0, F32, 1.0, int(bool(dynamic)))
+    f, b = C.c_int32(), C.c_int32()
+    st = lib().snp_default_chunks(C.byref(d), int(tile_size), C.byref(f), C.byref(b))
+    if st != SNP_OK:
+        raise SnpError(st, "bad scene description or tile size")
+    return f.value, b.value
 
 
 def make_camera(cam) -> Camera:

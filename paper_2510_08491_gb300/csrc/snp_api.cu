@@ -369,6 +369,19 @@ snp_status snp_get_net_layout(const snp_scene_desc *desc, snp_net_layout *out)
     return SNP_OK;
 }
 
+snp_status snp_default_chunks(const snp_scene_desc *desc, int32_t tile_size, int32_t *fwd_chunk, int32_t *bwd_chunk)
+{
+    if (!desc || !fwd_chunk || !bwd_chunk) return SNP_ERR_INVALID_ARG;
+    const snp_status s = check_desc(nullptr, desc);
+    if (s != SNP_OK) return s;
+    const int ts = tile_size == 0 ? 16 : tile_size;
+    if (ts != 8 && ts != 16 && ts != 32) return SNP_ERR_UNSUPPORTED;
+    const bool dyn = desc->dynamic != 0;
+    *fwd_chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, false, ts, dyn);
+    *bwd_chunk = raster_default_chunk(desc->color_mode, desc->n_c, desc->n_sigma, true, ts, dyn);
+    return SNP_OK;
+}
+
 snp_status snp_create(int32_t device, snp_context **out)
 {
     if (!out) return SNP_ERR_INVALID_ARG;

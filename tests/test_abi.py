@@ -11,7 +11,8 @@ from paper_2510_08491_gb300 import _lib as L
 def test_header_declares_the_boundary():
     syms = L.header_symbols()
     for s in ("snp_create", "snp_destroy", "snp_render_forward", "snp_render_backward", "snp_reserve",
-              "snp_debug_keys", "snp_get_stats", "snp_last_error", "snp_get_net_layout"):
+              "snp_debug_keys", "snp_get_stats", "snp_last_error", "snp_get_net_layout",
+              "snp_default_chunks"):
         assert s in syms
 
 
@@ -102,3 +103,23 @@ def test_argument_errors_are_reported_before_any_device_work():
     # misaligned key (8-byte) or value (4-byte) pointers are refused before the device is touched
     assert f(4100, 8192, 4, 32, null) == bad
     assert f(8192, 4098, 4, 32, null) == bad
+
+
+def test_default_chunks_follow_the_shared_memory_budgets():
+    """snp_default_chunks is host-only.  At N_sigma = 16, N_c = 32 both passes stage 5
+    entries (73 KB of the forward's three-CTA budget, 105 KB of the backward's
+    two-CTA budget).  At N_sigma = 32, N_c = 64 the tensor-memory backward stages 4:
+    the most its operand tiles can take at the chunk's end (4 x 16 KB), and 202 KB
+    of shared memory.  Bad arguments are refused."""
+    assert L.default_chunks(16, L.COLOR_MLP, 32) == (5, 5)
+    f64, b64 = L.default_chunks(32, L.COLOR_MLP, 64)
+    assert b64 == 4 and 1 <= f64 <= 32
+    f0, b0 = L.default_chunks(8, L.COLOR_SH, 0)
+    assert 1 <= f0 <= 32 and 1 <= b0 <= 8
+    assert L.default_chunks(16, L.COLOR_MLP, 32, tile_size=0) == (5, 5)
+    lib = L.lib()
+    d = L.SceneDesc(10, 16, L.COLOR_MLP, 32, 0, 30.0, 0)
+    f, b = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.snp_default_chunks(None, 16, ctypes.byref(f), ctypes.byref(b)) == L.SNP_ERR_INVALID_ARG
+    assert lib.snp_default_chunks(ctypes.byref(d), 16, None, ctypes.byref(b)) == L.SNP_ERR_INVALID_ARG
+    assert lib.snp_default_chunks(ctypes.byref(d), 12, ctypes.byref(f), ctypes.byref(b)) == L.SNP_ERR_UNSUPPORTED
