@@ -159,12 +159,45 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
     }
 }
 
+// N_sigma known at compile time (NS > 0): a pair's gradient values form one stream,
+// the 5 NS density values (dL/dW1_k row, dL/db1_k, dL/dw2_k for k = 0 .. NS-1), then
+// dL/db2, then the 22 slots of the geometry record, reduced across the warp 32 at a
+// time as they are produced: ceil((5 NS + 23) / 32) reduce-scatters per batch (2 at
+// N_sigma = 8, 6 at 32) instead of one per six density units plus one.  Put value
+// idx of the stream into its group's slot; a full group (or the last) is reduced
+// and each lane adds its sum to the accumulator A.  idx is a constant after
+// unrolling, so v stays in registers.
+template <int NS>
+__device__ __forceinline__ void pack_put(float (&v)[32], int idx, float x, const RasterArgs &a, float *A, int gvo)
+{
+    constexpr int kTotal = 5 * NS + 23;
+    v[idx & 31] = x;
+    if ((idx & 31) == 31 || idx == kTotal - 1) {
+#pragma unroll
+        for (int i = (idx & 31) + 1; i < 32; ++i) v[i] = 0.0f;  // the tail of a last group
+        const float r = warp_reduce_scatter32(v);
+        const int q = (idx & ~31) + (int)lane_id();  // the stream index this lane summed
+        if (r != 0.0f) {
+            int dst = -1;
+            if (q < 5 * NS) {
+                const int k = q / 5, c = q - 5 * k;
+                dst = c < 3 ? a.off_W1 + 3 * k + c : (c == 3 ? a.off_b1 + k : a.off_w2 + k);
+            } else if (q == 5 * NS) {
+                dst = a.off_b2;
+            } else if (q < kTotal) {
+                dst = gvo + (q - 5 * NS - 1);
+            }
+            if (dst >= 0) atomicAdd(A + dst, r);
+        }
+    }
+}
+
 // Density and geometry gradient of one (pixel, primitive) pair, reduced across
 // the warp into the entry's shared-memory accumulator A (the colour MLP's part is
 // a separate work item, warp_color_bwd_pass).  All 32 lanes call it together;
 // lanes without a pair pass contrib = false (their contributions are zero).
 // g_c: dL/dcolour, used for a constant colour only.
-template <int NC, int FORM>
+template <int NC, int FORM, int NS>
 __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *R, const float *D, int ns,
                                               const CamK &ck,
                                               const PixRay &ry, bool contrib, float g_ah, float3 g_c, float *A,
@@ -209,75 +242,93 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
         g_tout = gscale * b2;
         g_tin = -gscale * b2;
     }
-    for (int k0 = 0; k0 < ns; k0 += 6) {
-        float vv[32];
+    // density unit k: its five gradient values (returned), and its share of the
+    // sums the geometry part uses (accumulated)
+    auto dens_k = [&](int k, float (&gw)[3], float &gb1, float &gw2) {
+        const float4 w = W[k];
+        const float wk = w2[k];
+        const float g = fmaf(w.x, ry.g.x, fmaf(w.y, ry.g.y, w.z * ry.g.z));
+        if constexpr (FORM == 0) {
+            const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
+            const float th = g * hm;
+            float sp, cp, st, ct;
+            __sincosf(ph, &sp, &cp);
+            __sincosf(th, &st, &ct);
+            // sinc(th) and its derivative: series below |th| < kSincSeries, else one reciprocal
+            const float t2 = th * th, rt = __fdividef(1.0f, th);
+            const bool small = fabsf(th) < kSincSeries;
+            const float sc = small ? sinc_series(t2) : st * rt;
+            const float scp = small ? sinc_deriv_series(th, t2) : fmaf(th, ct, -st) * rt * rt;
+            S = fmaf(wk * cp, sc, S);
+            const float gphi = -gS * wk * sp * sc;
+            const float gth = gS * wk * cp * scp;
+            gw2 = gS * cp * sc;
+            gw[0] = fmaf(gphi, u.x, gth * hm * ry.g.x);
+            gw[1] = fmaf(gphi, u.y, gth * hm * ry.g.y);
+            gw[2] = fmaf(gphi, u.z, gth * hm * ry.g.z);
+            gb1 = gphi;
+            g_u.x = fmaf(gphi, w.x, g_u.x);
+            g_u.y = fmaf(gphi, w.y, g_u.y);
+            g_u.z = fmaf(gphi, w.z, g_u.z);
+            g_hm = fmaf(gth, g, g_hm);
+        } else {
+            const float ak = g * inv_m;
+            const float psi = fmaf(w.x, ocm.x, fmaf(w.y, ocm.y, fmaf(w.z, ocm.z, w.w)));
+            float s1, c1, s0, c0v;
+            __sincosf(fmaf(ak, tout, psi), &s1, &c1);
+            __sincosf(fmaf(ak, tin, psi), &s0, &c0v);
+            const float ia = gscale != 0.0f ? __fdividef(1.0f, ak) : 0.0f;
+            gw2 = gscale * (s1 - s0) * ia;
+            const float gpsi = gscale * wk * (c1 - c0v) * ia;
+            const float ga = gscale * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
+            gw[0] = fmaf(gpsi, ocm.x, ga * inv_m * ry.g.x);
+            gw[1] = fmaf(gpsi, ocm.y, ga * inv_m * ry.g.y);
+            gw[2] = fmaf(gpsi, ocm.z, ga * inv_m * ry.g.z);
+            gb1 = gpsi;
+            g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
+            g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
+            g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
+            g_invm = fmaf(ga, g, g_invm);
+            g_tout = fmaf(gscale * wk, c1, g_tout);
+            g_tin = fmaf(-gscale * wk, c0v, g_tin);
+        }
+    };
+    float pk[32];  // NS > 0: the current group of the packed gradient stream
+    if constexpr (NS == 0) {
+        for (int k0 = 0; k0 < ns; k0 += 6) {
+            float vv[32];
 #pragma unroll
-        for (int kk = 0; kk < 6; ++kk) {
-            const int k = k0 + kk;
-            float gw[3] = {0.f, 0.f, 0.f}, gb1 = 0.0f, gw2 = 0.0f;
-            if (k < ns) {
-                const float4 w = W[k];
-                const float wk = w2[k];
-                const float g = fmaf(w.x, ry.g.x, fmaf(w.y, ry.g.y, w.z * ry.g.z));
-                if constexpr (FORM == 0) {
-                    const float ph = fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, w.w)));
-                    const float th = g * hm;
-                    float sp, cp, st, ct;
-                    __sincosf(ph, &sp, &cp);
-                    __sincosf(th, &st, &ct);
-                    // sinc(th) and its derivative: series below |th| < kSincSeries, else one reciprocal
-                    const float t2 = th * th, rt = __fdividef(1.0f, th);
-                    const bool small = fabsf(th) < kSincSeries;
-                    const float sc = small ? sinc_series(t2) : st * rt;
-                    const float scp = small ? sinc_deriv_series(th, t2) : fmaf(th, ct, -st) * rt * rt;
-                    S = fmaf(wk * cp, sc, S);
-                    const float gphi = -gS * wk * sp * sc;
-                    const float gth = gS * wk * cp * scp;
-                    gw2 = gS * cp * sc;
-                    gw[0] = fmaf(gphi, u.x, gth * hm * ry.g.x);
-                    gw[1] = fmaf(gphi, u.y, gth * hm * ry.g.y);
-                    gw[2] = fmaf(gphi, u.z, gth * hm * ry.g.z);
-                    gb1 = gphi;
-                    g_u.x = fmaf(gphi, w.x, g_u.x);
-                    g_u.y = fmaf(gphi, w.y, g_u.y);
-                    g_u.z = fmaf(gphi, w.z, g_u.z);
-                    g_hm = fmaf(gth, g, g_hm);
-                } else {
-                    const float ak = g * inv_m;
-                    const float psi = fmaf(w.x, ocm.x, fmaf(w.y, ocm.y, fmaf(w.z, ocm.z, w.w)));
-                    float s1, c1, s0, c0v;
-                    __sincosf(fmaf(ak, tout, psi), &s1, &c1);
-                    __sincosf(fmaf(ak, tin, psi), &s0, &c0v);
-                    const float ia = gscale != 0.0f ? __fdividef(1.0f, ak) : 0.0f;
-                    gw2 = gscale * (s1 - s0) * ia;
-                    const float gpsi = gscale * wk * (c1 - c0v) * ia;
-                    const float ga = gscale * wk * ((c1 * tout - c0v * tin) * ia - (s1 - s0) * ia * ia);
-                    gw[0] = fmaf(gpsi, ocm.x, ga * inv_m * ry.g.x);
-                    gw[1] = fmaf(gpsi, ocm.y, ga * inv_m * ry.g.y);
-                    gw[2] = fmaf(gpsi, ocm.z, ga * inv_m * ry.g.z);
-                    gb1 = gpsi;
-                    g_ocm.x = fmaf(gpsi, w.x, g_ocm.x);
-                    g_ocm.y = fmaf(gpsi, w.y, g_ocm.y);
-                    g_ocm.z = fmaf(gpsi, w.z, g_ocm.z);
-                    g_invm = fmaf(ga, g, g_invm);
-                    g_tout = fmaf(gscale * wk, c1, g_tout);
-                    g_tin = fmaf(-gscale * wk, c0v, g_tin);
-                }
+            for (int kk = 0; kk < 6; ++kk) {
+                const int k = k0 + kk;
+                float gw[3] = {0.f, 0.f, 0.f}, gb1 = 0.0f, gw2 = 0.0f;
+                if (k < ns) dens_k(k, gw, gb1, gw2);
+                vv[5 * kk + 0] = gw[0];
+                vv[5 * kk + 1] = gw[1];
+                vv[5 * kk + 2] = gw[2];
+                vv[5 * kk + 3] = gb1;
+                vv[5 * kk + 4] = gw2;
             }
-            vv[5 * kk + 0] = gw[0];
-            vv[5 * kk + 1] = gw[1];
-            vv[5 * kk + 2] = gw[2];
-            vv[5 * kk + 3] = gb1;
-            vv[5 * kk + 4] = gw2;
+            vv[30] = 0.0f;
+            vv[31] = 0.0f;
+            const float r = warp_reduce_scatter32(vv);
+            const int kk = lane / 5, c = lane - 5 * kk, k = k0 + kk;
+            if (lane < 30 && k < ns && r != 0.0f) {
+                const int dst = c < 3 ? a.off_W1 + 3 * k + c : (c == 3 ? a.off_b1 + k : a.off_w2 + k);
+                atomicAdd(A + dst, r);
+            }
         }
-        vv[30] = 0.0f;
-        vv[31] = 0.0f;
-        const float r = warp_reduce_scatter32(vv);
-        const int kk = lane / 5, c = lane - 5 * kk, k = k0 + kk;
-        if (lane < 30 && k < ns && r != 0.0f) {
-            const int dst = c < 3 ? a.off_W1 + 3 * k + c : (c == 3 ? a.off_b1 + k : a.off_w2 + k);
-            atomicAdd(A + dst, r);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            float gw[3] = {0.f, 0.f, 0.f}, gb1 = 0.0f, gw2 = 0.0f;
+            dens_k(k, gw, gb1, gw2);
+            pack_put<NS>(pk, 5 * k + 0, gw[0], a, A, gvo);
+            pack_put<NS>(pk, 5 * k + 1, gw[1], a, A, gvo);
+            pack_put<NS>(pk, 5 * k + 2, gw[2], a, A, gvo);
+            pack_put<NS>(pk, 5 * k + 3, gb1, a, A, gvo);
+            pack_put<NS>(pk, 5 * k + 4, gw2, a, A, gvo);
         }
+        pack_put<NS>(pk, 5 * NS, g_b2, a, A, gvo);
     }
     // ---- geometry: (t, half) and u back to the record quantities
     float g_s = 0.0f;
@@ -323,21 +374,24 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
     const float g_dy = g_f.x * R[kRecG + 1] + g_f.y * R[kRecG + 4] + g_f.z * R[kRecG + 7] +
                        g_dg.x * ck.r1.x + g_dg.y * ck.r1.y + g_dg.z * ck.r1.z;
 
-    {
+    float gv[22];  // the geometry record's slots 0 .. 21 (22, 23 stay zero)
+    gv[kGvG + 0] = g_f.x * h.dx; gv[kGvG + 1] = g_f.x * h.dy;
+    gv[kGvG + 2] = g_f.y * h.dx; gv[kGvG + 3] = g_f.y * h.dy;
+    gv[kGvG + 4] = g_f.z * h.dx; gv[kGvG + 5] = g_f.z * h.dy;
+    gv[kGvE + 0] = g_e.x; gv[kGvE + 1] = g_e.y; gv[kGvE + 2] = g_e.z;
+    gv[kGvMz] = g_mz;
+    gv[kGvU] = -g_dx * ck.ifx;
+    gv[kGvV] = -g_dy * ck.ify;
+    gv[kGvAc + 0] = g_ac.x; gv[kGvAc + 1] = g_ac.y; gv[kGvAc + 2] = g_ac.z;
+    gv[kGvInvM] = g_invm;
+    gv[kGvOcm + 0] = g_ocm.x; gv[kGvOcm + 1] = g_ocm.y; gv[kGvOcm + 2] = g_ocm.z;
+    gv[kGvRgb + 0] = NC == 0 ? g_c.x : 0.0f;
+    gv[kGvRgb + 1] = NC == 0 ? g_c.y : 0.0f;
+    gv[kGvRgb + 2] = NC == 0 ? g_c.z : 0.0f;
+    if constexpr (NS == 0) {
         float vv[32];
-        vv[kGvG + 0] = g_f.x * h.dx; vv[kGvG + 1] = g_f.x * h.dy;
-        vv[kGvG + 2] = g_f.y * h.dx; vv[kGvG + 3] = g_f.y * h.dy;
-        vv[kGvG + 4] = g_f.z * h.dx; vv[kGvG + 5] = g_f.z * h.dy;
-        vv[kGvE + 0] = g_e.x; vv[kGvE + 1] = g_e.y; vv[kGvE + 2] = g_e.z;
-        vv[kGvMz] = g_mz;
-        vv[kGvU] = -g_dx * ck.ifx;
-        vv[kGvV] = -g_dy * ck.ify;
-        vv[kGvAc + 0] = g_ac.x; vv[kGvAc + 1] = g_ac.y; vv[kGvAc + 2] = g_ac.z;
-        vv[kGvInvM] = g_invm;
-        vv[kGvOcm + 0] = g_ocm.x; vv[kGvOcm + 1] = g_ocm.y; vv[kGvOcm + 2] = g_ocm.z;
-        vv[kGvRgb + 0] = NC == 0 ? g_c.x : 0.0f;
-        vv[kGvRgb + 1] = NC == 0 ? g_c.y : 0.0f;
-        vv[kGvRgb + 2] = NC == 0 ? g_c.z : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 22; ++q) vv[q] = gv[q];
         vv[22] = 0.0f;
         vv[23] = 0.0f;
         vv[24] = g_b2;
@@ -348,6 +402,9 @@ __device__ __forceinline__ void pair_backward(const RasterArgs &a, const float *
             if (lane < (unsigned)kGvFloats) atomicAdd(A + gvo + lane, r);
             else if (lane == 24) atomicAdd(A + a.off_b2, r);
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 22; ++q) pack_put<NS>(pk, 5 * NS + 1 + q, gv[q], a, A, gvo);
     }
 
 }
@@ -382,7 +439,9 @@ __host__ __device__ inline size_t bwd_smem_bytes(int nc, int ns, int chunk, int 
     return NPIX * (32 + 12) + (size_t)chunk * per_entry + stage;
 }
 
-template <int TS, int NC, int FORM, bool BF16>
+// NS > 0: built for n_sigma = NS (the density loop unrolled, its gradients packed;
+// see pack_put); NS = 0: any n_sigma.
+template <int TS, int NC, int FORM, bool BF16, int NS>
 __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_raster_bwd(RasterArgs a)
 {
     constexpr int NT = TileCfg<TS>::NT;
@@ -390,7 +449,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     constexpr int PPT = TileCfg<TS>::PPT;
     extern __shared__ float4 smem4[];
     const int CH = a.chunk;
-    const int ns = a.n_sigma;
+    const int ns = NS > 0 ? NS : a.n_sigma;
     const int es = entry_stride(ns, NC);
     constexpr int SW = tmem_wc2_floats(TS, NC);  // Wc2 floats not in the accumulator (TMEM path)
     const int vg = acc_stride(a.stride, NC) - SW;
@@ -726,7 +785,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                             const float wi = valid ? s_w[e * NPIX + pix] : 0.0f;
                             g_c = make_float3(wi * s_dl[pix], wi * s_dl[NPIX + pix], wi * s_dl[2 * NPIX + pix]);
                         }
-                        pair_backward<NC, FORM>(a, R, R + kRecFloats, ns, ck, r, valid, s_cs[e * NPIX + pix].w, g_c,
+                        pair_backward<NC, FORM, NS>(a, R, R + kRecFloats, ns, ck, r, valid, s_cs[e * NPIX + pix].w, g_c,
                                                 acc + e * vg, gvo);
                     }
                     int nx = 0;
