@@ -1,9 +1,9 @@
 """The allocation-free sort entry point (snp_sort_pairs_noalloc) through the C ABI.
 
-Callers that cannot allocate device memory while they run (a region being
-captured into a CUDA graph, an application whose memory pool owns the device, a
-loop that cannot take cudaMalloc's implicit synchronisation) sort with scratch
-that lives in a static device array of the library.  This checks, on two calls
+Callers that cannot allocate device memory while they run (an application
+whose memory pool owns the device, a plugin handed a fixed arena, a loop that
+cannot take cudaMalloc's implicit synchronisation) sort with scratch that lives
+in a static device array of the library.  This checks, on two calls
 in a row with different inputs, that it orders the tile keys exactly as the
 sort inside snp_render_forward does and as the oracle's stable sort does, that
 key bits above the sorted width do not change the order, that the device's free
