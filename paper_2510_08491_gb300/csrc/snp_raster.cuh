@@ -101,32 +101,52 @@ __device__ __forceinline__ void stage_chunk_issue(float *sm, const uint32_t *s_g
     }
 }
 
-template <int NC, bool BF16>
-__device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
-                                            const RasterArgs &a, int es, float xi)
+// The copies of stage_chunk without a colour network (one flat range of 16-byte
+// pieces over all entries), without the wait.
+__device__ __forceinline__ void stage_issue_flat(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
+                                                 const RasterArgs &a, int es)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr int kRec16 = kRecFloats / 4;
     const int per = es / 4;  // 16-byte pieces per entry: record, then the network block
+    const int total = cnt * per;
+    for (int idx = tid; idx < total; idx += nt) {
+        const int e = idx / per, q = idx - e * per;
+        const int64_t gid = s_gid[e];
+        const float *src = q < kRec16 ? a.rec + gid * kRecFloats + 4 * q
+                                      : a.npack + (gid - vn) * a.npack_stride + 4 * (q - kRec16);
+        cp_async16(sm + e * es + 4 * q, src);
+    }
+}
+
+// After the calling thread's stage_issue_flat copies have completed (its own
+// cp.async wait): the time-conditioned phase shift of the pieces it copied.
+template <bool BF16>
+__device__ __forceinline__ void stage_shift_flat(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
+                                                 const RasterArgs &a, int es, float xi)
+{
+    if (a.off_wt < 0) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr int kRec16 = kRecFloats / 4;
+    const int per = es / 4;
+    const int total = cnt * per;
+    for (int idx = tid; idx < total; idx += nt) {
+        const int e = idx / per, q = idx - e * per - kRec16;
+        if (q >= 0 && q < a.n_sigma) {
+            float *w = sm + e * es + 4 * (q + kRec16) + 3;
+            *w = fmaf(xi, ld_w<BF16>(a.net, (s_gid[e] - vn) * a.stride + a.off_wt + q), *w);
+        }
+    }
+}
+
+template <int NC, bool BF16>
+__device__ __forceinline__ void stage_chunk(float *sm, const uint32_t *s_gid, int cnt, int64_t vn,
+                                            const RasterArgs &a, int es, float xi)
+{
     if constexpr (NC == 0) {
-        const int total = cnt * per;
-        for (int idx = tid; idx < total; idx += nt) {
-            const int e = idx / per, q = idx - e * per;
-            const int64_t gid = s_gid[e];
-            const float *src = q < kRec16 ? a.rec + gid * kRecFloats + 4 * q
-                                          : a.npack + (gid - vn) * a.npack_stride + 4 * (q - kRec16);
-            cp_async16(sm + e * es + 4 * q, src);
-        }
+        stage_issue_flat(sm, s_gid, cnt, vn, a, es);
         cp_async_wait_all();
-        if (a.off_wt >= 0) {
-            for (int idx = tid; idx < total; idx += nt) {
-                const int e = idx / per, q = idx - e * per - kRec16;
-                if (q >= 0 && q < a.n_sigma) {
-                    float *w = sm + e * es + 4 * (q + kRec16) + 3;
-                    *w = fmaf(xi, ld_w<BF16>(a.net, (s_gid[e] - vn) * a.stride + a.off_wt + q), *w);
-                }
-            }
-        }
+        stage_shift_flat<BF16>(sm, s_gid, cnt, vn, a, es, xi);
     } else {
         stage_chunk_issue<NC, BF16>(sm, s_gid, cnt, vn, a, es);
         cp_async_wait_all();

@@ -464,6 +464,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     float *s_w = reinterpret_cast<float *>(s_cs + CH * NPIX);  // [CH][NPIX] weights of the composited pairs
     uint16_t *s_al = reinterpret_cast<uint16_t *>(s_w + CH * NPIX);  // [CH][NPIX] pair lists
     constexpr bool TM = bwd_tmem(TS, NC);
+    constexpr bool kEarly = NC == 0 || TM;  // begin the next chunk before the flush (below)
     // TM: per warp, the operand tiles of its tcgen05.mma (128-byte aligned)
     char *s_stage = reinterpret_cast<char *>(
         (reinterpret_cast<uintptr_t>(s_al + CH * NPIX) + 127) & ~static_cast<uintptr_t>(127));
@@ -471,7 +472,8 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
     __shared__ uint32_t s_koff[64];         // colour-store offsets of the chunk's keys (two halves)
     __shared__ bool s_stored;               // every composited pair of the chunk is in the store
     __shared__ uint32_t s_cmw[kMaskWords];  // composited-mask words of the chunk (two halves)
-    __shared__ int s_na[65], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
+    // s_na: composited pairs per entry of the current and the next chunk (two halves)
+    __shared__ int s_na[66], s_pa[65], s_nb[65], s_pb[65], s_np[65], s_pp[65];
     __shared__ int s_view, s_item;
     __shared__ int s_item6;  // P6 item counter (items past the first one of each warp)
     __shared__ uint32_t s_maxwalk;
@@ -563,87 +565,94 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
         __syncthreads();
         const uint32_t maxwalk = s_maxwalk;
 
-        // Per chunk: its keys' record ids, colour-store offsets and composited masks, in
-        // one of two halves of s_gid / s_koff / s_cmw; the next chunk's are copied into
-        // the other half (4-byte cp.async) while this chunk runs P6.
+        // Per chunk: its keys' record ids, colour-store offsets, composited masks and
+        // composited counts, in one of two halves of s_gid / s_koff / s_cmw / s_na; the
+        // next chunk's ids, offsets and masks are copied into the other half (4-byte
+        // cp.async) while this chunk runs P6.  With kEarly the next chunk is then begun
+        // before this chunk's flush: its staging copies are issued and P1 builds its pair
+        // lists and issues its store copies, so that the copies land while the flush
+        // runs.  (Measured: without a colour network 37.1 -> 35.7 ms on the 8-view 800 x 800
+        // speed protocol; at N_c = 32, two CTAs per SM, the other CTA already covers the
+        // copies and the early begin was 0.6 ms slower, so that kernel begins each chunk
+        // after the previous flush.)
+        uint32_t cm[PPT];  // per pixel: entries of the begun chunk it composited
+        // Begin chunk (c0b, cib): its ids, offsets and masks (copied in during the
+        // previous chunk's P6 if `prefetched`, else loaded here), its staging copies and P1.
+        auto begin_chunk = [&](uint32_t c0b, int cib, bool prefetched) {
+            const int cntb = min((int)(rg.y - c0b), CH);
+            uint32_t *const bg = s_gid + (cib & 1) * (kMaxChunk / 2);
+            uint32_t *const bko = s_koff + (cib & 1) * 32;
+            uint32_t *const bmw = s_cmw + (cib & 1) * (kMaskWords / 2);
+            int *const bna = s_na + (cib & 1) * 33;
+            if (prefetched) {
+                cp_async_wait_all();
+            } else {
+                if (tid < cntb) {
+                    bg[tid] = a.vals[c0b + tid];
+                    bko[tid] = has_store ? a.key_off[c0b + tid] : kNoStore;
+                }
+                // composited masks of the chunk's entries (none past the tile's walk length)
+                for (int i = tid; i < cntb * (NPIX / 32); i += NT) {
+                    const int e = i / (NPIX / 32);
+                    bmw[i] = c0b - rg.x + e < maxwalk ? a.cmask[(int64_t)c0b * (NPIX / 32) + i] : 0u;
+                }
+            }
+            if constexpr (TM) {
+                if (tid < cntb) s_tmstart[tid] = 0;
+            }
+            __syncthreads();
+            // staging copies in flight through P1, which needs only the masks; one wait
+            // covers them and P1's store copies
+            if constexpr (NC > 0) stage_chunk_issue<NC, BF16>(sm, bg, cntb, vn, a, es);
+            else stage_issue_flat(sm, bg, cntb, vn, a, es);
+            // P1: the pixels that composited each entry, from the forward's masks (entries
+            // at or past the tile's walk length were composited by no pixel)
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) cm[k] = 0u;
+            // Each entry's pair list is its composited pixels in slot order: a pixel's
+            // position is its rank among the set bits of the entry's mask (no atomics).
+            for (int e = 0; e < cntb; ++e) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const int slot = k * NT + tid;
+                    const unsigned word = bmw[e * (NPIX / 32) + (slot >> 5)];
+                    const bool act = (word >> lane) & 1u;
+                    cm[k] |= (uint32_t)act << e;
+                    if (act) {
+                        const uint32_t rank = mask_rank<NPIX>(bmw + e * (NPIX / 32), slot);
+                        s_al[e * NPIX + rank] = (uint16_t)slot;
+                        const uint32_t o = bko[e];
+                        if (o != kNoStore) {
+                            if constexpr (NC > 0) {
+                                // the pair's (colour, alpha_hat) from the forward's store
+                                cp_async16(s_cs + e * NPIX + slot, a.colstore + o + rank);
+                            } else {
+                                // alpha_hat from the store (the colour is the staged record's)
+                                cp_async4(reinterpret_cast<float *>(s_cs + e * NPIX + slot) + 3, a.ahstore + o + rank);
+                            }
+                        }
+                    }
+                }
+            }
+            if (tid < cntb) {
+                int c = 0;
+                for (int w = 0; w < NPIX / 32; ++w) c += __popc(bmw[tid * (NPIX / 32) + w]);
+                bna[tid] = c;
+            }
+        };
+
         bool pre = false;
         int ci = 0;
         for (uint32_t c0 = rg.x; c0 < rg.y && c0 - rg.x < maxwalk; c0 += CH, ++ci) {
             const int cnt = min((int)(rg.y - c0), CH);
             uint32_t *const cg = s_gid + (ci & 1) * (kMaxChunk / 2);
             uint32_t *const cko = s_koff + (ci & 1) * 32;
-            uint32_t *const cmw = s_cmw + (ci & 1) * (kMaskWords / 2);
-            __syncthreads();
-            if (pre) {
-                cp_async_wait_all();
-            } else {
-                if (tid < cnt) {
-                    cg[tid] = a.vals[c0 + tid];
-                    cko[tid] = has_store ? a.key_off[c0 + tid] : kNoStore;
-                }
-                // composited masks of the chunk's entries (none past the tile's walk length)
-                for (int i = tid; i < cnt * (NPIX / 32); i += NT) {
-                    const int e = i / (NPIX / 32);
-                    cmw[i] = c0 - rg.x + e < maxwalk ? a.cmask[(int64_t)c0 * (NPIX / 32) + i] : 0u;
-                }
-            }
-            if (tid < cnt) {
-                s_na[tid] = 0;
-                if constexpr (TM) s_tmstart[tid] = 0;
-            }
+            const int *const na = s_na + (ci & 1) * 33;
+            // (kEarly: a chunk after the first was begun before the previous chunk's flush)
+            if (ci == 0 || !kEarly) begin_chunk(c0, ci, ci > 0);
             if (tid == 0) s_item6 = 0;
-            __syncthreads();
-            if constexpr (NC > 0) {
-                // staging copies in flight through P1, which needs only the masks; one
-                // wait below covers them and P1's colour-store copies
-                stage_chunk_issue<NC, BF16>(sm, cg, cnt, vn, a, es);
-            } else {
-                stage_chunk<NC, BF16>(sm, cg, cnt, vn, a, es, V.time);
-                __syncthreads();
-            }
-
-            // P1: the pixels that composited each entry, from the forward's masks (entries
-            // at or past the tile's walk length were composited by no pixel)
-            uint32_t cm[PPT];  // per pixel: entries of this chunk it composited
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) cm[k] = 0u;
-            // Each entry's pair list is its composited pixels in slot order: a pixel's
-            // position is its rank among the set bits of the entry's mask (no atomics).
-            for (int e = 0; e < cnt; ++e) {
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const int slot = k * NT + tid;
-                    const unsigned word = cmw[e * (NPIX / 32) + (slot >> 5)];
-                    const bool act = (word >> lane) & 1u;
-                    cm[k] |= (uint32_t)act << e;
-                    if (act) {
-                        const uint32_t rank = mask_rank<NPIX>(cmw + e * (NPIX / 32), slot);
-                        s_al[e * NPIX + rank] = (uint16_t)slot;
-                        const uint32_t o = cko[e];
-                        if (o != kNoStore) {
-                            if constexpr (NC > 0) {
-                                // the pair's (colour, alpha_hat) from the forward's store, copied
-                                // asynchronously while the lists are built
-                                cp_async16(s_cs + e * NPIX + slot, a.colstore + o + rank);
-                            } else {
-                                // the primitive's colour from its staged record, alpha_hat from the store
-                                const float *R = sm + e * es;
-                                float *cs = reinterpret_cast<float *>(s_cs + e * NPIX + slot);
-                                cs[0] = R[kRecRgb + 0];
-                                cs[1] = R[kRecRgb + 1];
-                                cs[2] = R[kRecRgb + 2];
-                                cp_async4(cs + 3, a.ahstore + o + rank);
-                            }
-                        }
-                    }
-                }
-            }
-            if (tid < cnt) {
-                int c = 0;
-                for (int w = 0; w < NPIX / 32; ++w) c += __popc(cmw[tid * (NPIX / 32) + w]);
-                s_na[tid] = c;
-            }
-            if (NC > 0 || has_store) cp_async_wait_all();
+            cp_async_wait_all();  // this chunk's staging and store copies
+            if constexpr (NC == 0) stage_shift_flat<BF16>(sm, cg, cnt, vn, a, es, V.time);
             // the previous chunk's bulk adds have read its accumulators by now
             if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
             __syncthreads();
@@ -652,23 +661,23 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 for (int q = tid; q < clear_n; q += NT) A4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             if (tid < 32) {
-                warp_prefix64(s_na, cnt, s_pa);
-                warp_batch_prefix(s_na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
-                warp_batch_prefix(s_na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
-                const bool miss = (int)lane < cnt && s_na[lane] > 0 && cko[lane] == kNoStore;
-                const bool miss2 = (int)lane + 32 < cnt && s_na[lane + 32] > 0 && cko[lane + 32] == kNoStore;
-                const bool any = __any_sync(0xffffffffu, miss || miss2);
+                warp_prefix64(na, cnt, s_pa);
+                warp_batch_prefix(na, cnt, 5, s_nb, s_pb);  // density items: 32 pairs
+                warp_batch_prefix(na, cnt, 4, s_np, s_pp);  // colour items: 16 pairs
+                const bool miss = (int)lane < cnt && na[lane] > 0 && cko[lane] == kNoStore;
+                const bool any = __any_sync(0xffffffffu, miss);
                 if (lane == 0) s_stored = !any;
             }
             __syncthreads();
             const bool stored = s_stored;
             // P2: alpha_hat of every composited pair (per thread), then P4: their colours
             // (per warp, 16 pairs of one entry); independent, so one phase.  With the
-            // colour store both come from the forward (one 16-byte load per pair).
+            // store both come from the forward (without a colour network the colour is
+            // the staged record's).
             {
-                const int na = s_pa[cnt];
+                const int np2 = s_pa[cnt];
                 int e = 0;
-                for (int q = tid; q < (stored ? 0 : na); q += NT) {
+                for (int q = tid; q < (stored ? 0 : np2); q += NT) {
                     while (q >= s_pa[e + 1]) ++e;
                     const int pix = s_al[e * NPIX + (q - s_pa[e])];
                     const float *R = sm + e * es;
@@ -676,8 +685,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     Hit h;
                     float ah = 0.0f;
                     if (intersect(R, ck, r, h)) ah = integral<FORM>(R, R + kRecFloats, ns, ck, r, h);
-                    if constexpr (NC == 0) s_cs[e * NPIX + pix] = make_float4(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2], ah);
-                    else s_cs[e * NPIX + pix].w = ah;
+                    s_cs[e * NPIX + pix].w = ah;
                 }
             }
             if constexpr (NC > 0) {
@@ -687,7 +695,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     for (int q = wid; q < np; q += NT / 32) {
                         while (q >= s_pp[e + 1]) ++e;
                         warp_color_pass<NC, BF16>(sm + e * es + kRecFloats + den_stride(ns), s_ray,
-                                                  s_al + e * NPIX, (q - s_pp[e]) * 16, s_na[e],
+                                                  s_al + e * NPIX, (q - s_pp[e]) * 16, na[e],
                                                   reinterpret_cast<float *>(s_cs + e * NPIX), 4, 1);
                     }
                 }
@@ -707,7 +715,13 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     tau[k] += ah;
                     const float Tn = __expf(-tau[k]);
                     s_w[e * NPIX + slot] = w;
-                    const float3 col = make_float3(cs.x, cs.y, cs.z);
+                    float3 col;
+                    if constexpr (NC > 0) {
+                        col = make_float3(cs.x, cs.y, cs.z);
+                    } else {
+                        const float *R = sm + e * es;
+                        col = make_float3(R[kRecRgb + 0], R[kRecRgb + 1], R[kRecRgb + 2]);
+                    }
                     pref[k].x = fmaf(w, col.x, pref[k].x);
                     pref[k].y = fmaf(w, col.y, pref[k].y);
                     pref[k].z = fmaf(w, col.z, pref[k].z);
@@ -718,26 +732,24 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             }
             __syncthreads();
             // the next chunk's ids, store offsets and masks, in flight through P6
-            {
-                const uint32_t c0n = c0 + CH;
-                pre = c0n < rg.y && c0n - rg.x < maxwalk;
-                if (pre) {
-                    const int cntn = min((int)(rg.y - c0n), CH);
-                    uint32_t *const ng = s_gid + ((ci + 1) & 1) * (kMaxChunk / 2);
-                    uint32_t *const nko = s_koff + ((ci + 1) & 1) * 32;
-                    uint32_t *const nmw = s_cmw + ((ci + 1) & 1) * (kMaskWords / 2);
-                    if (tid < cntn) {
-                        cp_async4(ng + tid, a.vals + c0n + tid);
-                        if (has_store) cp_async4(nko + tid, a.key_off + c0n + tid);
-                        else nko[tid] = kNoStore;
-                    }
-                    for (int i = tid; i < cntn * (NPIX / 32); i += NT) {
-                        const int e = i / (NPIX / 32);
-                        if (c0n - rg.x + e < maxwalk) cp_async4(nmw + i, a.cmask + (int64_t)c0n * (NPIX / 32) + i);
-                        else nmw[i] = 0u;
-                    }
-                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+            const uint32_t c0n = c0 + CH;
+            pre = c0n < rg.y && c0n - rg.x < maxwalk;
+            if (pre) {
+                const int cntn = min((int)(rg.y - c0n), CH);
+                uint32_t *const ng = s_gid + ((ci + 1) & 1) * (kMaxChunk / 2);
+                uint32_t *const nko = s_koff + ((ci + 1) & 1) * 32;
+                uint32_t *const nmw = s_cmw + ((ci + 1) & 1) * (kMaskWords / 2);
+                if (tid < cntn) {
+                    cp_async4(ng + tid, a.vals + c0n + tid);
+                    if (has_store) cp_async4(nko + tid, a.key_off + c0n + tid);
+                    else nko[tid] = kNoStore;
                 }
+                for (int i = tid; i < cntn * (NPIX / 32); i += NT) {
+                    const int e = i / (NPIX / 32);
+                    if (c0n - rg.x + e < maxwalk) cp_async4(nmw + i, a.cmask + (int64_t)c0n * (NPIX / 32) + i);
+                    else nmw[i] = 0u;
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
             // P6: per-pair gradients.  Work items: colour-MLP passes of 16 pairs of one
             // entry (tensor cores), then density / geometry batches of 32 pairs of one
@@ -764,7 +776,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                                 tp.wait_status = a.wait_status;
                             }
                             warp_color_bwd_pass<NC, BF16, TM>(sm + ec * es + kRecFloats + den_stride(ns), s_ray,
-                                                              s_al + ec * NPIX, (it - s_pp[ec]) * 16, s_na[ec],
+                                                              s_al + ec * NPIX, (it - s_pp[ec]) * 16, na[ec],
                                                               s_w + ec * NPIX, s_dl, NPIX,
                                                               reinterpret_cast<const float *>(s_cs + ec * NPIX), 4,
                                                               1, A + a.off_Wc1, A + gvo + kGvFloats,
@@ -775,7 +787,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         const int q = it - np;
                         while (q >= s_pb[e + 1]) ++e;
                         const int kk = (q - s_pb[e]) * 32 + (int)lane;
-                        const bool valid = kk < s_na[e];
+                        const bool valid = kk < na[e];
                         const int pix = valid ? s_al[e * NPIX + kk] : 0;
                         const PixRay r = load_ray(s_ray, pix);
                         const float *R = sm + e * es;
@@ -811,7 +823,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     // warp w: rows 16 (w % 4) .. + 15, columns 32 (w / 4) .. + 31
                     const int half = wid >> 2;
                     for (int e = 0; e < cnt; ++e) {
-                        if (s_na[e] == 0) continue;
+                        if (na[e] == 0) continue;
                         uint32_t r[32];
                         tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)e + 32u * (uint32_t)half, r);
                         if (lane < 16) {
@@ -828,7 +840,7 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                     // hi half of dL/da2, lane l + 8 the same unit from the lo half; their sum
                     // is the row.  Warps w and w + 4 take alternate entries.
                     for (int e = wid >> 2; e < cnt; e += 2) {
-                        if (s_na[e] == 0) continue;
+                        if (na[e] == 0) continue;
                         uint32_t r[32];
                         tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 32u * (uint32_t)e, r);
                         float v[32];
@@ -848,7 +860,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 tc_fence_before_sync();
                 __syncthreads();
             }
-            flush_chunk<NC, NT, TM>(a, acc, vg, cg, cnt, s_na, vn, tid, NT, V.time, land);
+            // kEarly: the next chunk begins before this chunk's flush, so that its copies
+            // land meanwhile
+            if (kEarly && pre) begin_chunk(c0n, ci + 1, true);
+            flush_chunk<NC, NT, TM>(a, acc, vg, cg, cnt, na, vn, tid, NT, V.time, land);
             clear_n = cnt * vg / 4;
         }
         __syncthreads();

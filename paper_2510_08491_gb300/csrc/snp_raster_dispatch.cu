@@ -24,21 +24,25 @@ size_t raster_bwd_smem(int color_mode, int n_c, int n_sigma, int chunk, int ts, 
     return bwd_smem_bytes<16>(nc, n_sigma, chunk, stride);
 }
 
-// Largest chunk (<= 32 forward, <= 8 backward) within the shared-memory budget:
-// about half an SM for the forward (two CTAs per SM); for the backward half an SM
-// where it is built for two CTAs per SM, else most of one.
+// Largest chunk (<= 32 forward; backward <= 32 at 16-pixel tiles, else <= 8)
+// within the shared-memory budget: for k CTAs per SM, k (dynamic + static + the
+// 1 KB per-CTA reservation) must fit the SM's 228 KB, so the dynamic part of one
+// CTA stays below 228 KB / k - 1 KB - its static shared memory (about 2.6 KB in the
+// forward, 4.8 KB in the backward).  A budget above that silently drops a CTA per
+// SM: the time-conditioned backward at chunk 15 (108.7 KB) ran one CTA per SM and
+// took 55.6 ms against 36.8 ms at chunk 8.
 int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, int ts, bool dyn)
 {
     const int fmb = fwd_min_blocks(ts, nc_of(color_mode, n_c));
-    // (at 16-pixel tiles and N_c = 32 the 74 KB budget gives chunk 5, 73 KB, which
-    // still fits three CTAs per SM and measured faster than chunk 4: 22.3 against
-    // 23.2 ms at the four-view 1080p workload)
-    const size_t fwd_budget = fmb == 4 ? 52 * 1024 : (fmb == 3 ? 74 * 1024 : 104 * 1024);
+    // (at 16-pixel tiles and N_c = 32 the 72 KB budget gives chunk 5, 71.5 KB, which
+    // fits three CTAs per SM and measured faster than chunk 4: 22.3 against 23.2 ms at
+    // the four-view 1080p workload)
+    const size_t fwd_budget = fmb == 4 ? 52 * 1024 : (fmb == 3 ? 72 * 1024 : 104 * 1024);
     // (the tensor-memory backward at N_c = 64 also holds its operand tiles: most of one SM)
     const size_t bwd_budget = bwd_min_blocks(ts, nc_of(color_mode, n_c)) == 2
-                                  ? 110 * 1024
+                                  ? 108 * 1024
                                   : (bwd_tmem(ts, nc_of(color_mode, n_c)) ? 220 * 1024 : 200 * 1024);
-    int ch = backward ? 8 : 32;
+    int ch = backward ? (ts == 16 ? 32 : 8) : 32;
     if (backward && bwd_tmem(ts, nc_of(color_mode, n_c)))
         ch = tmem_max_chunk(ts == 8 ? 64 : 256, nc_of(color_mode, n_c));
     if (backward) {
