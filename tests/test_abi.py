@@ -107,15 +107,20 @@ def test_argument_errors_are_reported_before_any_device_work():
 
 def test_default_chunks_follow_the_shared_memory_budgets():
     """snp_default_chunks is host-only.  At N_sigma = 16, N_c = 32 both passes stage 5
-    entries (73 KB of the forward's three-CTA budget, 105 KB of the backward's
-    two-CTA budget).  At N_sigma = 32, N_c = 64 the tensor-memory backward stages 4:
-    the most its operand tiles can take at the chunk's end (4 x 16 KB), and 202 KB
-    of shared memory.  Bad arguments are refused."""
+    entries (71.5 KB of the forward's three-CTA budget of 72 KB, 105 KB of the
+    backward's two-CTA budget of 108 KB).  At N_sigma = 32, N_c = 64 the
+    tensor-memory backward stages 4: the most its operand tiles can take at the
+    chunk's end (4 x 16 KB), and 202 KB of shared memory.  Without a colour network
+    the 16-pixel backward's masks allow 32 entries, and the budget gives 15 at
+    N_sigma = 8 (106 KB), 14 time-conditioned (102 KB); 32-pixel tiles stay at
+    8 or fewer.  Bad arguments are refused."""
     assert L.default_chunks(16, L.COLOR_MLP, 32) == (5, 5)
     f64, b64 = L.default_chunks(32, L.COLOR_MLP, 64)
     assert b64 == 4 and 1 <= f64 <= 32
-    f0, b0 = L.default_chunks(8, L.COLOR_SH, 0)
-    assert 1 <= f0 <= 32 and 1 <= b0 <= 8
+    assert L.default_chunks(8, L.COLOR_SH, 0) == (32, 15)
+    assert L.default_chunks(8, L.COLOR_SH, 0, dynamic=True) == (32, 14)
+    f32t, b32t = L.default_chunks(8, L.COLOR_SH, 0, tile_size=32)
+    assert 1 <= f32t <= 32 and 1 <= b32t <= 8
     assert L.default_chunks(16, L.COLOR_MLP, 32, tile_size=0) == (5, 5)
     lib = L.lib()
     d = L.SceneDesc(10, 16, L.COLOR_MLP, 32, 0, 30.0, 0)
