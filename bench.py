@@ -719,6 +719,7 @@ def run_ours(args, rank, world):
                    "n_c": sc.n_c if sc.color == "mlp" else 0, "weights": sc.weight_dtype,
                    "tile": int(cfg.tile_size), "chunk": chunks_used(ps, cfg)[0],
                    "bwd_chunk": chunks_used(ps, cfg)[1],
+                   "ctas_per_sm": {"fwd": int(stats.fwd_ctas_per_sm), "bwd": int(stats.bwd_ctas_per_sm)},
                    "step": "forward+loss+backward" if target is not None else "forward+backward",
                    "graph": graph is not None, "autotuned": bool(args.autotune or batched),
                    "colour_store": not args.replay_color,
@@ -815,6 +816,7 @@ def batched_form(dev: int, steps: int, warmup: int):
     ms_fwd = timed(lambda: r.forward(ps, cams, cfg, out=img), steps)
     out = {"workload": "batch500k_16view", "weights": "bf16", "views": len(cams), "pixels": P,
            "tile": int(cfg.tile_size), "chunk": chunks_used(ps, cfg)[0], "bwd_chunk": chunks_used(ps, cfg)[1],
+           "ctas_per_sm": {"fwd": int(stats.fwd_ctas_per_sm), "bwd": int(stats.bwd_ctas_per_sm)},
            "graph": True, "autotuned": True,
            "fwd_bwd_mpix_s": round(P / (ms * 1e-3) / 1e6, 3), "fwd_bwd_ms": round(ms, 3),
            "fwd_mpix_s": round(P / (ms_fwd * 1e-3) / 1e6, 3), "fwd_ms": round(ms_fwd, 3), "keys": int(K),

@@ -223,6 +223,10 @@ typedef struct {
     int64_t n_candidates; /* (pixel, list entry) pairs visited before termination */
     int64_t n_hits;       /* of those, rays that enter the ellipsoid */
     int64_t n_composited; /* of those, alpha_hat > 0 (colour evaluated and blended) */
+    int32_t fwd_ctas_per_sm; /* CTAs per SM the last raster forward launch kept resident (its
+                              * persistent grid is this times the SM count, capped by the
+                              * tiles); 0 before any forward */
+    int32_t bwd_ctas_per_sm; /* the same for the last raster backward; 0 before any backward */
 } snp_stats;
 
 typedef struct snp_context snp_context;

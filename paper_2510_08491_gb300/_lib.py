@@ -60,7 +60,8 @@ class Config(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_keys", C.c_int64), ("n_tiles", C.c_int64), ("n_pixels", C.c_int64),
-                ("n_candidates", C.c_int64), ("n_hits", C.c_int64), ("n_composited", C.c_int64)]
+                ("n_candidates", C.c_int64), ("n_hits", C.c_int64), ("n_composited", C.c_int64),
+                ("fwd_ctas_per_sm", C.c_int32), ("bwd_ctas_per_sm", C.c_int32)]
 
 
 class PopctlConfig(C.Structure):

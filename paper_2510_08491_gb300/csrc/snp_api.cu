@@ -135,6 +135,7 @@ int tile_bits(int64_t tiles)
 
 struct snp_context {
     int device = 0;
+    int fwd_ctas = 0, bwd_ctas = 0;  // CTAs per SM of the last raster launches
     std::mutex mu;
     char err[512] = {0};
     bool reserved = false;
@@ -720,7 +721,9 @@ snp_status snp_render_forward(snp_context *ctx, const snp_scene_desc *desc, cons
         }
     }
     STAGE_BEGIN(SNP_STAGE_RASTER_FWD);
+    note_raster_ctas(0);
     s = launch_raster_fwd(a, desc->color_mode, desc->n_c, c.integral_form, desc->weight_dtype == SNP_BF16, ts, st);
+    if (s == SNP_OK) ctx->fwd_ctas = last_raster_ctas();
     STAGE_END();
     ctx->fwd_done = true;
     if (s != SNP_OK) return fail(ctx, s, "raster forward launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -785,10 +788,12 @@ snp_status snp_render_backward(snp_context *ctx, int64_t token, const snp_scene_
                   : nullptr;
     CK(cudaMemsetAsync(d_work, 0, 4, st));
     STAGE_BEGIN(SNP_STAGE_RASTER_BWD);
+    note_raster_ctas(0);
     s = launch_raster_bwd(a, desc->color_mode, desc->n_c, ctx->cfg.integral_form, desc->weight_dtype == SNP_BF16,
                           ctx->ts, st);
     STAGE_END();
     if (s != SNP_OK) return fail(ctx, s, "raster backward launch failed");
+    ctx->bwd_ctas = last_raster_ctas();
     STAGE_BEGIN(SNP_STAGE_POST_BWD);
     if (grads->geom)
         launch_project_bwd((const float *)scene->geom, n, (const View *)ctx->views.p, ctx->n_views,
@@ -951,6 +956,8 @@ snp_status snp_get_stats(snp_context *ctx, int64_t token, snp_stats *out, void *
     out->n_candidates = (int64_t)h[0];
     out->n_hits = (int64_t)h[1];
     out->n_composited = (int64_t)h[2];
+    out->fwd_ctas_per_sm = ctx->fwd_ctas;
+    out->bwd_ctas_per_sm = ctx->bwd_ctas;
     if (ctx->h_small[4] != 0) return fail(ctx, SNP_ERR_CAPACITY, "tile keys exceeded the reserved capacity");
     if (ctx->h_small[5] != 0) return fail(ctx, SNP_ERR_TIMEOUT, "a bounded device wait of the backward gave up");
     return SNP_OK;

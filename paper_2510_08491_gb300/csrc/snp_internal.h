@@ -94,6 +94,10 @@ constexpr uint32_t kNoStore = 0xffffffffu;
 constexpr uint32_t kColBlock = 8192;
 
 // snp_raster_*.cu
+// CTAs per SM of the calling thread's last persistent raster launch (recorded when
+// its grid is sized).
+void note_raster_ctas(int per_sm);
+int last_raster_ctas();
 snp_status launch_raster_fwd(const RasterArgs &a, int color_mode, int n_c, int form, int bf16, int ts,
                              cudaStream_t st);
 // snp_sh.cu

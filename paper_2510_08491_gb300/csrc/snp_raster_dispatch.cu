@@ -53,6 +53,10 @@ int raster_default_chunk(int color_mode, int n_c, int n_sigma, bool backward, in
     return ch;
 }
 
+static thread_local int t_raster_ctas = 0;
+void note_raster_ctas(int per_sm) { t_raster_ctas = per_sm; }
+int last_raster_ctas() { return t_raster_ctas; }
+
 int raster_npack_stride(int color_mode, int n_c, int n_sigma)
 {
     return den_stride(n_sigma) + col_stride(nc_of(color_mode, n_c));

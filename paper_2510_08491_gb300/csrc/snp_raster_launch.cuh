@@ -60,6 +60,7 @@ static int persistent_grid(K kern, int threads, size_t smem, int64_t n_tiles, in
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
     }
+    note_raster_ctas(nb > 0 ? nb : 1);
     int64_t g = (int64_t)(nb > 0 ? nb : 1) * sms;
     if (g > n_tiles) g = n_tiles;
     return (int)(g > 0 ? g : 1);
