@@ -827,12 +827,27 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                         uint32_t r[32];
                         tmem_ld32(s_tmaddr + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)e + 32u * (uint32_t)half, r);
                         if (lane < 16) {
+                            // The 16 rows are 256 bytes apart, so stores of the same 16-byte piece
+                            // of every row hit the same four banks (16-way).  Lane l rotates its
+                            // eight pieces by rot = l % 8 (a barrel shift of static register
+                            // indices): store j then writes piece (j + rot) % 8, and the 16 lanes
+                            // of one store cover all 32 banks.
+                            const int rot = (int)lane & 7;
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const bool b = (rot >> k) & 1;
+                                uint32_t t[32];
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) t[i] = b ? r[(i + (4 << k)) & 31] : r[i];
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) r[i] = t[i];
+                            }
                             float4 *dst = reinterpret_cast<float4 *>(land + e * NC * NC + (16 * q + (int)lane) * 64 +
                                                                      32 * half);
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                     __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                                dst[(j + rot) & 7] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
                         }
                     }
                 } else {
