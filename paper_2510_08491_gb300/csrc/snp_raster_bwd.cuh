@@ -85,34 +85,35 @@ __device__ __forceinline__ void flush_chunk(const RasterArgs &a, float *acc, int
     const int ns = a.n_sigma;
     if constexpr (NC > 0 && !TM) {  // (TM: the blocks came out of tensor memory row-major)
         // The fragment-order tiles (mn, nk) of row block mn hold exactly the rows
-        // 16 mn .. 16 mn + 15 of Wc2, and in both layouts that block occupies the
-        // same 16 NC words: permute block by block, in rounds of BR blocks held in
-        // registers (PB words per thread and block).
-        constexpr int NG8 = NC / 8, PB = 16 * NC / NT, BR = (16 / PB < 1 ? 1 : (16 / PB > NC / 16 ? NC / 16 : 16 / PB));
-        static_assert(PB * NT == 16 * NC, "a row block must split evenly over the threads");
-        for (int e = 0; e < cnt; ++e) {
-            if (na[e] == 0) continue;  // uniform over the block
+        // 16 mn .. 16 mn + 15 of Wc2, and in both layouts that block occupies the same
+        // 16 NC words: one warp per entry permutes it block by block in place, through
+        // registers.  Lane (g, t) takes the NC / 2 elements with its own (g, t) -- so
+        // every read of the warp covers 32 banks -- in an order chosen so that the
+        // writes do too: at step s it moves the element of tile nk = (g + s) mod 4
+        // (+ 4 (s / 16) at N_c = 64) and fragment register i = 2 ((s / 8) mod 2) +
+        // (g / 4 + s / 4) mod 2, whose row-major column 8 nk + 2 t + i mod 2 differs
+        // across the 32 lanes.  No block barrier is needed.
+        const int lane = tid & 31, g = lane >> 2, t = lane & 3;
+        for (int e = tid >> 5; e < cnt; e += nt >> 5) {
+            if (na[e] == 0) continue;  // uniform over the warp
             float *W = acc + e * vg + a.off_Wc2;
-            for (int b0 = 0; b0 < NC / 16; b0 += BR) {
-                float v[BR][PB];
+            for (int mn = 0; mn < NC / 16; ++mn) {
+                float *B = W + mn * 16 * NC;
+                float v[NC / 2];
 #pragma unroll
-                for (int b = 0; b < BR; ++b)
-#pragma unroll
-                    for (int j = 0; j < PB; ++j) v[b][j] = W[(b0 + b) * 16 * NC + tid + j * NT];
-                __syncthreads();
-#pragma unroll
-                for (int b = 0; b < BR; ++b) {
-#pragma unroll
-                    for (int j = 0; j < PB; ++j) {
-                        // fragment order ((mn NC/8 + nk) 4 + i) 32 + l -> row n, column k
-                        const int q = (b0 + b) * 16 * NC + tid + j * NT;
-                        const int ln = q & 31, i = (q >> 5) & 3, tile = q >> 7;
-                        const int n = 16 * (tile / NG8) + (ln >> 2) + 8 * (i >> 1);
-                        const int k = 8 * (tile % NG8) + 2 * (ln & 3) + (i & 1);
-                        W[n * NC + k] = v[b][j];
-                    }
+                for (int s = 0; s < NC / 2; ++s) {
+                    const int nk = ((g + s) & 3) | (NC == 64 ? ((s >> 4) & 1) << 2 : 0);
+                    const int i = 2 * ((s >> 3) & 1) + (((g >> 2) + (s >> 2)) & 1);
+                    v[s] = B[(nk * 4 + i) * 32 + lane];
                 }
-                __syncthreads();
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < NC / 2; ++s) {
+                    const int nk = ((g + s) & 3) | (NC == 64 ? ((s >> 4) & 1) << 2 : 0);
+                    const int ih = (s >> 3) & 1, c = ((g >> 2) + (s >> 2)) & 1;
+                    B[(g + 8 * ih) * NC + 8 * nk + 2 * t + c] = v[s];
+                }
+                __syncwarp();
             }
         }
     }

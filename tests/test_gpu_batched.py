@@ -50,11 +50,14 @@ def test_tile_sizes_give_identical_images(R, oracle_lib, color):
     assert_image_close(imgs[16], ref, flags)
 
 
-@pytest.mark.parametrize("ts", [8, 32])
-def test_tile_size_backward(R, oracle_lib, ts):
+@pytest.mark.parametrize("ts,nc", [(8, 32), (32, 32), (8, 64)])
+def test_tile_size_backward(R, oracle_lib, ts, nc):
+    """Backward at 8- and 32-pixel tiles against the oracle; at 8-pixel tiles and
+    N_c = 64 the kernel accumulates dL/dWc2 with shared-memory atomics (not in
+    tensor memory) and its flush permutes the 64 x 64 block from fragment order."""
     from test_gpu_backward import _check, _dl, _gpu_grads_cfg, _oracle_grads
     O = oracle_lib
-    sc = synth.make_scene(1200, seed=3, center_half=1.5, n_sigma=16, omega0=5.0, color="mlp", n_c=32)
+    sc = synth.make_scene(1200, seed=3, center_half=1.5, n_sigma=16, omega0=5.0, color="mlp", n_c=nc)
     cams = [synth.look_at_camera((0.0, 0.5, 6.0), (0, 0, 0), 72, 56)]
     dLv = _dl(O, sc, cams, 3)
     g = _gpu_grads_cfg(R, sc, cams, np.concatenate(dLv), tile_size=ts)
