@@ -612,14 +612,14 @@ __device__ __forceinline__ void warp_color_bwd_pass(const float *Cb, const float
                            w * dl[2 * npix + q] * cz * (1.0f - cz));
     };
     const float3 e0 = ga3(pr.v0, pr.pix0), e1 = ga3(pr.v1, pr.pix1);
-    // dL/dbc3 = sum of dL/da3 over the pass (one lane per row pair contributes)
+    // dL/dbc3 = sum of dL/da3 over the pass.  The four lanes of a row pair hold the
+    // same e0, e1: lane (g, t < 3) takes channel t and the sum runs over g only
+    // (lane bits 2..4), leaving channel t's total in lane t.
     {
-        float b[3] = {t == 0 ? e0.x + e1.x : 0.0f, t == 0 ? e0.y + e1.y : 0.0f, t == 0 ? e0.z + e1.z : 0.0f};
+        float b = t == 0 ? e0.x + e1.x : (t == 1 ? e0.y + e1.y : (t == 2 ? e0.z + e1.z : 0.0f));
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            b[k] = warp_sum(b[k]);
-            if (lane == k && b[k] != 0.0f) atomicAdd(AB3 + k, b[k]);
-        }
+        for (int o = 4; o < 32; o <<= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (lane < 3 && b != 0.0f) atomicAdd(AB3 + lane, b);
     }
     float z[NC / 8][4];
     color_layer1<NC>(C1, d0, d1, z);
