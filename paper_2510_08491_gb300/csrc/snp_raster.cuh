@@ -195,7 +195,9 @@ __global__ void __launch_bounds__(256) k_pack_net(RasterArgs a)
             }
             C[cb_C1(NC) + idx] = v;
         }
-        // Wc2 rows as bf16 hi / lo pairs, padded to w2_ld(NC) columns
+        // Wc2 rows as bf16 hi / lo pairs, padded to w2_ld(NC) columns (with BF16
+        // weights the lo half is zero, and neither staging copies nor the kernels
+        // read it: it is not written)
         uint32_t *W = reinterpret_cast<uint32_t *>(C + cb_W2(NC));
         constexpr int rowp = w2_ld(NC) / 2;
         for (int q = lane; q < NC * rowp; q += 32) {
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(256) k_pack_net(RasterArgs a)
                 sp = split2<!BF16>(ld_w<BF16>(a.net, w), ld_w<BF16>(a.net, w + 1));
             }
             W[q] = sp.hi;
-            W[NC * rowp + q] = sp.lo;
+            if constexpr (!BF16) W[NC * rowp + q] = sp.lo;
         }
         for (int j = lane; j < NC; j += 32) {
             C[cb_B2(NC) + j] = ld_w<BF16>(a.net, base + a.off_bc2 + j);
