@@ -569,17 +569,17 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
         // Per chunk: its keys' record ids, colour-store offsets, composited masks and
         // composited counts, in one of two halves of s_gid / s_koff / s_cmw / s_na; the
         // next chunk's ids, offsets and masks are copied into the other half (4-byte
-        // cp.async) while this chunk runs P6.  With kEarly the next chunk is then begun
-        // before this chunk's flush: its staging copies are issued and P1 builds its pair
-        // lists and issues its store copies, so that the copies land while the flush
-        // runs.  (Measured: without a colour network 37.1 -> 35.7 ms on the 8-view 800 x 800
-        // speed protocol; at N_c = 32, two CTAs per SM, the other CTA already covers the
-        // copies and the early begin was 0.6 ms slower, so that kernel begins each chunk
-        // after the previous flush.)
-        uint32_t cm[PPT];  // per pixel: entries of the begun chunk it composited
-        // Begin chunk (c0b, cib): its ids, offsets and masks (copied in during the
-        // previous chunk's P6 if `prefetched`, else loaded here), its staging copies and P1.
-        auto begin_chunk = [&](uint32_t c0b, int cib, bool prefetched) {
+        // cp.async) while this chunk runs P6.  Before this chunk's flush the next chunk's
+        // staging copies are issued, and with kEarly P1 also builds its pair lists and
+        // issues its store copies there, so that the copies land while the flush runs.
+        // (Measured: without a colour network 37.1 -> 35.7 ms on the 8-view 800 x 800
+        // speed protocol.  At N_c = 32, two CTAs per SM, P1 before the flush was 0.6 ms
+        // slower, the staging copies alone there 0.3 ms faster: that kernel builds its
+        // lists after the flush.)
+        uint32_t cm[PPT];  // per pixel: entries of the chunk whose lists were built last
+        // Chunk (c0b, cib): its ids, offsets and masks (copied in during the previous
+        // chunk's P6 if `prefetched`, else loaded here) and its staging copies.
+        auto stage_begin = [&](uint32_t c0b, int cib, bool prefetched) {
             const int cntb = min((int)(rg.y - c0b), CH);
             uint32_t *const bg = s_gid + (cib & 1) * (kMaxChunk / 2);
             uint32_t *const bko = s_koff + (cib & 1) * 32;
@@ -606,6 +606,13 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             // covers them and P1's store copies
             if constexpr (NC > 0) stage_chunk_issue<NC, BF16>(sm, bg, cntb, vn, a, es);
             else stage_issue_flat(sm, bg, cntb, vn, a, es);
+        };
+        // P1 of chunk (c0b, cib), whose ids, offsets and masks are in place
+        auto build_lists = [&](uint32_t c0b, int cib) {
+            const int cntb = min((int)(rg.y - c0b), CH);
+            const uint32_t *const bko = s_koff + (cib & 1) * 32;
+            const uint32_t *const bmw = s_cmw + (cib & 1) * (kMaskWords / 2);
+            int *const bna = s_na + (cib & 1) * 33;
             // P1: the pixels that composited each entry, from the forward's masks (entries
             // at or past the tile's walk length were composited by no pixel)
 #pragma unroll
@@ -649,8 +656,10 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
             uint32_t *const cg = s_gid + (ci & 1) * (kMaxChunk / 2);
             uint32_t *const cko = s_koff + (ci & 1) * 32;
             const int *const na = s_na + (ci & 1) * 33;
-            // (kEarly: a chunk after the first was begun before the previous chunk's flush)
-            if (ci == 0 || !kEarly) begin_chunk(c0, ci, ci > 0);
+            // A chunk after the first had its staging copies issued before the previous
+            // chunk's flush, and with kEarly its pair lists built there too.
+            if (ci == 0) stage_begin(c0, 0, false);
+            if (ci == 0 || !kEarly) build_lists(c0, ci);
             if (tid == 0) s_item6 = 0;
             cp_async_wait_all();  // this chunk's staging and store copies
             if constexpr (NC == 0) stage_shift_flat<BF16>(sm, cg, cnt, vn, a, es, V.time);
@@ -876,9 +885,12 @@ __global__ void __launch_bounds__(TileCfg<TS>::NT, bwd_min_blocks(TS, NC)) k_ras
                 tc_fence_before_sync();
                 __syncthreads();
             }
-            // kEarly: the next chunk begins before this chunk's flush, so that its copies
-            // land meanwhile
-            if (kEarly && pre) begin_chunk(c0n, ci + 1, true);
+            // the next chunk's staging copies (and with kEarly its lists) before this
+            // chunk's flush, so that the copies land meanwhile
+            if (pre) {
+                stage_begin(c0n, ci + 1, true);
+                if constexpr (kEarly) build_lists(c0n, ci + 1);
+            }
             flush_chunk<NC, NT, TM>(a, acc, vg, cg, cnt, na, vn, tid, NT, V.time, land);
             clear_n = cnt * vg / 4;
         }
